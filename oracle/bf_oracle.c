@@ -1,0 +1,414 @@
+/*
+ * FP64 CPU oracle for the trigonometric O(1) bilateral filter
+ * (Chaudhury, Sage, Unser, "Fast O(1) bilateral filtering using trigonometric
+ * range kernels").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header, table or constant
+ * with the CUDA library; the two meet only through seeded synthetic inputs.
+ *
+ * Everything here is written out from the paper's definitions, slowly and in
+ * double precision:
+ *   - or_bf_brute*     : the bilateral filter in its unbiased form,
+ *                        eq. (BF) and eq. (normalization), summed directly
+ *                        over the support of the spatial kernel;
+ *   - or_bf_trig       : Algorithm 1, steps 3-5, with the N+1 complex
+ *                        auxiliary images of the raised-cosine expansion
+ *                        (Section 2.3) and eq. (final-form);
+ *   - or_bf_grad       : the exact derivative of eq. (BF) with respect to
+ *                        every input pixel and to sigma_r (not in the paper;
+ *                        the chain rule applied to the definition);
+ *   - or_bf_fd_grad_f  : central finite differences of or_bf_brute for the
+ *                        same gradient.
+ *
+ * Readings of the paper used here (each one also listed in the design notes):
+ *   - Degree rule (Algorithm 1 step 2, Table 1 last row):
+ *       N = max(1, ceil((gamma*sigma_r)^-2)), gamma = pi/(2T).
+ *   - Range kernel (Algorithm 1 step 3 with rho = gamma*sigma_r):
+ *       phi(s) = cos(gamma*s/(rho*sqrt(N)))^N = cos(s/(sigma_r*sqrt(N)))^N,
+ *     evaluated directly as a power, never through its expansion.
+ *     Mode 1 is the Gaussian exp(-s^2/(2 sigma_r^2)) that eq. (convergence1)
+ *     approximates.
+ *   - Boundary: the paper integrates over Omega and is silent about image
+ *     borders; the image is extended by clamping each coordinate to the
+ *     nearest edge pixel.
+ *   - Spatial kernels: a truncated Gaussian normalised over [-R, R]
+ *     (the experiments use the support [-3 sigma, 3 sigma]), or an iterated
+ *     box b*b*...*b with b = 1/(2r+1) on [-r, r].  Both are separable
+ *     w(y1, y2) = w1(y1) w1(y2) and have unit mass (eq. (averaging)).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <complex.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+
+static int or_clamp(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Degree rule: Algorithm 1 step 2 ("set N = (gamma sigma_r)^-2"), rounded up
+ * as in the last row of Table 1.  A relative guard of 1e-12 keeps a value that
+ * is an integer in exact arithmetic from being pushed up by rounding. */
+int or_n_rule(double sigma_r, double T)
+{
+    double gamma = OR_PI / (2.0 * T);
+    double x = 1.0 / ((gamma * sigma_r) * (gamma * sigma_r));
+    double n = ceil(x * (1.0 - 1e-12));
+    if (n < 1.0) n = 1.0;
+    if (n > 1e7) n = 1e7;
+    return (int)n;
+}
+
+/* One-dimensional spatial weights w1[0 .. 2R] (index k <-> offset k - R).
+ * kind 0: truncated Gaussian exp(-i^2 / (2 sigma_s^2)) on |i| <= R,
+ *         R = radius_override > 0 ? radius_override : ceil(3 sigma_s),
+ *         normalised to unit sum.
+ * kind 1: iterated box, `passes` boxes of half-width r
+ *         (r = radius_override > 0 ? radius_override : the r whose
+ *          variance passes*((2r+1)^2-1)/12 is closest to sigma_s^2),
+ *         built as exact integer counts divided by (2r+1)^passes.
+ * Returns R (support half-width), or -1 when cap is too small. */
+int or_spatial_w1(int kind, double sigma_s, int radius_override, int passes,
+                  double *w1, int cap)
+{
+    if (kind == 0) {
+        int R = radius_override > 0 ? radius_override : (int)ceil(3.0 * sigma_s);
+        if (R < 0) R = 0;
+        if (2 * R + 1 > cap) return -1;
+        double s = 0.0;
+        for (int i = -R; i <= R; i++) {
+            double v = exp(-(double)i * i / (2.0 * sigma_s * sigma_s));
+            w1[i + R] = v;
+            s += v;
+        }
+        for (int k = 0; k <= 2 * R; k++) w1[k] /= s;
+        return R;
+    } else {
+        if (passes <= 0) passes = 3;
+        int r = radius_override;
+        if (r <= 0) {
+            double L = sqrt(12.0 * sigma_s * sigma_s / passes + 1.0);
+            r = (int)floor((L - 1.0) / 2.0 + 0.5);
+            if (r < 1) r = 1;
+        }
+        int R = passes * r;
+        if (2 * R + 1 > cap) return -1;
+        /* counts[k] = number of ways offsets of `passes` boxes sum to k - R */
+        double *cnt = (double *)calloc((size_t)(2 * R + 1), sizeof(double));
+        double *tmp = (double *)calloc((size_t)(2 * R + 1), sizeof(double));
+        int cur = 0; /* current half-width */
+        cnt[R] = 1.0;
+        for (int p = 0; p < passes; p++) {
+            memset(tmp, 0, sizeof(double) * (size_t)(2 * R + 1));
+            for (int k = -cur; k <= cur; k++)
+                for (int d = -r; d <= r; d++) tmp[k + d + R] += cnt[k + R];
+            memcpy(cnt, tmp, sizeof(double) * (size_t)(2 * R + 1));
+            cur += r;
+        }
+        double denom = pow(2.0 * r + 1.0, passes);
+        for (int k = 0; k <= 2 * R; k++) w1[k] = cnt[k] / denom;
+        free(cnt);
+        free(tmp);
+        return R;
+    }
+}
+
+/* Range kernel and its derivatives.  mode 0: raised cosine of degree N with
+ * k = 1/(sigma_r sqrt N); mode 1: Gaussian of standard deviation sigma_r. */
+typedef struct { int mode; int N; double k; double sigma_r; } or_range;
+
+static or_range or_make_range(int mode, double sigma_r, int N)
+{
+    or_range r;
+    r.mode = mode;
+    r.N = N < 1 ? 1 : N;
+    r.sigma_r = sigma_r;
+    r.k = 1.0 / (sigma_r * sqrt((double)r.N));
+    return r;
+}
+
+static double or_phi(const or_range *r, double s)
+{
+    if (r->mode == 1) return exp(-s * s / (2.0 * r->sigma_r * r->sigma_r));
+    return pow(cos(r->k * s), r->N);
+}
+
+/* d phi / d s */
+static double or_dphi(const or_range *r, double s)
+{
+    if (r->mode == 1) return -s / (r->sigma_r * r->sigma_r) * or_phi(r, s);
+    double c = cos(r->k * s);
+    double cn1 = r->N == 1 ? 1.0 : pow(c, r->N - 1);
+    return -(double)r->N * r->k * cn1 * sin(r->k * s);
+}
+
+/* d phi / d sigma_r at fixed N (N is piecewise constant in sigma_r). */
+static double or_dphi_dsigma(const or_range *r, double s)
+{
+    return -(s / r->sigma_r) * or_dphi(r, s);
+}
+
+/* eq. (BF) and eq. (normalization) at one pixel (i, j) of an H x W image. */
+static void or_pq_at(const double *f, int H, int W, const double *w1, int R,
+                     const or_range *rg, int i, int j, double *P, double *Q)
+{
+    double fx = f[(size_t)i * W + j];
+    double p = 0.0, q = 0.0;
+    for (int a = -R; a <= R; a++) {
+        int zi = or_clamp(i - a, 0, H - 1);
+        for (int b = -R; b <= R; b++) {
+            int zj = or_clamp(j - b, 0, W - 1);
+            double wt = w1[a + R] * w1[b + R];
+            double v = f[(size_t)zi * W + zj];
+            double ph = or_phi(rg, v - fx);
+            p += wt * ph * v;
+            q += wt * ph;
+        }
+    }
+    *P = p;
+    *Q = q;
+}
+
+/* Brute-force filter of a whole single-channel image.  q_out may be NULL. */
+void or_bf_brute(const double *f, int H, int W, const double *w1, int R,
+                 int mode, double sigma_r, int N, double *out, double *q_out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < H; i++) {
+        for (int j = 0; j < W; j++) {
+            double P, Q;
+            or_pq_at(f, H, W, w1, R, &rg, i, j, &P, &Q);
+            out[(size_t)i * W + j] = P / Q;
+            if (q_out) q_out[(size_t)i * W + j] = Q;
+        }
+    }
+}
+
+/* Brute-force filter at a list of flat pixel indices only. */
+void or_bf_brute_at(const double *f, int H, int W, const double *w1, int R,
+                    int mode, double sigma_r, int N, const long long *idx,
+                    long long n_idx, double *out, double *q_out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long t = 0; t < n_idx; t++) {
+        int i = (int)(idx[t] / W), j = (int)(idx[t] % W);
+        double P, Q;
+        or_pq_at(f, H, W, w1, R, &rg, i, j, &P, &Q);
+        out[t] = P / Q;
+        if (q_out) q_out[t] = Q;
+    }
+}
+
+/* Separable filtering of a complex image with clamp-to-edge extension:
+ * y(i,j) = sum_a sum_b w1(a) w1(b) x(clamp(i-a), clamp(j-b)). */
+static void or_filter_c(const double complex *x, int H, int W, const double *w1,
+                        int R, double complex *tmp, double complex *y)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < H; i++)
+        for (int j = 0; j < W; j++) {
+            double complex s = 0.0;
+            for (int b = -R; b <= R; b++)
+                s += w1[b + R] * x[(size_t)i * W + or_clamp(j - b, 0, W - 1)];
+            tmp[(size_t)i * W + j] = s;
+        }
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < H; i++)
+        for (int j = 0; j < W; j++) {
+            double complex s = 0.0;
+            for (int a = -R; a <= R; a++)
+                s += w1[a + R] * tmp[(size_t)or_clamp(i - a, 0, H - 1) * W + j];
+            y[(size_t)i * W + j] = s;
+        }
+}
+
+/* Algorithm 1, steps 1-5, in the paper's complex notation:
+ *   gamma = pi/(2T), rho = gamma sigma_r                          (step 1)
+ *   h_n = exp(j gamma (2n-N) f / (rho sqrt N)), g_n = f h_n,
+ *   d_n = 2^-N C(N,n) exp(-j gamma (2n-N) f / (rho sqrt N))       (step 3)
+ *   filter h_n and g_n with the spatial kernel                    (step 4)
+ *   out = sum_n d_n gbar_n / sum_n d_n hbar_n                      (step 5)
+ * The degree N is passed in (the caller applies the rule of step 2).
+ * Returns the largest |Im| / |Re| of numerator and denominator seen. */
+double or_bf_trig(const double *f, int H, int W, const double *w1, int R,
+                  double sigma_r, double T, int N, double *out, double *q_out)
+{
+    size_t n = (size_t)H * W;
+    double gamma = OR_PI / (2.0 * T);
+    double rho = gamma * sigma_r;
+    double complex *h = (double complex *)malloc(n * sizeof(double complex));
+    double complex *g = (double complex *)malloc(n * sizeof(double complex));
+    double complex *hb = (double complex *)malloc(n * sizeof(double complex));
+    double complex *gb = (double complex *)malloc(n * sizeof(double complex));
+    double complex *tmp = (double complex *)malloc(n * sizeof(double complex));
+    double complex *num = (double complex *)calloc(n, sizeof(double complex));
+    double complex *den = (double complex *)calloc(n, sizeof(double complex));
+    for (int k = 0; k <= N; k++) {
+        /* 2^-N C(N,k), through log-gamma to stay finite for large N */
+        double cn = exp(lgamma(N + 1.0) - lgamma(k + 1.0) - lgamma(N - k + 1.0) -
+                        N * log(2.0));
+        double freq = gamma * (double)(2 * k - N) / (rho * sqrt((double)N));
+        for (size_t p = 0; p < n; p++) {
+            h[p] = cexp(I * freq * f[p]);
+            g[p] = f[p] * h[p];
+        }
+        or_filter_c(h, H, W, w1, R, tmp, hb);
+        or_filter_c(g, H, W, w1, R, tmp, gb);
+        for (size_t p = 0; p < n; p++) {
+            double complex d = cn * cexp(-I * freq * f[p]);
+            num[p] += d * gb[p];
+            den[p] += d * hb[p];
+        }
+    }
+    double worst = 0.0;
+    for (size_t p = 0; p < n; p++) {
+        out[p] = creal(num[p]) / creal(den[p]);
+        if (q_out) q_out[p] = creal(den[p]);
+        double e1 = fabs(cimag(num[p])) / (fabs(creal(num[p])) + 1e-300);
+        double e2 = fabs(cimag(den[p])) / (fabs(creal(den[p])) + 1e-300);
+        if (e1 > worst) worst = e1;
+        if (e2 > worst) worst = e2;
+    }
+    free(h); free(g); free(hb); free(gb); free(tmp); free(num); free(den);
+    return worst;
+}
+
+/* Exact gradient of L = sum_x u(x) out(x) with respect to every pixel of f
+ * and to sigma_r (N held fixed).  Chain rule on eq. (BF):
+ *   dL/df(p) = sum_x alpha(x) [ dP(x)/df(p) - out(x) dQ(x)/df(p) ],
+ *   alpha = u / Q,
+ * where each neighbour z of x contributes through its clamped pixel
+ * clamp(z) (value and range-kernel argument) and through x itself (the
+ * argument f(z) - f(x)). */
+void or_bf_grad(const double *f, const double *u, int H, int W, const double *w1,
+                int R, int mode, double sigma_r, int N, double *grad_f,
+                double *grad_sigma_r)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+    size_t n = (size_t)H * W;
+    int nt = or_num_threads();
+    double *buf = (double *)calloc(n * (size_t)nt, sizeof(double));
+    double *gs = (double *)calloc((size_t)nt, sizeof(double));
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *g = buf + n * (size_t)tid;
+        double gsl = 0.0;
+#pragma omp for schedule(dynamic, 4)
+        for (int i = 0; i < H; i++) {
+            for (int j = 0; j < W; j++) {
+                double P, Q;
+                or_pq_at(f, H, W, w1, R, &rg, i, j, &P, &Q);
+                double o = P / Q;
+                double alpha = u[(size_t)i * W + j] / Q;
+                double fx = f[(size_t)i * W + j];
+                for (int a = -R; a <= R; a++) {
+                    int zi = or_clamp(i - a, 0, H - 1);
+                    for (int b = -R; b <= R; b++) {
+                        int zj = or_clamp(j - b, 0, W - 1);
+                        double wt = w1[a + R] * w1[b + R];
+                        double v = f[(size_t)zi * W + zj];
+                        double s = v - fx;
+                        double ph = or_phi(&rg, s);
+                        double dph = or_dphi(&rg, s);
+                        g[(size_t)zi * W + zj] += alpha * wt * (ph + dph * (v - o));
+                        g[(size_t)i * W + j] -= alpha * wt * dph * (v - o);
+                        gsl += alpha * wt * or_dphi_dsigma(&rg, s) * (v - o);
+                    }
+                }
+            }
+        }
+        gs[tid] = gsl;
+    }
+    for (size_t p = 0; p < n; p++) {
+        double s = 0.0;
+        for (int t = 0; t < nt; t++) s += buf[n * (size_t)t + p];
+        grad_f[p] = s;
+    }
+    double s = 0.0;
+    for (int t = 0; t < nt; t++) s += gs[t];
+    if (grad_sigma_r) *grad_sigma_r = s;
+    free(buf);
+    free(gs);
+}
+
+/* Central finite differences of L = sum_x u(x) out(x) with respect to the
+ * listed pixels.  Only outputs within R of the perturbed pixel change, so only
+ * those are recomputed (with clamping, a neighbour that maps onto p lies
+ * within R of every output that sees it). */
+void or_bf_fd_grad_f(const double *f, const double *u, int H, int W,
+                     const double *w1, int R, int mode, double sigma_r, int N,
+                     const long long *idx, long long n_idx, double h, double *out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+    size_t n = (size_t)H * W;
+#pragma omp parallel
+    {
+        double *fl = (double *)malloc(n * sizeof(double));
+        memcpy(fl, f, n * sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+        for (long long t = 0; t < n_idx; t++) {
+            int pi = (int)(idx[t] / W), pj = (int)(idx[t] % W);
+            int i0 = pi - R < 0 ? 0 : pi - R, i1 = pi + R > H - 1 ? H - 1 : pi + R;
+            int j0 = pj - R < 0 ? 0 : pj - R, j1 = pj + R > W - 1 ? W - 1 : pj + R;
+            double orig = fl[idx[t]];
+            double L[2];
+            for (int sgn = 0; sgn < 2; sgn++) {
+                fl[idx[t]] = orig + (sgn == 0 ? h : -h);
+                double acc = 0.0;
+                for (int i = i0; i <= i1; i++)
+                    for (int j = j0; j <= j1; j++) {
+                        double P, Q;
+                        or_pq_at(fl, H, W, w1, R, &rg, i, j, &P, &Q);
+                        acc += u[(size_t)i * W + j] * (P / Q);
+                    }
+                L[sgn] = acc;
+            }
+            fl[idx[t]] = orig;
+            out[t] = (L[0] - L[1]) / (2.0 * h);
+        }
+        free(fl);
+    }
+}
+
+/* L = sum_x u(x) out(x) for the whole image (used for sigma_r differences). */
+double or_bf_loss(const double *f, const double *u, int H, int W, const double *w1,
+                  int R, int mode, double sigma_r, int N)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+    double total = 0.0;
+#pragma omp parallel for reduction(+ : total) schedule(dynamic, 4)
+    for (int i = 0; i < H; i++)
+        for (int j = 0; j < W; j++) {
+            double P, Q;
+            or_pq_at(f, H, W, w1, R, &rg, i, j, &P, &Q);
+            total += u[(size_t)i * W + j] * (P / Q);
+        }
+    return total;
+}
+
+/* The range kernel itself, for tests of the convergence claim. */
+void or_phi_table(int mode, double sigma_r, int N, const double *s, long long n,
+                  double *out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+    for (long long t = 0; t < n; t++) out[t] = or_phi(&rg, s[t]);
+}

@@ -1,0 +1,269 @@
+"""Pins of the FP64 oracle to things other than itself.
+
+Each test ties one part of the oracle to a value printed in the paper, a
+closed form worked by hand from eq. (BF), a mathematical identity, an
+invariant of the filter, or an independent library routine (scipy, numpy,
+torch autograd).  Together they are chosen so that a dropped term, a wrong
+sign, a wrong clamp index or a transposed operand in the oracle fails at
+least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small_image(H=23, W=19, seed=3):
+    return synth.rectangles(H, W, n_rect=5, noise=6.0, seed=seed).astype(np.float64)
+
+
+# ---------------------------------------------------------------- degree rule
+
+def test_degree_rule_matches_table1(oracle):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table1_degree.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 7
+    for sigma, _n0, n_rule in rows:
+        assert oracle.n_rule(float(sigma), 255.0) == int(n_rule), sigma
+
+
+def test_degree_rule_keeps_phase_in_half_period(oracle):
+    # Section 2.5: N must make the argument of cos stay in [-pi/2, pi/2] on
+    # [-T, T], i.e. T / (sigma_r sqrt N) <= pi / 2.
+    for sr in [5.0, 10.0, 15.0, 20.0, 25.0, 30.0, 47.3, 60.0, 100.0, 161.0]:
+        N = oracle.n_rule(sr, 255.0)
+        assert 255.0 / (sr * math.sqrt(N)) <= math.pi / 2 + 1e-12
+        if N > 1:  # and N is the smallest such degree
+            assert 255.0 / (sr * math.sqrt(N - 1)) > math.pi / 2
+
+
+# ------------------------------------------------------------- spatial kernel
+
+@pytest.mark.parametrize("r,passes", [(1, 1), (1, 3), (2, 3), (5, 3), (4, 2)])
+def test_box_weights_are_repeated_box_convolution(oracle, r, passes):
+    w = oracle.spatial_w1("box", 1.0, radius=r, passes=passes)
+    ref = np.ones(1)
+    for _ in range(passes):
+        ref = np.convolve(ref, np.ones(2 * r + 1) / (2 * r + 1))
+    np.testing.assert_allclose(w, ref, rtol=0, atol=1e-15)
+    # variance of the sum of `passes` uniform integers on [-r, r]
+    k = np.arange(-passes * r, passes * r + 1)
+    var = float(np.sum(w * k * k))
+    assert var == pytest.approx(passes * ((2 * r + 1) ** 2 - 1) / 12.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("sigma_s,expect_r", [(2.0, 2), (8.0, 8), (32.0, 32)])
+def test_box_radius_from_sigma(oracle, sigma_s, expect_r):
+    w = oracle.spatial_w1("box", sigma_s, passes=3)
+    assert (len(w) - 1) // 2 == 3 * expect_r
+
+
+def test_gauss_weights(oracle):
+    for s, R in [(3.0, 9), (4.0, 12), (6.0, 18)]:
+        w = oracle.spatial_w1("gauss", s)
+        assert len(w) == 2 * R + 1
+        assert w.sum() == pytest.approx(1.0, abs=1e-15)
+        k = np.arange(-R, R + 1)
+        np.testing.assert_allclose(w / w[R], np.exp(-k * k / (2 * s * s)), rtol=1e-14)
+
+
+# --------------------------------------------------------- hand-worked examples
+
+def _golden_hand():
+    vals = {}
+    for l in open(os.path.join(GOLDEN, "hand_examples.txt")):
+        if l.strip() and not l.startswith("#"):
+            k, v = l.split()
+            vals[k] = float(v)
+    return vals
+
+
+def test_hand_examples(oracle):
+    g = _golden_hand()
+    c = math.cos(0.5)
+    # closed forms worked by hand from eq. (BF)
+    assert g["1d_p0"] == pytest.approx(100 * c / (2 + c), abs=5e-8)
+    assert g["2d_00"] == pytest.approx(400 * c / (5 + 4 * c), abs=5e-8)
+    w1 = oracle.spatial_w1("box", 1.0, radius=1, passes=1)
+    assert oracle.n_rule(200.0, 255.0) == 1
+    out1 = oracle.bf_brute(np.array([[0.0, 100.0]]), sigma_r=200.0, w1=w1)
+    np.testing.assert_allclose(out1[0], [100 * c / (2 + c), 200 / (2 + c)], atol=1e-12)
+    np.testing.assert_allclose(out1[0], [g["1d_p0"], g["1d_p1"]], atol=1e-7)
+    out2 = oracle.bf_brute(np.array([[0.0, 100.0], [100.0, 0.0]]), sigma_r=200.0, w1=w1)
+    np.testing.assert_allclose(out2, [[g["2d_00"], g["2d_01"]], [g["2d_10"], g["2d_11"]]],
+                               atol=1e-7)
+    # the complex form of Algorithm 1 gives the same numbers
+    out3 = oracle.bf_trig(np.array([[0.0, 100.0], [100.0, 0.0]]), sigma_r=200.0, w1=w1)
+    np.testing.assert_allclose(out3, out2, atol=1e-10)
+
+
+# ------------------------------------------------------------------ invariants
+
+@pytest.mark.parametrize("kind,ss", [("gauss", 2.0), ("box", 1.0)])
+def test_constant_image_preserved(oracle, kind, ss):
+    f = np.full((9, 13), 117.25)
+    out = oracle.bf_brute(f, sigma_s=ss, sigma_r=20.0, kind=kind)
+    np.testing.assert_allclose(out, 117.25, rtol=1e-13)
+
+
+def test_shift_equivariance(oracle):
+    f = _small_image()
+    a = oracle.bf_brute(f, sigma_s=2.0, sigma_r=25.0)
+    b = oracle.bf_brute(f + 31.5, sigma_s=2.0, sigma_r=25.0)
+    np.testing.assert_allclose(b, a + 31.5, atol=1e-9)
+
+
+def test_flip_and_transpose_equivariance(oracle):
+    f = _small_image()
+    kw = dict(sigma_s=1.5, sigma_r=30.0)
+    a = oracle.bf_brute(f, **kw)
+    np.testing.assert_allclose(oracle.bf_brute(f[::-1], **kw), a[::-1], atol=1e-10)
+    np.testing.assert_allclose(oracle.bf_brute(f[:, ::-1], **kw), a[:, ::-1], atol=1e-10)
+    np.testing.assert_allclose(oracle.bf_brute(f.T.copy(), **kw), a.T, atol=1e-10)
+
+
+def test_output_inside_neighbourhood_range(oracle):
+    f = _small_image()
+    R = 3
+    out = oracle.bf_brute(f, sigma_s=1.0, sigma_r=15.0)  # R = ceil(3 * 1) = 3
+    H, W = f.shape
+    for i in range(H):
+        for j in range(W):
+            nb = f[max(0, i - R):i + R + 1, max(0, j - R):j + R + 1]
+            assert nb.min() - 1e-9 <= out[i, j] <= nb.max() + 1e-9
+
+
+def test_linear_limit_is_clamped_convolution(oracle):
+    # sigma_r -> infinity: phi -> 1 and eq. (BF) reduces to eq. (averaging).
+    from scipy.ndimage import convolve1d
+    f = _small_image()
+    for kind, ss in [("gauss", 2.0), ("box", 1.0)]:
+        w1 = oracle.spatial_w1(kind, ss)
+        out = oracle.bf_brute(f, sigma_r=1e9, w1=w1)
+        ref = convolve1d(convolve1d(f, w1, axis=0, mode="nearest"), w1, axis=1,
+                         mode="nearest")
+        np.testing.assert_allclose(out, ref, atol=1e-9)
+
+
+# ------------------------------------------------ raised cosine and its expansion
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 11, 30, 66])
+def test_raised_cosine_binomial_identity(oracle, N):
+    # Section 2.3: cos^N(x) = sum_n 2^-N C(N,n) exp(j (2n-N) x), exact integers.
+    sr = 20.0
+    s = np.linspace(-255, 255, 1021)
+    x = s / (sr * math.sqrt(N))
+    expansion = sum(math.comb(N, n) * np.cos((2 * n - N) * x) for n in range(N + 1))
+    expansion = expansion / 2.0 ** N
+    np.testing.assert_allclose(oracle.phi(s, sr, N=N), expansion, atol=1e-13)
+
+
+def test_raised_cosine_approaches_gaussian(oracle):
+    # eq. (convergence1): cos^N(s / (sigma sqrt N)) -> exp(-s^2 / 2 sigma^2).
+    s = np.linspace(-255, 255, 2041)
+    sr = 40.0
+    g = oracle.phi(s, sr, range_mode="gaussian")
+    errs = [np.max(np.abs(oracle.phi(s, sr, N=N) - g)) for N in [17, 34, 68, 136, 272]]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 2e-3
+    # and the filter output follows
+    f = _small_image(17, 15)
+    out_g = oracle.bf_brute(f, sigma_s=1.5, sigma_r=sr, range_mode="gaussian")
+    diffs = [np.max(np.abs(oracle.bf_brute(f, sigma_s=1.5, sigma_r=sr, N=N) - out_g))
+             for N in [17, 68, 272]]
+    assert diffs[2] < diffs[0]
+
+
+@pytest.mark.parametrize("kind,ss,sr,N", [
+    ("gauss", 2.0, 30.0, None),   # N = 30 (even)
+    ("gauss", 1.0, 50.0, None),   # N = 11 (odd)
+    ("box", 1.0, 20.0, None),     # N = 66
+    ("box", 2.0, 200.0, None),    # N = 1
+    ("gauss", 1.0, 25.0, 2),      # N override
+])
+def test_algorithm1_complex_form_matches_definition(oracle, kind, ss, sr, N):
+    # Section 2.2 says eq. (final-form) is exact for trigonometric kernels.
+    f = _small_image(21, 18, seed=7)
+    w1 = oracle.spatial_w1(kind, ss)
+    a = oracle.bf_brute(f, sigma_r=sr, w1=w1, N=N)
+    b, worst_imag = oracle.bf_trig(f, sigma_r=sr, w1=w1, N=N, return_imag=True)
+    np.testing.assert_allclose(b, a, atol=1e-8)
+    assert worst_imag < 1e-9
+
+
+def test_brute_at_matches_full(oracle):
+    f = _small_image()
+    w1 = oracle.spatial_w1("box", 1.0)
+    full, q = oracle.bf_brute(f, sigma_r=30.0, w1=w1, return_q=True)
+    idx = synth.sample_indices(*f.shape, 20, seed=1)
+    o, qq = oracle.bf_brute_at(f, idx, sigma_r=30.0, w1=w1, return_q=True)
+    np.testing.assert_array_equal(o, full.ravel()[idx])
+    np.testing.assert_array_equal(qq, q.ravel()[idx])
+
+
+def test_multichannel_is_per_channel(oracle):
+    img = synth.rect_disk_u8(14, 11, C=3, n_shapes=6, seed=2).astype(np.float64)
+    out = oracle.bf_brute(img, sigma_s=1.0, sigma_r=30.0)
+    for c in range(3):
+        np.testing.assert_array_equal(out[:, :, c],
+                                      oracle.bf_brute(img[:, :, c], sigma_s=1.0, sigma_r=30.0))
+
+
+# ------------------------------------------------------------------- gradient
+
+def test_gradient_matches_finite_differences(oracle):
+    f = _small_image(16, 14, seed=11)
+    u = synth.upstream(f.shape, seed=5).astype(np.float64)
+    kw = dict(sigma_s=1.3, sigma_r=25.0)  # R = 4, N = 43
+    g, gs = oracle.bf_grad(f, u, **kw)
+    idx = np.arange(f.size)  # every pixel: all of them touch a border here
+    fd = oracle.fd_grad_f(f, u, idx, h=1e-4, **kw)
+    np.testing.assert_allclose(g.ravel(), fd, atol=1e-6 * np.abs(fd).max())
+    fds = oracle.fd_grad_sigma_r(f, u, h=1e-4, **kw)
+    assert gs == pytest.approx(fds, rel=1e-6)
+
+
+def test_gradient_box_and_gaussian_range(oracle):
+    f = _small_image(12, 15, seed=4)
+    u = synth.upstream(f.shape, seed=8).astype(np.float64)
+    for kw in [dict(kind="box", sigma_s=1.0, sigma_r=40.0),
+               dict(kind="gauss", sigma_s=1.0, sigma_r=35.0, range_mode="gaussian")]:
+        g, gs = oracle.bf_grad(f, u, **kw)
+        idx = np.arange(f.size)
+        fd = oracle.fd_grad_f(f, u, idx, h=1e-4, **kw)
+        np.testing.assert_allclose(g.ravel(), fd, atol=1e-6 * np.abs(fd).max())
+        assert gs == pytest.approx(oracle.fd_grad_sigma_r(f, u, h=1e-4, **kw), rel=1e-6)
+
+
+def test_gradient_matches_torch_autograd(oracle):
+    # An independent derivative: torch's reverse-mode autodiff of eq. (BF)
+    # evaluated with gathers over the clamp-extended image.
+    torch = pytest.importorskip("torch")
+    f = _small_image(9, 8, seed=9)
+    u = synth.upstream(f.shape, seed=1).astype(np.float64)
+    sr, ss = 22.0, 0.9
+    w1 = oracle.spatial_w1("gauss", ss)
+    R = (len(w1) - 1) // 2
+    N = oracle.n_rule(sr)
+    H, W = f.shape
+    ft = torch.tensor(f, dtype=torch.float64, requires_grad=True)
+    srt = torch.tensor(sr, dtype=torch.float64, requires_grad=True)
+    ii = torch.arange(H)[:, None, None, None]
+    jj = torch.arange(W)[None, :, None, None]
+    aa = torch.arange(-R, R + 1)[None, None, :, None]
+    bb = torch.arange(-R, R + 1)[None, None, None, :]
+    zi = (ii - aa).clamp(0, H - 1)
+    zj = (jj - bb).clamp(0, W - 1)
+    nb = ft[zi, zj]                                   # H x W x (2R+1) x (2R+1)
+    wt = torch.tensor(np.outer(w1, w1))[None, None]
+    ph = torch.cos((nb - ft[:, :, None, None]) / (srt * math.sqrt(N))) ** N
+    out = (wt * ph * nb).sum((2, 3)) / (wt * ph).sum((2, 3))
+    (out * torch.tensor(u)).sum().backward()
+    g, gs = oracle.bf_grad(f, u, sigma_s=ss, sigma_r=sr, w1=w1)
+    np.testing.assert_allclose(g, ft.grad.numpy(), atol=1e-11)
+    assert gs == pytest.approx(float(srt.grad), rel=1e-10)
