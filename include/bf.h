@@ -1,0 +1,212 @@
+/*
+ * libbf -- the trigonometric O(1) bilateral filter of Chaudhury, Sage and
+ * Unser ("Fast O(1) bilateral filtering using trigonometric range kernels"),
+ * as hand-written CUDA for GB300 (sm_103a).
+ *
+ * What every entry point computes (Section 1, eq. (BF) and
+ * eq. (normalization), the unbiased form):
+ *
+ *     out(x) = sum_y w(y) phi(f(x-y) - f(x)) f(x-y) / sum_y w(y) phi(f(x-y) - f(x))
+ *
+ * with the raised-cosine range kernel of Section 2.3 scaled as in Algorithm 1
+ * step 3 (rho = gamma sigma_r, gamma = pi/(2T)):
+ *
+ *     phi(s) = cos(s / (sigma_r sqrt(N)))^N
+ *            = sum_{n=0..N} 2^-N C(N,n) exp(j (2n-N) s / (sigma_r sqrt(N)))
+ *
+ * evaluated through eq. (final-form): spatial averages of the auxiliary images
+ * cos(w f), sin(w f), f cos(w f), f sin(w f), combined per pixel and divided.
+ * The degree is N = max(1, ceil((gamma sigma_r)^-2)) (Algorithm 1 step 2,
+ * Table 1).  The image is extended past its border by clamping coordinates to
+ * the nearest edge pixel (the paper integrates over Omega and does not say).
+ *
+ * Conventions shared by all calls:
+ *   - Every pointer named in/out/f/q/grad/workspace is a DEVICE pointer owned
+ *     by the caller; the library never frees it.  Host pointers are named as
+ *     such.  Images are row-major.
+ *   - Calls that take a cudaStream_t are asynchronous on that stream; the
+ *     returned status covers argument checks and launch errors only.
+ *   - On any status other than BF_OK, bf_last_error() returns a message for
+ *     the calling thread.  No call aborts the process.
+ *   - Input values are expected in [0, T] (Section 2.1); they are not checked.
+ */
+#ifndef BF_H_
+#define BF_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same definition as the CUDA runtime's; repeated so this header stands alone. */
+typedef struct CUstream_st *cudaStream_t;
+
+typedef enum {
+    BF_OK = 0,
+    BF_EINVAL = 1,         /* bad argument (NULL pointer, size, sigma, stride) */
+    BF_EUNSUPPORTED = 2,   /* valid but outside what the kernels implement */
+    BF_ECUDA = 3,          /* a CUDA runtime call or launch failed */
+    BF_ENOMEM = 4,         /* host or device allocation failed */
+    BF_ETIMEOUT = 5        /* a bounded device-side wait ran out */
+} bf_status;
+
+typedef enum {
+    BF_SPATIAL_GAUSS_TRUNC = 0,  /* w1(i) ~ exp(-i^2 / 2 sigma_s^2), |i| <= R, unit sum */
+    BF_SPATIAL_BOX_ITER = 1      /* box_passes boxes of half-width r, convolved */
+} bf_spatial_kind;
+
+typedef enum { BF_F32 = 0, BF_U8 = 1 } bf_dtype;
+
+typedef struct {
+    int N_override;      /* degree N; 0 = the rule N = max(1, ceil((gamma sigma_r)^-2)) */
+    int radius_override; /* Gaussian: support half-width R (0 = ceil(3 sigma_s));
+                            box: half-width r of one box (0 = the r whose
+                            box_passes-fold variance is closest to sigma_s^2) */
+    int box_passes;      /* box only; 0 = 3.  Only 3 is implemented. */
+} bf_plan_opts;
+
+/* Opaque, host-owned plan.  Creating one never touches a GPU. */
+typedef struct bf_plan bf_plan;
+
+/*
+ * Algorithm 1 steps 1-3, on the host in double precision: the degree N, the
+ * binomial coefficients 2^-N C(N,n) folded into one real weight per distinct
+ * frequency |2n - N| / (sigma_r sqrt N), and the 1-D spatial taps.
+ *   out      : receives the plan (host memory, free with bf_plan_destroy)
+ *   sigma_s  : spatial standard deviation, > 0
+ *   sigma_r  : range standard deviation, > 0
+ *   T        : dynamic range bound of the image values, > 0 (255 for 8-bit)
+ *   kind     : spatial kernel
+ *   opts     : NULL for defaults
+ * Errors: BF_EINVAL for non-positive or non-finite sigma/T or a NULL out;
+ *         BF_EUNSUPPORTED for N > 4096, a support radius above the kernels'
+ *         limits, or box_passes other than 3.
+ */
+bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_r, double T,
+                         bf_spatial_kind kind, const bf_plan_opts *opts);
+
+void bf_plan_destroy(bf_plan *plan);
+
+/*
+ * Host-side facts about a plan (any output pointer may be NULL):
+ *   N                : degree of the raised cosine
+ *   n_freq           : number of terms the kernels evaluate: distinct nonzero
+ *                      frequencies whose FP32 weight is not 0, plus one for
+ *                      the constant term when N is even
+ *   radius           : support half-width of the 2-D spatial kernel per axis
+ *                      (R for the Gaussian, box_passes*r for the box)
+ *   achieved_sigma_s : standard deviation of the 1-D spatial kernel in use
+ */
+bf_status bf_plan_info(const bf_plan *plan, int *N, int *n_freq, int *radius,
+                       double *achieved_sigma_s);
+
+/*
+ * The plan's term table in FP64 (host memory): for term k,
+ *   a[k]     weight of cos(omega[k] (f(y) - f(x))) in phi, and
+ *   omega[k] its angular frequency in radians per gray level.
+ * Terms come in the order the kernels accumulate them (smallest weight first,
+ * the constant term omega = 0 last).  sum_k a[k] cos(omega[k] s) = phi(s).
+ * cap is the capacity of both arrays; *count receives the number of terms.
+ */
+bf_status bf_plan_terms(const bf_plan *plan, double *a, double *omega, int cap, int *count);
+
+/* The 1-D spatial taps w1[0 .. 2*radius] in FP64 (host memory), unit sum. */
+bf_status bf_plan_weights(const bf_plan *plan, double *w1, int cap, int *count);
+
+/*
+ * Fused forward filter (Algorithm 1 steps 3-5 in one kernel): the auxiliary
+ * images are generated on chip from each tile of f, filtered on chip, and
+ * combined in registers; HBM sees one read of f and one write of out.
+ *   in               : device image, H x W x C interleaved (HWC), element type dt
+ *   dt               : BF_F32 or BF_U8 (u8 is converted exactly to float)
+ *   out              : device float image, H x W x C, row stride W*C
+ *   H, W, C          : image size; H, W >= 1; 1 <= C <= 4; channels are
+ *                      filtered independently with the same plan (Section 3)
+ *   row_stride_elems : distance between rows of `in` in elements, >= W*C
+ *   q_out            : NULL, or device float H x W x C receiving the
+ *                      normaliser eq. (normalization) (unit-mass w), kept for
+ *                      the backward pass
+ *   stream           : CUDA stream
+ * Errors: BF_EINVAL (NULL pointers, sizes), BF_EUNSUPPORTED (C > 4),
+ *         BF_ECUDA (launch failure).
+ */
+bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *out,
+                     int H, int W, int C, long long row_stride_elems, float *q_out,
+                     cudaStream_t stream);
+
+/*
+ * The same filter, unfused: Algorithm 1 read literally (Section 2.2's
+ * description of the O(1) algorithm), one term at a time -- the four
+ * auxiliary images of the term are written to device memory, filtered by
+ * separate kernels, and accumulated into numerator and denominator images in
+ * device memory.  A baseline for the fused kernel; f32, one channel.
+ *   workspace : device scratch of at least bf_forward_unfused_workspace(H, W)
+ *               bytes, 256-byte aligned; contents on entry do not matter
+ */
+size_t bf_forward_unfused_workspace(int H, int W);
+bf_status bf_forward_unfused(const bf_plan *plan, const float *in, float *out, int H,
+                             int W, void *workspace, size_t workspace_bytes,
+                             cudaStream_t stream);
+
+/*
+ * Adjoint of bf_forward for one f32 single-channel image (not in the paper:
+ * the chain rule on eq. (BF), with the range-kernel derivative expanded in
+ * the same trigonometric terms, and the spatial filter's adjoint -- the
+ * filter itself in the interior, plus the clamped halo folded back onto the
+ * edge pixels).  Given L = sum_x grad_out(x) out(x):
+ *   f, out, q     : device H x W floats: the input and bf_forward's out, q_out
+ *   grad_out      : device H x W floats, dL/d out
+ *   grad_in       : device H x W floats, receives dL/df
+ *   grad_sigma_r  : NULL, or a device double receiving dL/d sigma_r with N
+ *                   held fixed (N is piecewise constant in sigma_r)
+ *   workspace     : device scratch of bf_backward_workspace(plan, H, W) bytes
+ *                   (needed only when grad_sigma_r is not NULL)
+ * The planes are recomputed from f; nothing from the forward pass other than
+ * out and q is stored.
+ */
+size_t bf_backward_workspace(const bf_plan *plan, int H, int W);
+bf_status bf_backward(const bf_plan *plan, const float *f, const float *out,
+                      const float *q, const float *grad_out, float *grad_in,
+                      double *grad_sigma_r, int H, int W, void *workspace,
+                      size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * Batched forward: many f32 single-channel images of uneven sizes, each with
+ * its own plan (own sigma_s, sigma_r and hence N), in ONE persistent launch
+ * that pulls tiles from a device work queue, largest cost first.  The launch
+ * is recorded once into a CUDA graph and replayed by bf_batch_forward.
+ *
+ * bf_batch_create  : plans[count], H[count], W[count] are host arrays; the
+ *                    batch copies what it needs (the plans may be destroyed
+ *                    afterwards).  Allocates the batch's device tables and
+ *                    queue (freed by bf_batch_destroy).  The tile shape and
+ *                    grid size come from the autotuner's cache.
+ * bf_batch_bind    : in[count], out[count] are host arrays of device
+ *                    pointers (f32, row stride W); copied to the device on
+ *                    `stream`.  Call again whenever the buffers change.
+ * bf_batch_forward : replays the graph on `stream` (capturable, allocates
+ *                    nothing).
+ * bf_batch_check   : waits for `stream` and reports the device error flag
+ *                    (non-zero if a tile-queue bound was hit).
+ */
+typedef struct bf_batch bf_batch;
+bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans, const int *H,
+                          const int *W, int count);
+bf_status bf_batch_bind(bf_batch *batch, const float *const *in, float *const *out,
+                        cudaStream_t stream);
+bf_status bf_batch_forward(bf_batch *batch, cudaStream_t stream);
+bf_status bf_batch_check(bf_batch *batch, cudaStream_t stream, int *device_error);
+void bf_batch_destroy(bf_batch *batch);
+
+/* Message for the last non-OK status returned on the calling thread. */
+const char *bf_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int bf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_H_ */

@@ -1,0 +1,8 @@
+"""GB300-native trigonometric O(1) bilateral filter (Chaudhury, Sage, Unser).
+
+The compute path is the CUDA library ``libbf.so`` (built from ``csrc/`` for
+sm_103a by ``build.build()``); this package is its thin Python binding.
+"""
+from .api import BOX, GAUSS, Plan, forward, forward_host, forward_unfused  # noqa: F401
+
+__all__ = ["Plan", "forward", "forward_host", "forward_unfused", "GAUSS", "BOX"]

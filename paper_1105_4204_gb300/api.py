@@ -1,0 +1,153 @@
+"""Python binding of libbf: argument marshalling only.
+
+Every step of the filter runs in the CUDA library; torch provides device
+memory and the current stream.  Images are torch CUDA tensors, row-major,
+H x W (one channel) or H x W x C (interleaved channels).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._lib import PlanOpts, check, lib
+
+GAUSS = 0
+BOX = 1
+_KINDS = {"gauss": GAUSS, "box": BOX}
+
+
+def _kind(kind) -> int:
+    return _KINDS[kind] if isinstance(kind, str) else int(kind)
+
+
+def _stream_ptr(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Host-side plan: degree N, folded binomial term table, spatial taps
+    (Algorithm 1 steps 1-3).  Creating it never touches the GPU."""
+
+    def __init__(self, sigma_s: float, sigma_r: float, T: float = 255.0, kind="gauss",
+                 N: int = 0, radius: int = 0, passes: int = 0):
+        self._lib = lib()
+        self._h = ctypes.c_void_p()
+        opts = PlanOpts(int(N), int(radius), int(passes))
+        check(self._lib.bf_plan_create(ctypes.byref(self._h), float(sigma_s), float(sigma_r),
+                                       float(T), _kind(kind), ctypes.byref(opts)))
+        self.sigma_s, self.sigma_r, self.T, self.kind = float(sigma_s), float(sigma_r), float(T), kind
+        n, nf, rad = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        sig = ctypes.c_double()
+        check(self._lib.bf_plan_info(self._h, ctypes.byref(n), ctypes.byref(nf),
+                                     ctypes.byref(rad), ctypes.byref(sig)))
+        self.N, self.n_terms, self.radius = n.value, nf.value, rad.value
+        self.achieved_sigma_s = sig.value
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def terms(self):
+        """(a, omega): FP64 weights and angular frequencies (rad per gray level)
+        in the kernels' accumulation order."""
+        a = np.zeros(self.n_terms, dtype=np.float64)
+        w = np.zeros(self.n_terms, dtype=np.float64)
+        cnt = ctypes.c_int()
+        check(self._lib.bf_plan_terms(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      self.n_terms, ctypes.byref(cnt)))
+        return a, w
+
+    def weights(self) -> np.ndarray:
+        """1-D spatial taps w1[-R..R] (unit sum)."""
+        w = np.zeros(2 * self.radius + 1, dtype=np.float64)
+        cnt = ctypes.c_int()
+        check(self._lib.bf_plan_weights(self._h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        len(w), ctypes.byref(cnt)))
+        return w
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                self._lib.bf_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = ctypes.c_void_p()
+
+
+def _image_args(img: torch.Tensor):
+    if not img.is_cuda:
+        raise ValueError("image must be a CUDA tensor")
+    if img.dtype == torch.float32:
+        dt = 0
+    elif img.dtype == torch.uint8:
+        dt = 1
+    else:
+        raise ValueError("image dtype must be float32 or uint8")
+    if img.dim() == 2:
+        H, W = img.shape
+        C = 1
+        if img.stride(1) != 1:
+            raise ValueError("rows must be contiguous")
+        row_stride = img.stride(0)
+    elif img.dim() == 3:
+        H, W, C = img.shape
+        if img.stride(2) != 1 or img.stride(1) != C:
+            raise ValueError("H x W x C image must have interleaved, contiguous rows")
+        row_stride = img.stride(0)
+    else:
+        raise ValueError("image must be H x W or H x W x C")
+    return dt, H, W, C, row_stride
+
+
+def forward(plan: Plan, img: torch.Tensor, return_q: bool = False, out: torch.Tensor | None = None,
+            q: torch.Tensor | None = None, stream=None):
+    """Fused forward filter; returns a float32 tensor of img's shape (and the
+    normaliser Q when ``return_q``)."""
+    dt, H, W, C, rs = _image_args(img)
+    shape = tuple(img.shape)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=img.device)
+    if return_q and q is None:
+        q = torch.empty(shape, dtype=torch.float32, device=img.device)
+    check(lib().bf_forward(plan.handle, ctypes.c_void_p(img.data_ptr()), dt,
+                           ctypes.c_void_p(out.data_ptr()), H, W, C, rs,
+                           ctypes.c_void_p(q.data_ptr() if return_q else 0), _stream_ptr(stream)))
+    return (out, q) if return_q else out
+
+
+def forward_host(plan: Plan, img_host: torch.Tensor, out_host: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """End-to-end call for host images: copy in (pinned host -> device), filter,
+    copy the result back (device -> host)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = stream if stream is not None else torch.cuda.current_stream()
+    with torch.cuda.stream(s):
+        d_in = img_host.to(dev, non_blocking=True)
+        d_out = forward(plan, d_in, stream=s)
+        if out_host is None:
+            out_host = torch.empty(tuple(img_host.shape), dtype=torch.float32, pin_memory=True)
+        out_host.copy_(d_out, non_blocking=True)
+    return out_host
+
+
+def forward_unfused(plan: Plan, img: torch.Tensor, out: torch.Tensor | None = None,
+                    workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Unfused per-term baseline (single-channel float32 only)."""
+    dt, H, W, C, rs = _image_args(img)
+    if dt != 0 or C != 1 or rs != W:
+        raise ValueError("unfused baseline takes a contiguous H x W float32 image")
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    nbytes = lib().bf_forward_unfused_workspace(H, W)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=img.device)
+    check(lib().bf_forward_unfused(plan.handle, ctypes.c_void_p(img.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), H, W,
+                                   ctypes.c_void_p(workspace.data_ptr()), nbytes,
+                                   _stream_ptr(stream)))
+    return out

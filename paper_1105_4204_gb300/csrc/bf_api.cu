@@ -1,0 +1,110 @@
+// C-ABI entry points of libbf: argument checks, kernel selection, error text.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "bf_internal.h"
+
+namespace bf {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+bf_status fail(bf_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+bf_status cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return BF_OK;
+    return fail(BF_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                              cudaGetErrorString(e) + ")");
+}
+
+int gauss_tile_radius(int R);
+int box_tile_max_r();
+cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s);
+cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img, cudaStream_t s);
+
+bool tile_supported(const bf_plan *p) {
+    if (p->kind == BF_SPATIAL_GAUSS_TRUNC) return gauss_tile_radius(p->R) > 0;
+    return p->r_box >= 1 && p->r_box <= box_tile_max_r();
+}
+
+cudaError_t launch_tile_forward(const bf_plan *p, const BfImage &img, cudaStream_t s) {
+    if (p->kind == BF_SPATIAL_GAUSS_TRUNC) return launch_tile_gauss(p, img, s);
+    return launch_tile_box(p, img, s);
+}
+
+}  // namespace bf
+
+using namespace bf;
+
+extern "C" const char *bf_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int bf_version(void) { return 100; }
+
+extern "C" bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *out,
+                                int H, int W, int C, long long row_stride_elems, float *q_out,
+                                cudaStream_t stream) {
+    if (!plan) return fail(BF_EINVAL, "bf_forward: plan is NULL");
+    if (!in || !out) return fail(BF_EINVAL, "bf_forward: in/out is NULL");
+    if (H < 1 || W < 1) return fail(BF_EINVAL, "bf_forward: H and W must be >= 1");
+    if (C < 1) return fail(BF_EINVAL, "bf_forward: C must be >= 1");
+    if (C > 4) return fail(BF_EUNSUPPORTED, "bf_forward: at most 4 channels");
+    if (dt != BF_F32 && dt != BF_U8) return fail(BF_EINVAL, "bf_forward: unknown dtype");
+    if (row_stride_elems < (long long)W * C)
+        return fail(BF_EINVAL, "bf_forward: row_stride_elems < W*C");
+    if ((long long)H * W > (1LL << 31) / 4)
+        return fail(BF_EUNSUPPORTED, "bf_forward: image too large");
+    BfImage img;
+    img.in = in;
+    img.out = out;
+    img.q_out = q_out;
+    img.in_row_stride = row_stride_elems;
+    img.H = H;
+    img.W = W;
+    img.C = C;
+    img.dtype = (int)dt;
+    img.q_scale = plan->q_scale;
+    if (!tile_supported(plan))
+        return fail(BF_EUNSUPPORTED, "bf_forward: no kernel for this spatial support");
+    return cuda_check(launch_tile_forward(plan, img, stream), "bf_forward launch");
+}
+
+// ---- not yet available ------------------------------------------------------
+
+extern "C" size_t bf_forward_unfused_workspace(int H, int W) {
+    return (size_t)H * (size_t)W * sizeof(float) * 8 + 256;
+}
+
+extern "C" bf_status bf_forward_unfused(const bf_plan *, const float *, float *, int, int,
+                                        void *, size_t, cudaStream_t) {
+    return fail(BF_EUNSUPPORTED, "bf_forward_unfused: not built yet");
+}
+
+extern "C" size_t bf_backward_workspace(const bf_plan *, int, int) { return 0; }
+
+extern "C" bf_status bf_backward(const bf_plan *, const float *, const float *, const float *,
+                                 const float *, float *, double *, int, int, void *, size_t,
+                                 cudaStream_t) {
+    return fail(BF_EUNSUPPORTED, "bf_backward: not built yet");
+}
+
+extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *, const int *,
+                                     const int *, int) {
+    if (out) *out = nullptr;
+    return fail(BF_EUNSUPPORTED, "bf_batch_create: not built yet");
+}
+extern "C" bf_status bf_batch_bind(bf_batch *, const float *const *, float *const *,
+                                   cudaStream_t) {
+    return fail(BF_EUNSUPPORTED, "bf_batch_bind: not built yet");
+}
+extern "C" bf_status bf_batch_forward(bf_batch *, cudaStream_t) {
+    return fail(BF_EUNSUPPORTED, "bf_batch_forward: not built yet");
+}
+extern "C" bf_status bf_batch_check(bf_batch *, cudaStream_t, int *) {
+    return fail(BF_EUNSUPPORTED, "bf_batch_check: not built yet");
+}
+extern "C" void bf_batch_destroy(bf_batch *) {}

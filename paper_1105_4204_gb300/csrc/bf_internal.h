@@ -1,0 +1,71 @@
+// Internal declarations shared by the host side and the kernels of libbf.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bf.h"
+
+// Largest degree the kernels accept; terms = ceil(N/2) (+1 for even N).
+#define BF_MAX_N 1024
+#define BF_MAX_TERMS 520
+// Largest 1-D support half-width of a truncated Gaussian handled by taps.
+#define BF_MAX_TAPS_R 32
+
+struct bf_plan {
+    double sigma_s = 0, sigma_r = 0, T = 0;
+    int kind = 0;          // bf_spatial_kind
+    int N = 1;             // degree
+    int passes = 3;        // box passes
+    int r_box = 0;         // box half-width
+    int R = 0;             // support half-width per axis
+    double achieved_sigma = 0;
+    // Terms in accumulation order (smallest weight first, omega = 0 last).
+    std::vector<double> a, omega;
+    std::vector<float> a32, turns32;  // FP32 weight, omega / (2 pi) in turns per gray level
+    bool has_center = false;
+    std::vector<double> w1;           // 1-D taps, 2R+1, unit sum
+    std::vector<float> w1f;
+    // Normaliser scale: the kernels filter the box unnormalised (integer
+    // weights) since the ratio P/Q does not depend on a common scale.
+    float q_scale = 1.f;
+};
+
+// Per-launch term table, passed by value as a kernel parameter (constant bank).
+struct BfTerms {
+    int n_terms;
+    float a[BF_MAX_TERMS];
+    float t[BF_MAX_TERMS];  // turns per gray level
+};
+
+struct BfTaps {
+    float w[2 * BF_MAX_TAPS_R + 1];
+};
+
+struct BfImage {
+    const void *in;
+    float *out;
+    float *q_out;
+    long long in_row_stride;  // elements
+    int H, W, C;
+    int dtype;                // 0 f32, 1 u8
+    float q_scale;
+};
+
+namespace bf {
+
+void set_error(const std::string &msg);
+bf_status fail(bf_status st, const std::string &msg);
+bf_status cuda_check(cudaError_t e, const char *what);
+
+void fill_terms(const bf_plan *p, BfTerms *t);
+void fill_taps(const bf_plan *p, BfTaps *t);
+
+// Launchers (return cudaGetLastError() of the launch).
+// Fused tile kernel for the truncated Gaussian / small-radius box.
+bool tile_supported(const bf_plan *p);
+cudaError_t launch_tile_forward(const bf_plan *p, const BfImage &img, cudaStream_t s);
+
+}  // namespace bf

@@ -1,0 +1,230 @@
+// Host-side plan: Algorithm 1 steps 1-3 in double precision.
+//
+//   step 1: gamma = pi / (2T), rho = gamma sigma_r
+//   step 2: N = (gamma sigma_r)^-2 rounded up (last row of Table 1), N >= 1
+//   step 3: the raised cosine cos^N of Section 2.3 expanded by the binomial
+//           theorem into N+1 exponentials with weights 2^-N C(N,n) and
+//           frequencies gamma (2n - N) / (rho sqrt N) = (2n - N) / (sigma_r sqrt N).
+//
+// Terms n and N-n are complex conjugates with equal weights (the c_n of
+// eq. (kernel) are real and symmetric), so each pair folds into one real
+// cosine term of weight 2 * 2^-N C(N,n) at frequency m / (sigma_r sqrt N),
+// m = N - 2n > 0; for even N the middle term n = N/2 is the constant
+// 2^-N C(N, N/2) (Section 2.3).  A term whose FP32 weight rounds to exactly 0
+// contributes exactly 0 in the kernels' FP32 arithmetic and is dropped.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "bf_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Degree rule with a relative guard so that a value that is an integer in
+// exact arithmetic is not pushed up by rounding.
+int degree_rule(double sigma_r, double T) {
+    double gamma = kPi / (2.0 * T);
+    double x = 1.0 / ((gamma * sigma_r) * (gamma * sigma_r));
+    if (!(x < 1e9)) return 1 << 30;
+    double n = std::ceil(x * (1.0 - 1e-12));
+    return n < 1.0 ? 1 : (int)n;
+}
+
+// p[n] = 2^-N C(N, n), n = 0..N, by the ratio C(N,n-1)/C(N,n) = n/(N-n+1)
+// walked outward from the middle and normalised to unit sum (the binomial
+// weights sum to 1).  Tails below the double range become 0.
+std::vector<double> binomial_weights(int N) {
+    std::vector<double> u(N + 1, 0.0);
+    int mid = N / 2;
+    u[mid] = 1.0;
+    for (int n = mid; n >= 1; --n) u[n - 1] = u[n] * (double)n / (double)(N - n + 1);
+    for (int n = mid; n < N; ++n) u[n + 1] = u[n] * (double)(N - n) / (double)(n + 1);
+    double s = 0.0;
+    for (int n = 0; n <= N; ++n) s += u[n];
+    for (int n = 0; n <= N; ++n) u[n] /= s;
+    return u;
+}
+
+}  // namespace
+
+extern "C" bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_r, double T,
+                                    bf_spatial_kind kind, const bf_plan_opts *opts) {
+    if (!out) return bf::fail(BF_EINVAL, "bf_plan_create: out is NULL");
+    *out = nullptr;
+    if (!(sigma_s > 0) || !std::isfinite(sigma_s))
+        return bf::fail(BF_EINVAL, "bf_plan_create: sigma_s must be finite and > 0");
+    if (!(sigma_r > 0) || !std::isfinite(sigma_r))
+        return bf::fail(BF_EINVAL, "bf_plan_create: sigma_r must be finite and > 0");
+    if (!(T > 0) || !std::isfinite(T))
+        return bf::fail(BF_EINVAL, "bf_plan_create: T must be finite and > 0");
+    if (kind != BF_SPATIAL_GAUSS_TRUNC && kind != BF_SPATIAL_BOX_ITER)
+        return bf::fail(BF_EINVAL, "bf_plan_create: unknown spatial kind");
+    bf_plan_opts o{};
+    if (opts) o = *opts;
+    if (o.N_override < 0 || o.radius_override < 0 || o.box_passes < 0)
+        return bf::fail(BF_EINVAL, "bf_plan_create: negative option");
+
+    bf_plan *p = new (std::nothrow) bf_plan();
+    if (!p) return bf::fail(BF_ENOMEM, "bf_plan_create: out of host memory");
+    p->sigma_s = sigma_s;
+    p->sigma_r = sigma_r;
+    p->T = T;
+    p->kind = (int)kind;
+
+    int N = o.N_override > 0 ? o.N_override : degree_rule(sigma_r, T);
+    if (N > BF_MAX_N) {
+        delete p;
+        return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: degree N = " + std::to_string(N) +
+                                             " exceeds " + std::to_string(BF_MAX_N) +
+                                             " (sigma_r too small for T)");
+    }
+    p->N = N;
+
+    // ---- spatial kernel
+    if (kind == BF_SPATIAL_GAUSS_TRUNC) {
+        int R = o.radius_override > 0 ? o.radius_override : (int)std::ceil(3.0 * sigma_s);
+        if (R > BF_MAX_TAPS_R) {
+            delete p;
+            return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: Gaussian support radius " +
+                                                 std::to_string(R) + " exceeds " +
+                                                 std::to_string(BF_MAX_TAPS_R));
+        }
+        p->R = R;
+        p->w1.resize(2 * R + 1);
+        double s = 0.0;
+        for (int i = -R; i <= R; ++i) {
+            double v = std::exp(-(double)i * i / (2.0 * sigma_s * sigma_s));
+            p->w1[i + R] = v;
+            s += v;
+        }
+        double var = 0.0;
+        for (int i = -R; i <= R; ++i) {
+            p->w1[i + R] /= s;
+            var += p->w1[i + R] * (double)i * i;
+        }
+        p->achieved_sigma = std::sqrt(var);
+        p->q_scale = 1.f;
+    } else {
+        int passes = o.box_passes > 0 ? o.box_passes : 3;
+        if (passes != 3) {
+            delete p;
+            return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: only 3 box passes are implemented");
+        }
+        int r = o.radius_override;
+        if (r <= 0) {
+            // passes boxes of width 2r+1 have variance passes ((2r+1)^2 - 1) / 12
+            double L = std::sqrt(12.0 * sigma_s * sigma_s / passes + 1.0);
+            r = (int)std::floor((L - 1.0) / 2.0 + 0.5);
+            if (r < 1) r = 1;
+        }
+        if (r > 64) {
+            delete p;
+            return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: box half-width " +
+                                                 std::to_string(r) + " exceeds 64");
+        }
+        p->passes = passes;
+        p->r_box = r;
+        p->R = passes * r;
+        // taps: convolution of `passes` boxes, exact integer counts / (2r+1)^passes
+        std::vector<double> c(1, 1.0);
+        for (int k = 0; k < passes; ++k) {
+            std::vector<double> n(c.size() + 2 * r, 0.0);
+            for (size_t i = 0; i < c.size(); ++i)
+                for (int d = 0; d <= 2 * r; ++d) n[i + d] += c[i];
+            c.swap(n);
+        }
+        double denom = std::pow(2.0 * r + 1.0, passes);
+        p->w1.resize(c.size());
+        for (size_t i = 0; i < c.size(); ++i) p->w1[i] = c[i] / denom;
+        double L = 2.0 * r + 1.0;
+        p->achieved_sigma = std::sqrt(passes * (L * L - 1.0) / 12.0);
+        // the kernels sum the 2-D box cascade without dividing: scale = L^(-2 passes)
+        p->q_scale = (float)std::pow(L, -2.0 * passes);
+    }
+    p->w1f.assign(p->w1.begin(), p->w1.end());
+
+    // ---- range kernel terms (folded conjugate pairs)
+    std::vector<double> bw = binomial_weights(N);
+    double delta = 1.0 / (sigma_r * std::sqrt((double)N));  // gamma / (rho sqrt N)
+    for (int n = 0; 2 * n < N; ++n) {  // m = N - 2n > 0, largest m (smallest weight) first
+        int m = N - 2 * n;
+        double a = 2.0 * bw[n];
+        if ((float)a == 0.0f) continue;
+        double w = m * delta;
+        p->a.push_back(a);
+        p->omega.push_back(w);
+    }
+    if (N % 2 == 0) {
+        p->a.push_back(bw[N / 2]);
+        p->omega.push_back(0.0);
+        p->has_center = true;
+    }
+    if ((int)p->a.size() > BF_MAX_TERMS) {
+        delete p;
+        return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: too many terms");
+    }
+    for (size_t k = 0; k < p->a.size(); ++k) {
+        p->a32.push_back((float)p->a[k]);
+        p->turns32.push_back((float)(p->omega[k] / (2.0 * kPi)));
+    }
+    *out = p;
+    return BF_OK;
+}
+
+extern "C" void bf_plan_destroy(bf_plan *plan) { delete plan; }
+
+extern "C" bf_status bf_plan_info(const bf_plan *p, int *N, int *n_freq, int *radius,
+                                  double *achieved_sigma_s) {
+    if (!p) return bf::fail(BF_EINVAL, "bf_plan_info: plan is NULL");
+    if (N) *N = p->N;
+    if (n_freq) *n_freq = (int)p->a.size();
+    if (radius) *radius = p->R;
+    if (achieved_sigma_s) *achieved_sigma_s = p->achieved_sigma;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_plan_terms(const bf_plan *p, double *a, double *omega, int cap,
+                                   int *count) {
+    if (!p) return bf::fail(BF_EINVAL, "bf_plan_terms: plan is NULL");
+    int n = (int)p->a.size();
+    if (count) *count = n;
+    if (a || omega) {
+        if (cap < n) return bf::fail(BF_EINVAL, "bf_plan_terms: cap too small");
+        for (int k = 0; k < n; ++k) {
+            if (a) a[k] = p->a[k];
+            if (omega) omega[k] = p->omega[k];
+        }
+    }
+    return BF_OK;
+}
+
+extern "C" bf_status bf_plan_weights(const bf_plan *p, double *w1, int cap, int *count) {
+    if (!p) return bf::fail(BF_EINVAL, "bf_plan_weights: plan is NULL");
+    int n = (int)p->w1.size();
+    if (count) *count = n;
+    if (w1) {
+        if (cap < n) return bf::fail(BF_EINVAL, "bf_plan_weights: cap too small");
+        std::memcpy(w1, p->w1.data(), sizeof(double) * n);
+    }
+    return BF_OK;
+}
+
+namespace bf {
+
+void fill_terms(const bf_plan *p, BfTerms *t) {
+    t->n_terms = (int)p->a32.size();
+    for (int k = 0; k < t->n_terms; ++k) {
+        t->a[k] = p->a32[k];
+        t->t[k] = p->turns32[k];
+    }
+}
+
+void fill_taps(const bf_plan *p, BfTaps *t) {
+    std::memset(t, 0, sizeof(*t));
+    int n = (int)p->w1f.size();
+    for (int k = 0; k < n && k < 2 * BF_MAX_TAPS_R + 1; ++k) t->w[k] = p->w1f[k];
+}
+
+}  // namespace bf

@@ -1,0 +1,26 @@
+// Instantiations of the fused tile kernel for the 3-pass iterated box.
+#include "bf_tile.cuh"
+
+namespace bf {
+
+int box_tile_max_r() { return 8; }
+
+cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t s) {
+    TileParams prm;
+    prm.img = img0;
+    fill_terms(pl, &prm.terms);
+    for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) prm.taps.w[k] = 0.f;
+    switch (pl->r_box) {
+        case 1: return launch_tile<1, 1, 32, 64, 16>(prm, s);
+        case 2: return launch_tile<1, 2, 32, 64, 16>(prm, s);
+        case 3: return launch_tile<1, 3, 32, 64, 16>(prm, s);
+        case 4: return launch_tile<1, 4, 32, 64, 16>(prm, s);
+        case 5: return launch_tile<1, 5, 32, 64, 16>(prm, s);
+        case 6: return launch_tile<1, 6, 32, 64, 16>(prm, s);
+        case 7: return launch_tile<1, 7, 32, 64, 16>(prm, s);
+        case 8: return launch_tile<1, 8, 32, 64, 16>(prm, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bf

@@ -1,0 +1,145 @@
+"""Host-side tests of libbf: it builds, loads, exports what include/bf.h
+declares, and its plan (pure host code) follows the paper.  No GPU needed."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bf.h")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def bf():
+    from paper_1105_4204_gb300 import build
+    build.build()
+    import paper_1105_4204_gb300 as pkg
+    from paper_1105_4204_gb300 import _lib
+    _lib.lib()
+    return pkg
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(bf_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ["bf_plan_create", "bf_plan_destroy", "bf_plan_info", "bf_forward",
+                     "bf_backward", "bf_batch_forward", "bf_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(bf):
+    from paper_1105_4204_gb300 import _lib
+    l = ctypes.CDLL(_lib.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(l, n)]
+    assert not missing, missing
+
+
+def test_plan_degree_rule_matches_table1(bf):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table1_degree.txt"))
+            if l.strip() and not l.startswith("#")]
+    for sigma, _n0, n_rule in rows:
+        assert bf.Plan(3.0, float(sigma), 255.0).N == int(n_rule)
+
+
+@pytest.mark.parametrize("sr,N", [(10.0, 264), (15.0, 118), (20.0, 66), (25.0, 43), (30.0, 30),
+                                  (50.0, 11), (60.0, 8)])
+def test_plan_degree_at_workload_sigmas(bf, sr, N):
+    assert bf.Plan(3.0, sr).N == N
+
+
+@pytest.mark.parametrize("sr", [10.0, 20.0, 25.0, 30.0, 50.0, 200.0])
+def test_plan_terms_reproduce_raised_cosine(bf, sr):
+    # Section 2.3: cos^N(x) = sum_n 2^-N C(N,n) exp(j (2n-N) x); the plan folds
+    # conjugate pairs into real cosines.  Check against the direct power.
+    p = bf.Plan(3.0, sr)
+    a, w = p.terms()
+    s = np.linspace(-255.0, 255.0, 2001)
+    phi = np.sum(a[:, None] * np.cos(w[:, None] * s[None, :]), axis=0)
+    ref = np.cos(s / (sr * math.sqrt(p.N))) ** p.N
+    # terms dropped because their FP32 weight is 0 are below 1e-38 each
+    np.testing.assert_allclose(phi, ref, atol=1e-12)
+    # accumulation order: nondecreasing weight, constant term last for even N
+    assert np.all(np.diff(a[:-1] if p.N % 2 == 0 else a) >= 0)
+    if p.N % 2 == 0:
+        assert w[-1] == 0.0
+    assert p.n_terms == len(a)
+
+
+def test_plan_terms_exact_binomials_small_n(bf):
+    for N in range(1, 14):
+        p = bf.Plan(3.0, 30.0, N=N)
+        a, w = p.terms()
+        k = 1.0 / (30.0 * math.sqrt(N))
+        for n in range((N + 1) // 2):
+            m = N - 2 * n
+            idx = int(np.argmin(np.abs(w - m * k)))
+            assert w[idx] == pytest.approx(m * k, rel=1e-15)
+            assert a[idx] == pytest.approx(2 * math.comb(N, n) / 2.0 ** N, rel=1e-14)
+        if N % 2 == 0:
+            assert a[-1] == pytest.approx(math.comb(N, N // 2) / 2.0 ** N, rel=1e-14)
+
+
+def test_plan_zero_weights_dropped_at_large_degree(bf):
+    p = bf.Plan(6.0, 10.0)  # N = 264
+    a, _ = p.terms()
+    assert p.N == 264
+    # 132 folded frequencies + constant; 50 of the 265 binomial weights (25
+    # conjugate pairs) round to 0 in FP32
+    assert p.n_terms == 133 - 25
+    assert np.all(a.astype(np.float32) > 0)
+
+
+def test_plan_spatial_weights(bf):
+    g = bf.Plan(3.0, 30.0, kind="gauss")
+    w = g.weights()
+    assert g.radius == 9 and len(w) == 19
+    k = np.arange(-9, 10)
+    np.testing.assert_allclose(w / w[9], np.exp(-k * k / 18.0), rtol=1e-14)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    for ss, r in [(2.0, 2), (8.0, 8), (32.0, 32)]:
+        b = bf.Plan(ss, 20.0, kind="box")
+        assert b.radius == 3 * r
+        ref = np.ones(1)
+        for _ in range(3):
+            ref = np.convolve(ref, np.ones(2 * r + 1) / (2 * r + 1))
+        np.testing.assert_allclose(b.weights(), ref, atol=1e-15)
+        assert b.achieved_sigma_s == pytest.approx(math.sqrt((2 * r + 1) ** 2 - 1) / 2, rel=1e-12)
+
+
+def test_plan_rejects_bad_arguments(bf):
+    from paper_1105_4204_gb300._lib import BfError
+    for args in [(0.0, 30.0), (3.0, 0.0), (3.0, -1.0), (float("nan"), 30.0)]:
+        with pytest.raises(BfError) as e:
+            bf.Plan(*args)
+        assert e.value.status == 1  # BF_EINVAL
+    with pytest.raises(BfError) as e:
+        bf.Plan(3.0, 2.0)  # N = 4121 > 1024
+    assert e.value.status == 2  # BF_EUNSUPPORTED
+    with pytest.raises(BfError) as e:
+        bf.Plan(3.0, 20.0, kind="box", passes=2)
+    assert e.value.status == 2
+
+
+def test_forward_rejects_bad_arguments_without_touching_a_gpu(bf):
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    p = bf.Plan(3.0, 30.0)
+    null = ctypes.c_void_p(0)
+    st = l.bf_forward(p.handle, null, 0, null, 16, 16, 1, 16, null, null)
+    assert st == 1 and b"NULL" in l.bf_last_error()
+    fake = ctypes.c_void_p(0x1000)
+    assert l.bf_forward(p.handle, fake, 0, fake, 0, 16, 1, 16, null, null) == 1
+    assert l.bf_forward(p.handle, fake, 0, fake, 16, 16, 1, 8, null, null) == 1   # stride < W
+    assert l.bf_forward(p.handle, fake, 0, fake, 16, 16, 5, 80, null, null) == 2  # C > 4
+    assert l.bf_forward(p.handle, fake, 7, fake, 16, 16, 1, 16, null, null) == 1  # dtype
+    assert l.bf_forward(None, fake, 0, fake, 16, 16, 1, 16, null, null) == 1

@@ -1,0 +1,156 @@
+"""GPU parity of the fused forward kernels against the FP64 oracle.
+
+The bar (from the task's accuracy target): max |GPU - oracle| <= 0.05 gray
+levels on the 0..255 scale, element by element.  Sizes span several tiles and
+ragged tails; full-size workloads are checked on sampled pixels (every border
+pixel plus seeded interior pixels), computed one by one by the oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 0.05
+
+
+@pytest.fixture(scope="module")
+def bf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_4204_gb300 import build
+    build.build()
+    import paper_1105_4204_gb300 as pkg
+    return pkg
+
+
+def _run(bf, img_np, plan, return_q=False):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(img_np)).cuda()
+    res = bf.forward(plan, t, return_q=return_q)
+    torch.cuda.synchronize()
+    if return_q:
+        return res[0].cpu().numpy(), res[1].cpu().numpy()
+    return res.cpu().numpy()
+
+
+def _oracle_full(oracle, img, plan, return_q=False):
+    return oracle.bf_brute(img.astype(np.float64), sigma_r=plan.sigma_r, T=plan.T,
+                           w1=plan_w1(oracle, plan), N=plan.N, return_q=return_q)
+
+
+def plan_w1(oracle, plan):
+    # the oracle builds its own taps from the same spatial parameters
+    if plan.kind == "gauss":
+        return oracle.spatial_w1("gauss", plan.sigma_s, radius=plan.radius)
+    return oracle.spatial_w1("box", plan.sigma_s, radius=plan.radius // 3, passes=3)
+
+
+def test_config1_full_image(bf, oracle):
+    # 256 x 256 rectangles + noise 10, Gaussian sigma_s = 3 (R = 9), sigma_r = 30 (N = 30)
+    img = synth.rectangles(256, 256, n_rect=12, noise=10.0, seed=0)
+    plan = bf.Plan(3.0, 30.0, 255.0, kind="gauss")
+    assert plan.N == 30 and plan.radius == 9
+    out, q = _run(bf, img, plan, return_q=True)
+    ref, qref = _oracle_full(oracle, img, plan, return_q=True)
+    err = np.abs(out - ref).max()
+    print("config1 max abs err %.3e" % err)
+    assert err <= TOL
+    np.testing.assert_allclose(q, qref, rtol=2e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 17), (5, 3), (37, 53), (70, 131), (97, 64)])
+@pytest.mark.parametrize("sigma_s,sigma_r", [(1.0, 30.0), (3.0, 20.0), (2.0, 200.0)])
+def test_gauss_ragged_sizes(bf, oracle, H, W, sigma_s, sigma_r):
+    img = synth.rectangles(H, W, n_rect=4, noise=10.0, seed=H * 1000 + W)
+    plan = bf.Plan(sigma_s, sigma_r, kind="gauss")
+    out = _run(bf, img, plan)
+    ref = _oracle_full(oracle, img, plan)
+    assert np.abs(out - ref).max() <= TOL
+
+
+@pytest.mark.parametrize("R", [1, 3, 4, 5, 9, 12, 16, 18, 24])
+def test_gauss_every_radius(bf, oracle, R):
+    img = synth.rectangles(45, 77, n_rect=6, noise=10.0, seed=R)
+    plan = bf.Plan(max(R / 3.0, 0.5), 25.0, kind="gauss", radius=R)
+    out = _run(bf, img, plan)
+    ref = _oracle_full(oracle, img, plan)
+    assert np.abs(out - ref).max() <= TOL
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_box_every_radius(bf, oracle, r):
+    img = synth.smooth_field(61, 90, noise=5.0, seed=r)
+    plan = bf.Plan(float(r), 20.0, kind="box", radius=r)
+    assert plan.N == 66
+    out = _run(bf, img, plan)
+    ref = _oracle_full(oracle, img, plan)
+    assert np.abs(out - ref).max() <= TOL
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 7, 11, 30, 66, 118, 264])
+def test_degrees(bf, oracle, N):
+    # sigma_r chosen so that N meets the validity bound of Section 2.5,
+    # T / (sigma_r sqrt N) <= pi / 2 (below it phi goes negative and Q can vanish)
+    sigma_r = 1.001 * 2 * 255.0 / (np.pi * np.sqrt(N))
+    img = synth.rectangles(50, 70, n_rect=6, noise=8.0, seed=N)
+    plan = bf.Plan(2.0, sigma_r, kind="gauss", N=N)
+    out = _run(bf, img, plan)
+    ref = _oracle_full(oracle, img, plan)
+    assert np.abs(out - ref).max() <= TOL
+
+
+def test_constant_image(bf):
+    img = np.full((40, 90), 123.0, dtype=np.float32)
+    for kind, ss in [("gauss", 3.0), ("box", 4.0)]:
+        out = _run(bf, img, bf.Plan(ss, 20.0, kind=kind))
+        assert np.abs(out - 123.0).max() <= 1e-3
+
+
+def test_u8_interleaved_channels(bf, oracle):
+    img = synth.rect_disk_u8(48, 67, C=3, n_shapes=10, noise=8.0, seed=5)
+    plan = bf.Plan(2.0, 50.0, kind="gauss")
+    out = _run(bf, img, plan)
+    assert out.shape == img.shape and out.dtype == np.float32
+    ref = oracle.bf_brute(img.astype(np.float64), sigma_r=50.0, w1=plan_w1(oracle, plan), N=plan.N)
+    assert np.abs(out - ref).max() <= TOL
+    # u8 and the same values as f32 give identical results
+    out_f = _run(bf, img.astype(np.float32), plan)
+    np.testing.assert_array_equal(out, out_f)
+
+
+def test_row_stride_and_channels_f32(bf, oracle):
+    import torch
+    base = synth.rect_disk_u8(33, 40, C=2, n_shapes=6, seed=9).astype(np.float32)
+    padded = np.zeros((33, 52, 2), dtype=np.float32)
+    padded[:, :40] = base
+    t = torch.from_numpy(padded).cuda()[:, :40]
+    plan = bf.Plan(1.5, 30.0, kind="box")
+    out = bf.forward(plan, t).cpu().numpy()
+    ref = oracle.bf_brute(base.astype(np.float64), sigma_r=30.0, w1=plan_w1(oracle, plan), N=plan.N)
+    assert np.abs(out - ref).max() <= TOL
+
+
+def test_outlier_pixels(bf, oracle):
+    # isolated outliers make Q small (close to w(0)); the FP32 path must stay in tolerance
+    rng = np.random.default_rng(4)
+    img = np.full((64, 64), 20.0, dtype=np.float32)
+    pts = rng.integers(0, 64, size=(12, 2))
+    img[pts[:, 0], pts[:, 1]] = 240.0
+    for kind, ss, sr in [("gauss", 3.0, 30.0), ("box", 2.0, 20.0), ("gauss", 2.0, 15.0)]:
+        plan = bf.Plan(ss, sr, kind=kind)
+        out = _run(bf, img, plan)
+        ref = _oracle_full(oracle, img, plan)
+        err = np.abs(out - ref).max()
+        print(kind, ss, sr, "outlier max abs err %.3e" % err)
+        assert err <= TOL
+
+
+def test_repeat_is_deterministic(bf):
+    img = synth.rectangles(100, 120, seed=1)
+    plan = bf.Plan(3.0, 30.0)
+    a = _run(bf, img, plan)
+    b = _run(bf, img, plan)
+    np.testing.assert_array_equal(a, b)
