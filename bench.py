@@ -1,0 +1,404 @@
+"""Benchmark of the trigonometric O(1) bilateral filter on GB300.
+
+Workload (one step): the 2048 x 2048 FP32 image of the plain-forward
+benchmark configuration (seeded smooth field of 20 random 2-D sinusoids plus
+piecewise-constant regions plus N(0, 5^2) noise, in [0, 255]), filtered with
+the 3-pass iterated box at sigma_s = 2, 8 and 32 (r = 2, 8, 32) and
+sigma_r = 20 (N = 66), T = 255: three forward calls per step.
+
+Metric: Mpixel/s of filtered output (whole job over all ranks).  The JSON line
+also carries the roofline of the dominant kernel, the FP64 oracle's CPU rate,
+an end-to-end rate through the public API with host buffers, and (as
+extras) the unfused per-term baseline, the accuracy against the oracle, and
+the other workloads' rates where their paths exist.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the only reference there is:
+the paper ships no code) on a bounded pixel sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s fwd and fwd+bwd vs plain forward; % of FP32/HBM roofline; max abs err"
+UNIT = "Mpixel/s"
+H = W = 2048
+SIGMA_S = [2.0, 8.0, 32.0]
+SIGMA_R = 20.0
+T_RANGE = 255.0
+WORKLOAD = ("2048x2048 f32 smooth field (20 sinusoids + regions + noise 5, seed 0), "
+            "3-pass box sigma_s in {2, 8, 32} (r = 2, 8, 32), sigma_r = 20 (N = 66), T = 255, "
+            "clamp-to-edge; 3 forwards per step")
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def _load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+# ------------------------------------------------------------------ helpers
+
+def box_instr_per_px(n_nonzero: int, has_center: bool) -> float:
+    """Algorithmic FP32-pipe instructions per output pixel for the 3-pass box:
+    per nonzero frequency 3 (phase, f cos, f sin) + 4 planes x 12 (3 passes x
+    2 axes x add/sub) + 6 (combine); the constant term 12 + 3; the divide 4."""
+    return 57.0 * n_nonzero + (15.0 if has_center else 0.0) + 4.0
+
+
+def gauss_instr_per_px(n_nonzero: int, has_center: bool, R: int) -> float:
+    fs = 2.0 * (2 * R + 1)
+    return (9.0 + 4.0 * fs) * n_nonzero + ((fs + 3.0) if has_center else 0.0) + 4.0
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            self.path = "/tmp/bf_clocks_%d_%d.csv" % (os.getpid(), self.gpu)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names[1:], parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": float(max(power)) if power else None}
+
+
+# -------------------------------------------------------------- CPU baseline
+
+def oracle_rate(step_seconds_budget: float, seed: int = 0):
+    """FP64 brute-force oracle on a pixel sample of each sigma_s; returns
+    (Mpixel/s extrapolated to the workload, cores, sample description)."""
+    import oracle
+    import synth
+    img = synth.smooth_field(H, W, noise=5.0, seed=seed).astype(np.float64)
+    rng = np.random.default_rng(seed + 1)
+    cores = oracle.num_threads()
+    total_s_per_px = 0.0
+    desc = []
+    per = step_seconds_budget / len(SIGMA_S)
+    for ss in SIGMA_S:
+        w1 = oracle.spatial_w1("box", ss)
+        support = len(w1) ** 2
+        # size the sample from an estimate of ~30 ns per kernel tap per core
+        n = int(max(64, min(H * W, per * cores / (support * 30e-9))))
+        idx = rng.choice(H * W, size=n, replace=False)
+        t0 = time.perf_counter()
+        oracle.bf_brute_at(img, idx, sigma_r=SIGMA_R, T=T_RANGE, w1=w1)
+        dt = time.perf_counter() - t0
+        total_s_per_px += dt / n
+        desc.append("sigma_s=%g: %d px in %.2f s" % (ss, n, dt))
+    mpx = len(SIGMA_S) / total_s_per_px / 1e6
+    return mpx, cores, "; ".join(desc) + " (brute force of eq. (BF), extrapolated per pixel)"
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each step a bounded sample; the whole run stays near two minutes of CPU time
+    budget = min(6.0, 120.0 / max(1, args.steps + args.warmup))
+    vals = []
+    cores, sample = None, None
+    for i in range(args.warmup + args.steps):
+        v, cores, sample = oracle_rate(budget, seed=0)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    ms = len(SIGMA_S) * H * W / (value * 1e6) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "FP64 CPU brute-force oracle (the "
+                       "paper ships no code); each step times a bounded pixel sample"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1105_4204_gb300 as bf
+    import synth
+    from paper_1105_4204_gb300 import build as _build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+
+    peaks, peak_kind = _load_peaks()
+    img_np = synth.smooth_field(H, W, noise=5.0, seed=rank)
+    img = torch.from_numpy(img_np).to(dev)
+    plans = [bf.Plan(ss, SIGMA_R, T_RANGE, kind="box") for ss in SIGMA_S]
+    outs = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in SIGMA_S]
+    from paper_1105_4204_gb300._lib import lib as _l
+    fused = [True for _ in plans]  # bf_forward picks the tile or the streaming kernels
+    ws = None
+    stream = torch.cuda.current_stream()
+
+    def one(i):
+        if fused[i]:
+            bf.forward(plans[i], img, out=outs[i])
+        else:
+            bf.forward_unfused(plans[i], img, out=outs[i], workspace=ws)
+
+    def n_launches(p):
+        r = p.radius // 3
+        if r <= 8:
+            return 1
+        return 2 * p.n_terms + 1  # two sweeps per term + final
+
+    launches_per_call = [n_launches(p) for p in plans]
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        for i in range(len(plans)):
+            one(i)
+    torch.cuda.synchronize()
+
+    # per-call CUDA events on the launching stream; L2 flushed before every step
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in plans] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        for i in range(len(plans)):
+            ev[k][i][0].record(stream)
+            one(i)
+            ev[k][i][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    per_call = np.array([[ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(len(plans))]
+                         for k in range(args.steps)])  # ms
+    step_ms = float(per_call.sum(axis=1).mean())
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    px_per_step = len(plans) * H * W * world
+    value = px_per_step / (step_ms * 1e-3) / 1e6
+
+    # ---- roofline of the dominant kernel (largest share of step time)
+    call_ms = per_call.mean(axis=0)
+    dom = int(np.argmax(call_ms))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_instr = sm_count * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", SM_MAX_MHZ) * 1e6
+    rl = []
+    for i, p in enumerate(plans):
+        a, w = p.terms()
+        nz = int(np.sum(w > 0))
+        instr = box_instr_per_px(nz, bool(np.any(w == 0))) * H * W
+        ach = instr / (call_ms[i] * 1e-3)
+        rl.append({"sigma_s": SIGMA_S[i], "r": p.radius // 3,
+                   "kernel": "bf_tile_fwd" if p.radius // 3 <= 8
+                   else "streaming sweeps (lr_vert + lr_horz per term, lr_final)",
+                   "ms": float(call_ms[i]), "achieved_tinstr_s": ach / 1e12,
+                   "frac": ach / peak_instr})
+    roofline = {"bound": "alu", "achieved": rl[dom]["achieved_tinstr_s"],
+                "peak": peak_instr / 1e12, "unit": "T FP32-pipe instr/s",
+                "frac": rl[dom]["frac"], "traffic": None,
+                "kernel": rl[dom]["kernel"], "per_call": rl,
+                "peak_note": "SMs x 128 FP32 lanes x max SM clock %.0f MHz (%s)" % (
+                    peaks.get("sm_max_mhz", SM_MAX_MHZ), peak_kind)}
+
+    # ---- end to end through the public API with host buffers
+    host_in = torch.from_numpy(img_np).pin_memory()
+    host_out = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in plans]
+    e2e_steps = max(3, min(args.steps, 20))
+
+    def e2e_step():
+        d_in = host_in.to(dev, non_blocking=True)
+        for i in range(len(plans)):
+            if fused[i]:
+                o = bf.forward(plans[i], d_in, out=outs[i])
+            else:
+                o = bf.forward_unfused(plans[i], d_in, out=outs[i], workspace=ws)
+            host_out[i].copy_(o, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": px_per_step / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": H * W * 4, "d2h_bytes_per_step": len(plans) * H * W * 4}
+
+    extras = {}
+    if rank == 0:
+        # ---- accuracy on sampled pixels (outside the timed region)
+        import oracle
+        idx = synth.sample_indices(H, W, 1024, seed=3)
+        errs = {}
+        for i, p in enumerate(plans):
+            one(i)
+            torch.cuda.synchronize()
+            got = outs[i].cpu().numpy().ravel()[idx]
+            ref = oracle.bf_brute_at(img_np.astype(np.float64), idx, sigma_r=SIGMA_R, T=T_RANGE,
+                                     w1=oracle.spatial_w1("box", SIGMA_S[i]))
+            errs["sigma_s=%g" % SIGMA_S[i]] = float(np.abs(got - ref).max())
+        extras["max_abs_err_vs_oracle"] = errs
+        extras["max_abs_err_sample"] = "%d pixels (all borders + 1024 seeded)" % len(idx)
+        # ---- unfused baseline on the same workload (fused vs per-term materialised)
+        if ws is None:
+            ws = torch.empty(_l().bf_forward_unfused_workspace(H, W), dtype=torch.uint8,
+                             device=dev)
+        uf_ms = []
+        for i, p in enumerate(plans):
+            for _ in range(2):
+                bf.forward_unfused(p, img, out=outs[i], workspace=ws)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(3):
+                bf.forward_unfused(p, img, out=outs[i], workspace=ws)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            uf_ms.append(a0.elapsed_time(a1) / 3)
+        extras["unfused_ms_per_call"] = {"sigma_s=%g" % s: m for s, m in zip(SIGMA_S, uf_ms)}
+        extras["fused_ms_per_call"] = {"sigma_s=%g" % s: float(m) for s, m in zip(SIGMA_S, call_ms)}
+        extras["wall_s_timed_region"] = t_wall
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_rate(float(os.environ.get("BF_CPU_SECONDS", "15")))
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "l2": "flushed before every step "
+                           "(256 MiB write, outside the per-call events)",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "kernels": ["fused" if f else "unfused" for f in fused]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(args.steps * sum(launches_per_call)),
+                "clocks": clk, "extras": extras}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

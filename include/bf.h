@@ -80,7 +80,7 @@ typedef struct bf_plan bf_plan;
  *   kind     : spatial kernel
  *   opts     : NULL for defaults
  * Errors: BF_EINVAL for non-positive or non-finite sigma/T or a NULL out;
- *         BF_EUNSUPPORTED for N > 4096, a support radius above the kernels'
+ *         BF_EUNSUPPORTED for N > 1024, a support radius above the kernels'
  *         limits, or box_passes other than 3.
  */
 bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_r, double T,
@@ -128,12 +128,23 @@ bf_status bf_plan_weights(const bf_plan *plan, double *w1, int cap, int *count);
  *                      normaliser eq. (normalization) (unit-mass w), kept for
  *                      the backward pass
  *   stream           : CUDA stream
+ * Kernels: the fused tile kernel serves the truncated Gaussian (R <= 24) and
+ * the box with r <= 8.  For the box with 8 < r <= 64 the support does not fit
+ * on chip and the filter runs as streaming sweeps (vertical, then horizontal
+ * over a transposed copy) through a scratch buffer of 8 * H * W floats that
+ * the library allocates on the current device the first time it is needed,
+ * and keeps for reuse until bf_release_scratch().  The first such call on a
+ * device must therefore not happen during stream capture.
  * Errors: BF_EINVAL (NULL pointers, sizes), BF_EUNSUPPORTED (C > 4),
- *         BF_ECUDA (launch failure).
+ *         BF_ENOMEM (scratch allocation), BF_ECUDA (launch failure).
  */
 bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *out,
                      int H, int W, int C, long long row_stride_elems, float *q_out,
                      cudaStream_t stream);
+
+/* Frees the scratch buffers bf_forward allocated (all devices).  Call only
+ * when no work that uses them is in flight. */
+void bf_release_scratch(void);
 
 /*
  * The same filter, unfused: Algorithm 1 read literally (Section 2.2's

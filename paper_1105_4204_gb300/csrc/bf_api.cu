@@ -1,6 +1,7 @@
 // C-ABI entry points of libbf: argument checks, kernel selection, error text.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "bf_internal.h"
@@ -26,6 +27,39 @@ int gauss_tile_radius(int R);
 int box_tile_max_r();
 cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s);
 cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img, cudaStream_t s);
+
+size_t large_workspace(int H, int W);
+cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cudaStream_t s);
+
+// Library-owned scratch for the large-radius box path, one buffer per device,
+// grown on demand and reused until bf_release_scratch().
+static std::mutex g_scratch_mu;
+static void *g_scratch[64];
+static size_t g_scratch_bytes[64];
+
+static cudaError_t get_scratch(size_t bytes, void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (g_scratch_bytes[dev] < bytes) {
+        if (g_scratch[dev]) {
+            e = cudaFree(g_scratch[dev]);  // synchronises with work still using it
+            g_scratch[dev] = nullptr;
+            g_scratch_bytes[dev] = 0;
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaMalloc(&g_scratch[dev], bytes);
+        if (e != cudaSuccess) {
+            g_scratch[dev] = nullptr;
+            return e;
+        }
+        g_scratch_bytes[dev] = bytes;
+    }
+    *out = g_scratch[dev];
+    return cudaSuccess;
+}
 
 bool tile_supported(const bf_plan *p) {
     if (p->kind == BF_SPATIAL_GAUSS_TRUNC) return gauss_tile_radius(p->R) > 0;
@@ -68,21 +102,64 @@ extern "C" bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt
     img.C = C;
     img.dtype = (int)dt;
     img.q_scale = plan->q_scale;
-    if (!tile_supported(plan))
-        return fail(BF_EUNSUPPORTED, "bf_forward: no kernel for this spatial support");
-    return cuda_check(launch_tile_forward(plan, img, stream), "bf_forward launch");
+    if (tile_supported(plan))
+        return cuda_check(launch_tile_forward(plan, img, stream), "bf_forward launch");
+    if (plan->kind == BF_SPATIAL_BOX_ITER) {
+        void *ws = nullptr;
+        cudaError_t e = get_scratch(large_workspace(H, W), &ws);
+        if (e == cudaErrorMemoryAllocation)
+            return fail(BF_ENOMEM, "bf_forward: cannot allocate the large-radius scratch");
+        if (e != cudaSuccess) return cuda_check(e, "bf_forward scratch");
+        return cuda_check(launch_large_box(plan, img, ws, stream), "bf_forward launch");
+    }
+    return fail(BF_EUNSUPPORTED, "bf_forward: no kernel for this spatial support");
+}
+
+extern "C" void bf_release_scratch(void) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < 64; ++d) {
+        if (g_scratch[d]) {
+            cudaSetDevice(d);
+            cudaFree(g_scratch[d]);
+            g_scratch[d] = nullptr;
+            g_scratch_bytes[d] = 0;
+        }
+    }
+    cudaSetDevice(cur);
+}
+
+// ---- unfused baseline ---------------------------------------------------------
+
+namespace bf {
+size_t unfused_workspace(int H, int W);
+cudaError_t launch_unfused(const bf_plan *pl, const float *in, float *out, int H, int W,
+                           void *ws, cudaStream_t s);
+}  // namespace bf
+
+extern "C" size_t bf_forward_unfused_workspace(int H, int W) {
+    if (H < 1 || W < 1) return 0;
+    return unfused_workspace(H, W);
+}
+
+extern "C" bf_status bf_forward_unfused(const bf_plan *plan, const float *in, float *out, int H,
+                                        int W, void *workspace, size_t workspace_bytes,
+                                        cudaStream_t stream) {
+    if (!plan) return fail(BF_EINVAL, "bf_forward_unfused: plan is NULL");
+    if (!in || !out || !workspace)
+        return fail(BF_EINVAL, "bf_forward_unfused: in/out/workspace is NULL");
+    if (H < 1 || W < 1) return fail(BF_EINVAL, "bf_forward_unfused: H and W must be >= 1");
+    if ((long long)H * W > (1LL << 31) / 16)
+        return fail(BF_EUNSUPPORTED, "bf_forward_unfused: image too large");
+    if (workspace_bytes < unfused_workspace(H, W))
+        return fail(BF_EINVAL, "bf_forward_unfused: workspace too small (need " +
+                                   std::to_string(unfused_workspace(H, W)) + " bytes)");
+    return cuda_check(launch_unfused(plan, in, out, H, W, workspace, stream),
+                      "bf_forward_unfused launch");
 }
 
 // ---- not yet available ------------------------------------------------------
-
-extern "C" size_t bf_forward_unfused_workspace(int H, int W) {
-    return (size_t)H * (size_t)W * sizeof(float) * 8 + 256;
-}
-
-extern "C" bf_status bf_forward_unfused(const bf_plan *, const float *, float *, int, int,
-                                        void *, size_t, cudaStream_t) {
-    return fail(BF_EUNSUPPORTED, "bf_forward_unfused: not built yet");
-}
 
 extern "C" size_t bf_backward_workspace(const bf_plan *, int, int) { return 0; }
 

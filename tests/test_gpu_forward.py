@@ -154,3 +154,44 @@ def test_repeat_is_deterministic(bf):
     a = _run(bf, img, plan)
     b = _run(bf, img, plan)
     np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("r,H,W", [(9, 70, 90), (12, 64, 130), (16, 101, 77), (32, 150, 170),
+                                   (32, 20, 300)])
+def test_box_large_radius(bf, oracle, r, H, W):
+    # streaming sweeps through the library scratch buffer (support 3r > 24)
+    img = synth.smooth_field(H, W, noise=5.0, seed=r + H)
+    plan = bf.Plan(float(r), 20.0, kind="box", radius=r)
+    out, q = _run(bf, img, plan, return_q=True)
+    ref, qref = _oracle_full(oracle, img, plan, return_q=True)
+    err = np.abs(out - ref).max()
+    print("box r=%d %dx%d max abs err %.3e" % (r, H, W, err))
+    assert err <= TOL
+    np.testing.assert_allclose(q, qref, rtol=2e-4, atol=1e-7)
+
+
+def test_box_large_radius_u8_channels(bf, oracle):
+    img = synth.rect_disk_u8(60, 75, C=3, n_shapes=8, seed=12)
+    plan = bf.Plan(12.0, 30.0, kind="box")
+    assert plan.radius // 3 == 12
+    out = _run(bf, img, plan)
+    ref = oracle.bf_brute(img.astype(np.float64), sigma_r=30.0, w1=plan_w1(oracle, plan), N=plan.N)
+    assert np.abs(out - ref).max() <= TOL
+
+
+@pytest.mark.parametrize("sigma_s", [2.0, 8.0, 32.0])
+def test_config2_full_size_sampled(bf, oracle, sigma_s):
+    # 2048 x 2048 smooth field, 3-pass box, sigma_r = 20 (N = 66): the benchmark
+    # workload, checked on every border pixel plus seeded interior pixels
+    img = synth.smooth_field(2048, 2048, noise=5.0, seed=0)
+    plan = bf.Plan(sigma_s, 20.0, kind="box")
+    out = _run(bf, img, plan)
+    n_int = 4096 if sigma_s < 32 else 1024
+    idx = synth.sample_indices(2048, 2048, n_int, seed=5)
+    if sigma_s >= 32:
+        idx = idx[::4]  # keep the oracle's share of the test within seconds
+    ref = oracle.bf_brute_at(img.astype(np.float64), idx, sigma_r=20.0, w1=plan_w1(oracle, plan),
+                             N=plan.N)
+    err = np.abs(out.ravel()[idx] - ref).max()
+    print("config2 sigma_s=%g max abs err %.3e on %d px" % (sigma_s, err, len(idx)))
+    assert err <= TOL
