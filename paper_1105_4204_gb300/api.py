@@ -151,3 +151,81 @@ def forward_unfused(plan: Plan, img: torch.Tensor, out: torch.Tensor | None = No
                                    ctypes.c_void_p(workspace.data_ptr()), nbytes,
                                    _stream_ptr(stream)))
     return out
+
+
+def backward(plan: Plan, f: torch.Tensor, out: torch.Tensor, q: torch.Tensor,
+             grad_out: torch.Tensor, need_sigma: bool = True, grad_in: torch.Tensor | None = None,
+             workspace: torch.Tensor | None = None, stream=None):
+    """Adjoint of ``forward`` for one H x W float32 image.  Returns (dL/df,
+    dL/dsigma_r as a 0-dim float64 device tensor or None)."""
+    for t in (f, out, q, grad_out):
+        if not t.is_cuda or t.dtype != torch.float32 or t.dim() != 2 or not t.is_contiguous():
+            raise ValueError("backward takes contiguous H x W float32 CUDA tensors")
+    H, W = f.shape
+    if grad_in is None:
+        grad_in = torch.empty((H, W), dtype=torch.float32, device=f.device)
+    gs = None
+    ws_ptr, nbytes = 0, 0
+    if need_sigma:
+        gs = torch.empty((), dtype=torch.float64, device=f.device)
+        nbytes = lib().bf_backward_workspace(plan.handle, H, W)
+        if workspace is None or workspace.numel() * workspace.element_size() < nbytes:
+            workspace = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=f.device)
+        ws_ptr = workspace.data_ptr()
+    check(lib().bf_backward(plan.handle, ctypes.c_void_p(f.data_ptr()),
+                            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                            ctypes.c_void_p(grad_out.data_ptr()),
+                            ctypes.c_void_p(grad_in.data_ptr()),
+                            ctypes.c_void_p(gs.data_ptr() if gs is not None else 0), H, W,
+                            ctypes.c_void_p(ws_ptr), nbytes, _stream_ptr(stream)))
+    return grad_in, gs
+
+
+class BilateralFunction(torch.autograd.Function):
+    """Differentiable filter: forward through the fused kernel, backward through
+    the fused adjoint kernel (gradients w.r.t. the image and sigma_r; N is held
+    at the degree the rule gives for the forward's sigma_r)."""
+
+    @staticmethod
+    def forward(ctx, f, sigma_r, sigma_s, T, kind, radius):
+        sr = float(sigma_r)
+        plan = Plan(sigma_s, sr, T, kind=kind, radius=radius)
+        imgs = f if f.dim() == 3 else f.unsqueeze(0)
+        outs, qs = [], []
+        for b in range(imgs.shape[0]):
+            o, q = forward(plan, imgs[b].contiguous(), return_q=True)
+            outs.append(o)
+            qs.append(q)
+        out = torch.stack(outs)
+        q = torch.stack(qs)
+        ctx.plan = plan
+        ctx.squeeze = f.dim() == 2
+        ctx.sigma_is_tensor = isinstance(sigma_r, torch.Tensor)
+        ctx.save_for_backward(imgs, out, q)
+        return out[0] if ctx.squeeze else out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        imgs, out, q = ctx.saved_tensors
+        g = grad_out if grad_out.dim() == 3 else grad_out.unsqueeze(0)
+        need_sigma = ctx.sigma_is_tensor and ctx.needs_input_grad[1]
+        grads = []
+        gsum = None
+        for b in range(imgs.shape[0]):
+            gf, gs = backward(ctx.plan, imgs[b].contiguous(), out[b], q[b], g[b].contiguous(),
+                              need_sigma=need_sigma)
+            grads.append(gf)
+            if gs is not None:
+                gsum = gs if gsum is None else gsum + gs
+        gf = torch.stack(grads)
+        if ctx.squeeze:
+            gf = gf[0]
+        gsig = gsum.to(torch.float32) if gsum is not None else None
+        return gf, gsig, None, None, None, None
+
+
+def bilateral(f: torch.Tensor, sigma_s: float, sigma_r, T: float = 255.0, kind="gauss",
+              radius: int = 0) -> torch.Tensor:
+    """Differentiable bilateral filter of an H x W or B x H x W float32 CUDA
+    tensor; ``sigma_r`` may be a float or a 0-dim tensor requiring grad."""
+    return BilateralFunction.apply(f, sigma_r, float(sigma_s), float(T), kind, int(radius))

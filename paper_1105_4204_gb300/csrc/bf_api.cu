@@ -161,12 +161,46 @@ extern "C" bf_status bf_forward_unfused(const bf_plan *plan, const float *in, fl
 
 // ---- not yet available ------------------------------------------------------
 
-extern "C" size_t bf_backward_workspace(const bf_plan *, int, int) { return 0; }
+// ---- backward -------------------------------------------------------------
 
-extern "C" bf_status bf_backward(const bf_plan *, const float *, const float *, const float *,
-                                 const float *, float *, double *, int, int, void *, size_t,
-                                 cudaStream_t) {
-    return fail(BF_EUNSUPPORTED, "bf_backward: not built yet");
+namespace bf {
+bool bwd_supported(const bf_plan *p);
+size_t bwd_blocks(int H, int W);
+cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, const float *q,
+                            const float *u, float *grad, double *grad_sigma_r, double *partials,
+                            int H, int W, cudaStream_t s);
+}  // namespace bf
+
+extern "C" size_t bf_backward_workspace(const bf_plan *plan, int H, int W) {
+    if (!plan || H < 1 || W < 1) return 0;
+    return bwd_blocks(H, W) * sizeof(double);
+}
+
+extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const float *out,
+                                 const float *q, const float *grad_out, float *grad_in,
+                                 double *grad_sigma_r, int H, int W, void *workspace,
+                                 size_t workspace_bytes, cudaStream_t stream) {
+    if (!plan) return fail(BF_EINVAL, "bf_backward: plan is NULL");
+    if (!f || !out || !q || !grad_out || !grad_in)
+        return fail(BF_EINVAL, "bf_backward: a data pointer is NULL");
+    if (H < 1 || W < 1) return fail(BF_EINVAL, "bf_backward: H and W must be >= 1");
+    if ((long long)H * W > (1LL << 31) / 4)
+        return fail(BF_EUNSUPPORTED, "bf_backward: image too large");
+    if (!bwd_supported(plan))
+        return fail(BF_EUNSUPPORTED, "bf_backward: no kernel for this spatial support "
+                                     "(Gaussian R <= 24 or box r <= 8)");
+    if (grad_sigma_r) {
+        if (!workspace) return fail(BF_EINVAL, "bf_backward: workspace is NULL");
+        if (workspace_bytes < bwd_blocks(H, W) * sizeof(double))
+            return fail(BF_EINVAL, "bf_backward: workspace too small (need " +
+                                       std::to_string(bwd_blocks(H, W) * sizeof(double)) +
+                                       " bytes)");
+        if ((uintptr_t)workspace % 8 != 0)
+            return fail(BF_EINVAL, "bf_backward: workspace must be 8-byte aligned");
+    }
+    return cuda_check(launch_backward(plan, f, out, q, grad_out, grad_in, grad_sigma_r,
+                                      reinterpret_cast<double *>(workspace), H, W, stream),
+                      "bf_backward launch");
 }
 
 extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *, const int *,

@@ -1,0 +1,142 @@
+"""GPU parity of the fused adjoint kernel (dL/df and dL/dsigma_r) against the
+FP64 oracle: its exact gradient of eq. (BF), and central finite differences of
+its brute force.  Bar: relative error <= 1e-3 (norm-wise, and per element
+against the largest element), as the differentiable workload specifies."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+REL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def bf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_4204_gb300 import build
+    build.build()
+    import paper_1105_4204_gb300 as pkg
+    return pkg
+
+
+def _gpu_grad(bf, img, u, plan):
+    import torch
+    f = torch.from_numpy(img).cuda()
+    out, q = bf.forward(plan, f, return_q=True)
+    g, gs = bf.backward(plan, f, out, q, torch.from_numpy(u).cuda())
+    torch.cuda.synchronize()
+    return g.cpu().numpy().astype(np.float64), float(gs.item())
+
+
+def _w1(oracle, plan):
+    if plan.kind == "gauss":
+        return oracle.spatial_w1("gauss", plan.sigma_s, radius=plan.radius)
+    return oracle.spatial_w1("box", plan.sigma_s, radius=plan.radius // 3, passes=3)
+
+
+def _check(g, gref, gs, gsref):
+    scale = np.abs(gref).max()
+    assert np.abs(g - gref).max() <= REL * scale, np.abs(g - gref).max() / scale
+    assert np.linalg.norm(g - gref) <= REL * np.linalg.norm(gref)
+    assert abs(gs - gsref) <= REL * abs(gsref), (gs, gsref)
+
+
+def test_config5_crop_against_exact_gradient(bf, oracle):
+    # 64 x 64 crop of the differentiable workload: Gaussian sigma_s = 4 (R = 12),
+    # sigma_r = 25 (N = 43), random-normal upstream gradient
+    img = synth.rectangles(512, 512, seed=0)[100:164, 200:264].copy()
+    u = synth.upstream(img.shape, seed=1)
+    plan = bf.Plan(4.0, 25.0, kind="gauss")
+    assert plan.N == 43 and plan.radius == 12
+    g, gs = _gpu_grad(bf, img, u, plan)
+    gref, gsref = oracle.bf_grad(img.astype(np.float64), u.astype(np.float64), sigma_r=25.0,
+                                 w1=_w1(oracle, plan), N=plan.N)
+    print("config5 crop: max rel %.3e, sigma_r %.6g vs %.6g" % (
+        np.abs(g - gref).max() / np.abs(gref).max(), gs, gsref))
+    _check(g, gref, gs, gsref)
+
+
+def test_config5_crop_against_finite_differences(bf, oracle):
+    img = synth.rectangles(512, 512, seed=3)[300:364, 40:104].copy()
+    u = synth.upstream(img.shape, seed=2)
+    plan = bf.Plan(4.0, 25.0, kind="gauss")
+    g, gs = _gpu_grad(bf, img, u, plan)
+    w1 = _w1(oracle, plan)
+    idx = synth.sample_indices(64, 64, 200, seed=4)
+    fd = oracle.fd_grad_f(img.astype(np.float64), u.astype(np.float64), idx, h=1e-3,
+                          sigma_r=25.0, w1=w1, N=plan.N)
+    gsel = g.ravel()[idx]
+    assert np.abs(gsel - fd).max() <= REL * np.abs(fd).max()
+    assert np.linalg.norm(gsel - fd) <= REL * np.linalg.norm(fd)
+    fds = oracle.fd_grad_sigma_r(img.astype(np.float64), u.astype(np.float64), h=1e-3,
+                                 sigma_r=25.0, w1=w1, N=plan.N)
+    assert abs(gs - fds) <= REL * abs(fds)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 17), (17, 1), (5, 3), (37, 53), (70, 131)])
+def test_ragged_and_degenerate_sizes(bf, oracle, H, W):
+    img = synth.rectangles(H, W, n_rect=4, noise=10.0, seed=H * 100 + W)
+    u = synth.upstream((H, W), seed=W)
+    plan = bf.Plan(1.5, 30.0, kind="gauss")
+    g, gs = _gpu_grad(bf, img, u, plan)
+    gref, gsref = oracle.bf_grad(img.astype(np.float64), u.astype(np.float64), sigma_r=30.0,
+                                 w1=_w1(oracle, plan), N=plan.N)
+    scale = max(np.abs(gref).max(), 1e-12)
+    assert np.abs(g - gref).max() <= REL * scale
+    # a one-pixel image has dL/dsigma_r = 0 exactly; FP32 cancellation of the
+    # f^2 planes (magnitude ~T^2) leaves ~1e-6 there
+    assert abs(gs - gsref) <= REL * abs(gsref) + 1e-5
+
+
+@pytest.mark.parametrize("r", [1, 2, 4, 8])
+def test_box_gradient(bf, oracle, r):
+    img = synth.smooth_field(48, 80, noise=5.0, seed=r)
+    u = synth.upstream(img.shape, seed=r)
+    plan = bf.Plan(float(r), 20.0, kind="box", radius=r)
+    g, gs = _gpu_grad(bf, img, u, plan)
+    gref, gsref = oracle.bf_grad(img.astype(np.float64), u.astype(np.float64), sigma_r=20.0,
+                                 w1=_w1(oracle, plan), N=plan.N)
+    _check(g, gref, gs, gsref)
+
+
+@pytest.mark.parametrize("R", [2, 5, 9, 18, 24])
+def test_gauss_radii_gradient(bf, oracle, R):
+    img = synth.rectangles(40, 70, n_rect=5, seed=R)
+    u = synth.upstream(img.shape, seed=R + 1)
+    plan = bf.Plan(R / 3.0, 35.0, kind="gauss", radius=R)
+    g, gs = _gpu_grad(bf, img, u, plan)
+    gref, gsref = oracle.bf_grad(img.astype(np.float64), u.astype(np.float64), sigma_r=35.0,
+                                 w1=_w1(oracle, plan), N=plan.N)
+    _check(g, gref, gs, gsref)
+
+
+def test_autograd_function(bf, oracle):
+    import torch
+    imgs = np.stack([synth.rectangles(40, 48, seed=s) for s in range(3)])
+    u = synth.upstream(imgs.shape, seed=9)
+    f = torch.from_numpy(imgs).cuda().requires_grad_(True)
+    sr = torch.tensor(25.0, device="cuda", requires_grad=True)
+    out = bf.bilateral(f, 2.0, sr)
+    (out * torch.from_numpy(u).cuda()).sum().backward()
+    plan = bf.Plan(2.0, 25.0)
+    gs_tot = 0.0
+    for b in range(3):
+        gref, gsref = oracle.bf_grad(imgs[b].astype(np.float64), u[b].astype(np.float64),
+                                     sigma_r=25.0, w1=_w1(oracle, plan), N=plan.N)
+        gb = f.grad[b].cpu().numpy()
+        assert np.abs(gb - gref).max() <= REL * np.abs(gref).max()
+        gs_tot += gsref
+    assert abs(float(sr.grad) - gs_tot) <= REL * abs(gs_tot)
+
+
+def test_backward_is_deterministic(bf):
+    img = synth.rectangles(100, 90, seed=5)
+    u = synth.upstream(img.shape, seed=5)
+    plan = bf.Plan(3.0, 30.0)
+    a = _gpu_grad(bf, img, u, plan)
+    b = _gpu_grad(bf, img, u, plan)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[1] == b[1]
