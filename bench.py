@@ -362,6 +362,10 @@ def run_ours(args):
         extras["fused_ms_per_call"] = {"sigma_s=%g" % s: float(m) for s, m in zip(SIGMA_S, call_ms)}
         extras["wall_s_timed_region"] = t_wall
 
+    if rank == 0 and not args.no_extras:
+        extras.update(measure_fwd_bwd(bf, torch, dev, stream))
+        extras.update(measure_batch(bf, torch, dev, stream))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_rate(float(os.environ.get("BF_CPU_SECONDS", "15")))
@@ -385,6 +389,81 @@ def run_ours(args):
     return 0
 
 
+def _time(fn, torch, stream, reps):
+    fn()
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        fn()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    return a0.elapsed_time(a1) / reps
+
+
+def measure_fwd_bwd(bf, torch, dev, stream):
+    """Differentiable workload: 16 x 512 x 512, Gaussian sigma_s = 4 (R = 12),
+    sigma_r = 25 (N = 43): forward with Q, then the adjoint w.r.t. the image and
+    sigma_r for a random-normal upstream gradient."""
+    import synth
+    B, HH, WW = 16, 512, 512
+    imgs = torch.from_numpy(np.stack([synth.rectangles(HH, WW, seed=s) for s in range(B)])).to(dev)
+    u = torch.from_numpy(synth.upstream((B, HH, WW), seed=1)).to(dev)
+    plan = bf.Plan(4.0, 25.0, 255.0, kind="gauss")
+    outs = torch.empty_like(imgs)
+    qs = torch.empty_like(imgs)
+    grads = torch.empty_like(imgs)
+    ws = torch.empty(64 * 1024, dtype=torch.float64, device=dev)
+
+    def fwd():
+        for b in range(B):
+            bf.forward(plan, imgs[b], return_q=True, out=outs[b], q=qs[b])
+
+    def fwd_bwd():
+        fwd()
+        for b in range(B):
+            bf.backward(plan, imgs[b], outs[b], qs[b], u[b], grad_in=grads[b], workspace=ws)
+
+    t_f = _time(fwd, torch, stream, 5)
+    t_fb = _time(fwd_bwd, torch, stream, 5)
+    px = B * HH * WW
+    a, w = plan.terms()
+    nz = int(np.sum(w > 0))
+    return {"fwd_bwd_config": "16 x 512^2, gauss sigma_s=4 (R=12), sigma_r=25 (N=43)",
+            "fwd_mpx_s": px / (t_f * 1e-3) / 1e6, "fwd_bwd_mpx_s": px / (t_fb * 1e-3) / 1e6,
+            "fwd_ms": t_f, "fwd_bwd_ms": t_fb,
+            "fwd_instr_per_px": gauss_instr_per_px(nz, bool(np.any(w == 0)), 12)}
+
+
+def measure_batch(bf, torch, dev, stream):
+    """Batched workload: 64 images, W ~ U[128,1920], H ~ U[128,1080], box
+    sigma_s ~ U[2,16], sigma_r ~ U[15,60]; one persistent launch replayed from
+    a CUDA graph, against a loop of single-image calls."""
+    import synth
+    specs = synth.batch_specs(64, seed=0)
+    imgs = synth.batch_images(specs, noise=10.0, seed=0)
+    plans = [bf.Plan(ss, sr, 255.0, kind="box") for (_, _, ss, sr) in specs]
+    ins = [torch.from_numpy(im).to(dev) for im in imgs]
+    outs = [torch.empty_like(t) for t in ins]
+    b = bf.Batch(plans, [(h, w) for (h, w, _, _) in specs])
+    b.bind(ins, outs)
+    tuned = b.tune(reps=2)
+    t_batch = _time(b.forward, torch, stream, 5)
+
+    def loop():
+        for i in range(len(plans)):
+            bf.forward(plans[i], ins[i], out=outs[i])
+
+    t_loop = _time(loop, torch, stream, 3)
+    px = sum(h * w for (h, w, _, _) in specs)
+    return {"batch_config": "64 images, box sigma_s~U[2,16], sigma_r~U[15,60], N in [%d, %d]" % (
+                min(p.N for p in plans), max(p.N for p in plans)),
+            "batch_mpx_s": px / (t_batch * 1e-3) / 1e6,
+            "batch_images_s": len(plans) / (t_batch * 1e-3),
+            "batch_loop_mpx_s": px / (t_loop * 1e-3) / 1e6,
+            "batch_ms": t_batch, "batch_loop_ms": t_loop, "batch_tuned": tuned}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,6 +471,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

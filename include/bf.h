@@ -190,9 +190,10 @@ bf_status bf_backward(const bf_plan *plan, const float *f, const float *out,
  *
  * bf_batch_create  : plans[count], H[count], W[count] are host arrays; the
  *                    batch copies what it needs (the plans may be destroyed
- *                    afterwards).  Allocates the batch's device tables and
- *                    queue (freed by bf_batch_destroy).  The tile shape and
- *                    grid size come from the autotuner's cache.
+ *                    afterwards).  Every plan must be the 3-pass box with
+ *                    1 <= r <= 16 (BF_EUNSUPPORTED otherwise).  Allocates the
+ *                    batch's device tables and queue (freed by
+ *                    bf_batch_destroy); builds the graph.
  * bf_batch_bind    : in[count], out[count] are host arrays of device
  *                    pointers (f32, row stride W); copied to the device on
  *                    `stream`.  Call again whenever the buffers change.
@@ -209,6 +210,17 @@ bf_status bf_batch_bind(bf_batch *batch, const float *const *in, float *const *o
 bf_status bf_batch_forward(bf_batch *batch, cudaStream_t stream);
 bf_status bf_batch_check(bf_batch *batch, cudaStream_t stream, int *device_error);
 void bf_batch_destroy(bf_batch *batch);
+
+/*
+ * Launch-configuration autotuner for a bound batch (not in the paper): times
+ * `reps` replays for each candidate -- persistent grid of 1x or 2x the
+ * resident blocks, tile queue in largest-cost-first or image order -- keeps
+ * the fastest in the batch's graph and reports it (any output may be NULL).
+ * Synchronises `stream`.  The tile shapes themselves are fixed per box
+ * half-width (32 x 64 for r <= 8, 16 x 64 above).
+ */
+bf_status bf_batch_tune(bf_batch *batch, cudaStream_t stream, int reps, int *grid,
+                        int *order, float *ms);
 
 /* Message for the last non-OK status returned on the calling thread. */
 const char *bf_last_error(void);

@@ -229,3 +229,55 @@ def bilateral(f: torch.Tensor, sigma_s: float, sigma_r, T: float = 255.0, kind="
     """Differentiable bilateral filter of an H x W or B x H x W float32 CUDA
     tensor; ``sigma_r`` may be a float or a 0-dim tensor requiring grad."""
     return BilateralFunction.apply(f, sigma_r, float(sigma_s), float(T), kind, int(radius))
+
+
+class Batch:
+    """Many float32 H x W images, each with its own plan, filtered by one
+    persistent launch replayed from a CUDA graph."""
+
+    def __init__(self, plans, sizes):
+        self._lib = lib()
+        self.plans = list(plans)
+        self.sizes = [(int(h), int(w)) for h, w in sizes]
+        n = len(self.plans)
+        arr = (ctypes.c_void_p * n)(*[p.handle.value for p in self.plans])
+        Hs = (ctypes.c_int * n)(*[h for h, _ in self.sizes])
+        Ws = (ctypes.c_int * n)(*[w for _, w in self.sizes])
+        self._h = ctypes.c_void_p()
+        check(self._lib.bf_batch_create(ctypes.byref(self._h), arr, Hs, Ws, n))
+        self._bound = None
+
+    def bind(self, ins, outs, stream=None):
+        n = len(self.plans)
+        for t, (h, w) in zip(list(ins) + list(outs), self.sizes + self.sizes):
+            if not t.is_cuda or t.dtype != torch.float32 or tuple(t.shape) != (h, w) \
+                    or not t.is_contiguous():
+                raise ValueError("batch images must be contiguous float32 CUDA tensors of their size")
+        pin = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ins])
+        pout = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+        check(self._lib.bf_batch_bind(self._h, pin, pout, _stream_ptr(stream)))
+        self._bound = (list(ins), list(outs))  # keep the buffers alive while bound
+
+    def forward(self, stream=None):
+        check(self._lib.bf_batch_forward(self._h, _stream_ptr(stream)))
+
+    def check(self, stream=None) -> int:
+        err = ctypes.c_int()
+        check(self._lib.bf_batch_check(self._h, _stream_ptr(stream), ctypes.byref(err)))
+        return err.value
+
+    def tune(self, reps: int = 3, stream=None):
+        g, o, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        check(self._lib.bf_batch_tune(self._h, _stream_ptr(stream), int(reps), ctypes.byref(g),
+                                      ctypes.byref(o), ctypes.byref(ms)))
+        return {"grid": g.value, "order": "largest-cost-first" if o.value == 0 else "image",
+                "ms": ms.value}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                self._lib.bf_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = ctypes.c_void_p()

@@ -202,20 +202,3 @@ extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const floa
                                       reinterpret_cast<double *>(workspace), H, W, stream),
                       "bf_backward launch");
 }
-
-extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *, const int *,
-                                     const int *, int) {
-    if (out) *out = nullptr;
-    return fail(BF_EUNSUPPORTED, "bf_batch_create: not built yet");
-}
-extern "C" bf_status bf_batch_bind(bf_batch *, const float *const *, float *const *,
-                                   cudaStream_t) {
-    return fail(BF_EUNSUPPORTED, "bf_batch_bind: not built yet");
-}
-extern "C" bf_status bf_batch_forward(bf_batch *, cudaStream_t) {
-    return fail(BF_EUNSUPPORTED, "bf_batch_forward: not built yet");
-}
-extern "C" bf_status bf_batch_check(bf_batch *, cudaStream_t, int *) {
-    return fail(BF_EUNSUPPORTED, "bf_batch_check: not built yet");
-}
-extern "C" void bf_batch_destroy(bf_batch *) {}

@@ -1,0 +1,412 @@
+// Batched forward: many single-channel f32 images of uneven sizes, each with
+// its own plan, in one persistent launch.
+//
+// The host flattens every image into tiles, orders them largest cost first
+// (longest-processing-time order: cost ~ terms x tile area including the
+// halo), and uploads the queue with a per-image descriptor and term table.
+// Each resident block of the persistent kernel claims the next tile with one
+// atomicAdd and runs the fused tile body of that image's box half-width r
+// (1 <= r <= 16, one instantiation per r), so small and large images, cheap
+// and expensive plans share the GPU without a tail of idle SMs per image.
+// The claim loop is bounded by the number of tiles; a block that would exceed
+// it sets the device error flag instead.  The counter reset and the launch are
+// recorded once as a CUDA graph (memset node + kernel node) and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bf_tile.cuh"
+
+namespace bf {
+
+namespace {
+
+constexpr int kBatchNT = 256;
+constexpr int kBatchMaxR = 16;
+
+// tile shapes of the batch bodies; every body uses kBatchNT threads
+template <int R>
+struct BatchShape {
+    static constexpr int TH = R <= 8 ? 32 : 16;
+    static constexpr int TW = 64;
+    static constexpr int TWT = R <= 8 ? 16 : 8;
+    using G = TileGeom<1, R, TH, TW, TWT>;
+    static_assert(G::NT == kBatchNT, "batch bodies share one block size");
+};
+
+int batch_tile_h(int r) { return r <= 8 ? 32 : 16; }
+constexpr int kBatchTW = 64;
+
+struct ImgDesc {
+    const float *in;
+    float *out;
+    int H, W, r, n_terms, term_off, tiles_x;
+    float q_scale;
+};
+
+struct BatchParams {
+    const ImgDesc *imgs;
+    const int4 *queue;  // (image, tile x, tile y, 0)
+    int n_tiles;
+    int *counter;
+    int *err;
+    const float *ta;    // term weights, all images
+    const float *tt;    // term frequencies (turns per gray level)
+};
+
+template <int R>
+__device__ __forceinline__ void run_tile(const BatchParams &p, const ImgDesc &d, int tx, int ty,
+                                         float *smem) {
+    using S = BatchShape<R>;
+    TileJob jb;
+    jb.in = d.in;
+    jb.out = d.out;
+    jb.q_out = nullptr;
+    jb.in_row_stride = d.W;
+    jb.H = d.H;
+    jb.W = d.W;
+    jb.C = 1;
+    jb.ch = 0;
+    jb.dtype = 0;
+    jb.q_scale = d.q_scale;
+    jb.a = p.ta + d.term_off;
+    jb.t = p.tt + d.term_off;
+    jb.n_terms = d.n_terms;
+    jb.w = nullptr;
+    jb.x0 = tx * S::TW;
+    jb.y0 = ty * S::TH;
+    tile_body<1, R, S::TH, S::TW, S::TWT>(jb, smem);
+}
+
+template <int... Rs>
+struct MaxSmem;
+template <int R>
+struct MaxSmem<R> {
+    static constexpr size_t v = BatchShape<R>::G::SMEM;
+};
+template <int R, int... Rs>
+struct MaxSmem<R, Rs...> {
+    static constexpr size_t v =
+        BatchShape<R>::G::SMEM > MaxSmem<Rs...>::v ? BatchShape<R>::G::SMEM : MaxSmem<Rs...>::v;
+};
+constexpr size_t kBatchSmem = MaxSmem<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16>::v;
+static_assert(kBatchSmem <= 227 * 1024, "batch shared memory");
+
+__global__ void __launch_bounds__(kBatchNT) bf_batch_persist(const __grid_constant__ BatchParams p) {
+    extern __shared__ float4 sm4[];
+    float *smem = reinterpret_cast<float *>(sm4);
+    __shared__ int s_tile;
+    for (int it = 0; it <= p.n_tiles; ++it) {
+        __syncthreads();  // the previous tile and s_tile are no longer in use
+        if (threadIdx.x == 0) s_tile = atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= p.n_tiles) return;
+        if (it == p.n_tiles) {  // more claims than tiles: cannot happen unless the queue is corrupt
+            if (threadIdx.x == 0) atomicExch(p.err, 1);
+            return;
+        }
+        const int4 w = p.queue[t];
+        const ImgDesc d = p.imgs[w.x];
+        switch (d.r) {
+            case 1: run_tile<1>(p, d, w.y, w.z, smem); break;
+            case 2: run_tile<2>(p, d, w.y, w.z, smem); break;
+            case 3: run_tile<3>(p, d, w.y, w.z, smem); break;
+            case 4: run_tile<4>(p, d, w.y, w.z, smem); break;
+            case 5: run_tile<5>(p, d, w.y, w.z, smem); break;
+            case 6: run_tile<6>(p, d, w.y, w.z, smem); break;
+            case 7: run_tile<7>(p, d, w.y, w.z, smem); break;
+            case 8: run_tile<8>(p, d, w.y, w.z, smem); break;
+            case 9: run_tile<9>(p, d, w.y, w.z, smem); break;
+            case 10: run_tile<10>(p, d, w.y, w.z, smem); break;
+            case 11: run_tile<11>(p, d, w.y, w.z, smem); break;
+            case 12: run_tile<12>(p, d, w.y, w.z, smem); break;
+            case 13: run_tile<13>(p, d, w.y, w.z, smem); break;
+            case 14: run_tile<14>(p, d, w.y, w.z, smem); break;
+            case 15: run_tile<15>(p, d, w.y, w.z, smem); break;
+            case 16: run_tile<16>(p, d, w.y, w.z, smem); break;
+            default:
+                if (threadIdx.x == 0) atomicExch(p.err, 2);
+                break;
+        }
+    }
+}
+
+}  // namespace
+
+}  // namespace bf
+
+using namespace bf;
+
+struct bf_batch {
+    int count = 0;
+    int dev = 0;
+    std::vector<ImgDesc> h_imgs;
+    std::vector<int4> h_queue_lpt, h_queue_rowmajor;
+    ImgDesc *d_imgs = nullptr;
+    int4 *d_queue = nullptr;
+    int *d_counter = nullptr;
+    int *d_err = nullptr;
+    float *d_ta = nullptr, *d_tt = nullptr;
+    int n_tiles = 0;
+    int grid = 0;
+    int order = 0;  // 0: largest cost first, 1: image by image
+    bool bound = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void batch_free(bf_batch *b) {
+    if (!b) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(b->dev);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_imgs);
+    cudaFree(b->d_queue);
+    cudaFree(b->d_counter);
+    cudaFree(b->d_err);
+    cudaFree(b->d_ta);
+    cudaFree(b->d_tt);
+    cudaSetDevice(cur);
+    delete b;
+}
+
+// (Re)build the graph: counter reset, then the persistent kernel.
+static cudaError_t batch_build_graph(bf_batch *b) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaError_t e = cudaGraphCreate(&b->graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaMemsetParams ms{};
+    ms.dst = b->d_counter;
+    ms.value = 0;
+    ms.elementSize = sizeof(int);
+    ms.width = 1;
+    ms.height = 1;
+    ms.pitch = sizeof(int);
+    cudaGraphNode_t n_memset, n_kernel;
+    e = cudaGraphAddMemsetNode(&n_memset, b->graph, nullptr, 0, &ms);
+    if (e != cudaSuccess) return e;
+    BatchParams prm;
+    prm.imgs = b->d_imgs;
+    prm.queue = b->d_queue;
+    prm.n_tiles = b->n_tiles;
+    prm.counter = b->d_counter;
+    prm.err = b->d_err;
+    prm.ta = b->d_ta;
+    prm.tt = b->d_tt;
+    void *args[] = {&prm};
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)bf_batch_persist;
+    kp.gridDim = dim3(b->grid);
+    kp.blockDim = dim3(kBatchNT);
+    kp.sharedMemBytes = (unsigned)kBatchSmem;
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&n_kernel, b->graph, &n_memset, 1, &kp);
+    if (e != cudaSuccess) return e;
+    return cudaGraphInstantiate(&b->exec, b->graph, 0);
+}
+
+static cudaError_t batch_upload_queue(bf_batch *b, cudaStream_t s) {
+    const std::vector<int4> &q = b->order == 0 ? b->h_queue_lpt : b->h_queue_rowmajor;
+    return cudaMemcpyAsync(b->d_queue, q.data(), sizeof(int4) * q.size(), cudaMemcpyHostToDevice, s);
+}
+
+extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans, const int *H,
+                                     const int *W, int count) {
+    if (!out) return fail(BF_EINVAL, "bf_batch_create: out is NULL");
+    *out = nullptr;
+    if (!plans || !H || !W || count < 1)
+        return fail(BF_EINVAL, "bf_batch_create: plans/H/W NULL or count < 1");
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i]) return fail(BF_EINVAL, "bf_batch_create: a plan is NULL");
+        if (H[i] < 1 || W[i] < 1) return fail(BF_EINVAL, "bf_batch_create: a size is < 1");
+        if ((long long)H[i] * W[i] > (1LL << 31) / 4)
+            return fail(BF_EUNSUPPORTED, "bf_batch_create: an image is too large");
+        if (plans[i]->kind != BF_SPATIAL_BOX_ITER || plans[i]->r_box < 1 ||
+            plans[i]->r_box > kBatchMaxR)
+            return fail(BF_EUNSUPPORTED,
+                        "bf_batch_create: the batch serves the 3-pass box with 1 <= r <= 16");
+    }
+    bf_batch *b = new (std::nothrow) bf_batch();
+    if (!b) return fail(BF_ENOMEM, "bf_batch_create: out of host memory");
+    cudaError_t e = cudaGetDevice(&b->dev);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_check(e, "bf_batch_create");
+    }
+    b->count = count;
+    std::vector<float> ta, tt;
+    struct Cost {
+        double c;
+        int4 w;
+    };
+    std::vector<Cost> tiles;
+    for (int i = 0; i < count; ++i) {
+        const bf_plan *pl = plans[i];
+        ImgDesc d{};
+        d.H = H[i];
+        d.W = W[i];
+        d.r = pl->r_box;
+        d.n_terms = (int)pl->a32.size();
+        d.term_off = (int)ta.size();
+        d.q_scale = pl->q_scale;
+        const int th = batch_tile_h(d.r);
+        d.tiles_x = (W[i] + kBatchTW - 1) / kBatchTW;
+        const int tiles_y = (H[i] + th - 1) / th;
+        for (int k = 0; k < d.n_terms; ++k) {
+            ta.push_back(pl->a32[k]);
+            tt.push_back(pl->turns32[k]);
+        }
+        b->h_imgs.push_back(d);
+        const double cost = (double)d.n_terms * (th + 6.0 * d.r) * (kBatchTW + 6.0 * d.r);
+        for (int ty = 0; ty < tiles_y; ++ty)
+            for (int tx = 0; tx < d.tiles_x; ++tx) {
+                const int4 w = make_int4(i, tx, ty, 0);
+                tiles.push_back({cost, w});
+                b->h_queue_rowmajor.push_back(w);
+            }
+    }
+    std::stable_sort(tiles.begin(), tiles.end(),
+                     [](const Cost &x, const Cost &y) { return x.c > y.c; });
+    for (auto &c : tiles) b->h_queue_lpt.push_back(c.w);
+    b->n_tiles = (int)tiles.size();
+
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(bf_batch_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kBatchSmem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf_batch_persist, kBatchNT,
+                                                          kBatchSmem);
+    if (e == cudaSuccess) {
+        b->grid = std::max(1, std::min(sms * std::max(per_sm, 1), b->n_tiles));
+        size_t nq = sizeof(int4) * (size_t)b->n_tiles;
+        e = cudaMalloc(&b->d_imgs, sizeof(ImgDesc) * count);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, nq);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_ta, sizeof(float) * std::max<size_t>(1, ta.size()));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_tt, sizeof(float) * std::max<size_t>(1, tt.size()));
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_queue, b->h_queue_lpt.data(), sizeof(int4) * b->n_tiles,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_ta, ta.data(), sizeof(float) * ta.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_tt, tt.data(), sizeof(float) * tt.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = batch_build_graph(b);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        if (e == cudaErrorMemoryAllocation)
+            return fail(BF_ENOMEM, "bf_batch_create: device allocation failed");
+        return cuda_check(e, "bf_batch_create");
+    }
+    *out = b;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_batch_bind(bf_batch *b, const float *const *in, float *const *out,
+                                   cudaStream_t stream) {
+    if (!b) return fail(BF_EINVAL, "bf_batch_bind: batch is NULL");
+    if (!in || !out) return fail(BF_EINVAL, "bf_batch_bind: in/out is NULL");
+    for (int i = 0; i < b->count; ++i) {
+        if (!in[i] || !out[i]) return fail(BF_EINVAL, "bf_batch_bind: an image pointer is NULL");
+        b->h_imgs[i].in = in[i];
+        b->h_imgs[i].out = out[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_imgs, b->h_imgs.data(), sizeof(ImgDesc) * b->count,
+                                    cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // h_imgs may change on the next bind
+    if (e != cudaSuccess) return cuda_check(e, "bf_batch_bind");
+    b->bound = true;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_batch_forward(bf_batch *b, cudaStream_t stream) {
+    if (!b) return fail(BF_EINVAL, "bf_batch_forward: batch is NULL");
+    if (!b->bound) return fail(BF_EINVAL, "bf_batch_forward: call bf_batch_bind first");
+    return cuda_check(cudaGraphLaunch(b->exec, stream), "bf_batch_forward");
+}
+
+extern "C" bf_status bf_batch_check(bf_batch *b, cudaStream_t stream, int *device_error) {
+    if (!b || !device_error) return fail(BF_EINVAL, "bf_batch_check: NULL argument");
+    cudaError_t e = cudaStreamSynchronize(stream);
+    int v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(e, "bf_batch_check");
+    *device_error = v;
+    return BF_OK;
+}
+
+extern "C" void bf_batch_destroy(bf_batch *b) { batch_free(b); }
+
+// Launch-configuration autotuner for a bound batch: times the graph for each
+// candidate (persistent grid of 1x or 2x the resident blocks, queue in
+// largest-cost-first or image order), keeps the fastest, and reports it.
+extern "C" bf_status bf_batch_tune(bf_batch *b, cudaStream_t stream, int reps, int *grid_out,
+                                   int *order_out, float *ms_out) {
+    if (!b) return fail(BF_EINVAL, "bf_batch_tune: batch is NULL");
+    if (!b->bound) return fail(BF_EINVAL, "bf_batch_tune: call bf_batch_bind first");
+    if (reps < 1) reps = 3;
+    int sms = 0, per_sm = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf_batch_persist, kBatchNT,
+                                                          kBatchSmem);
+    if (e != cudaSuccess) return cuda_check(e, "bf_batch_tune");
+    const int resident = sms * std::max(per_sm, 1);
+    const int grids[2] = {std::min(resident, b->n_tiles), std::min(2 * resident, b->n_tiles)};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_grid = b->grid, best_order = b->order;
+    for (int order = 0; order < 2 && e == cudaSuccess; ++order) {
+        for (int gi = 0; gi < 2 && e == cudaSuccess; ++gi) {
+            b->order = order;
+            b->grid = std::max(1, grids[gi]);
+            e = batch_upload_queue(b, stream);
+            if (e == cudaSuccess) e = batch_build_graph(b);
+            if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, stream);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+            for (int k = 0; k < reps && e == cudaSuccess; ++k) e = cudaGraphLaunch(b->exec, stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                best_grid = b->grid;
+                best_order = order;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_check(e, "bf_batch_tune");
+    b->order = best_order;
+    b->grid = best_grid;
+    e = batch_upload_queue(b, stream);
+    if (e == cudaSuccess) e = batch_build_graph(b);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_check(e, "bf_batch_tune");
+    if (grid_out) *grid_out = best_grid;
+    if (order_out) *order_out = best_order;
+    if (ms_out) *ms_out = best;
+    return BF_OK;
+}

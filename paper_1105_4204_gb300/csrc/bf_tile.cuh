@@ -128,21 +128,34 @@ struct TileParams {
     BfTaps taps;
 };
 
+// Everything one tile needs: the image, its term table and taps, the tile
+// origin.  The term and tap arrays may live in kernel parameter space or in
+// global memory.
+struct TileJob {
+    const void *in;
+    float *out;
+    float *q_out;
+    long long in_row_stride;
+    int H, W, C, ch, dtype;
+    float q_scale;
+    const float *a;
+    const float *t;
+    int n_terms;
+    const float *w;
+    int x0, y0;
+};
+
 template <int KIND, int RAD, int TH, int TW, int TWT>
-__global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT)
-    bf_tile_fwd(const __grid_constant__ TileParams p) {
+__device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
     using G = TileGeom<KIND, RAD, TH, TW, TWT>;
     constexpr int HALO = G::HALO, EH = G::EH, EW = G::EW;
-    extern __shared__ float4 smem4[];
-    float *Fs = reinterpret_cast<float *>(smem4);
+    float *Fs = smem;
     float *V = Fs + G::F_FLOATS;
     float *Cc = V + G::V_FLOATS;
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TW;
-    const int y0 = blockIdx.y * TH;
-    const int ch = blockIdx.z;
-    const int H = p.img.H, W = p.img.W, C = p.img.C;
+    const int x0 = jb.x0, y0 = jb.y0, ch = jb.ch;
+    const int H = jb.H, W = jb.W, C = jb.C;
 
     // ---- tile + halo of f, clamp-to-edge, converted to float
     for (int idx = tid; idx < EH * EW; idx += G::NT) {
@@ -150,12 +163,12 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT)
         const int j = idx - i * EW;
         const int gy = min(max(y0 - HALO + i, 0), H - 1);
         const int gx = min(max(x0 - HALO + j, 0), W - 1);
-        const long long off = (long long)gy * p.img.in_row_stride + (long long)gx * C + ch;
+        const long long off = (long long)gy * jb.in_row_stride + (long long)gx * C + ch;
         float v;
-        if (p.img.dtype == 0)
-            v = __ldg(reinterpret_cast<const float *>(p.img.in) + off);
+        if (jb.dtype == 0)
+            v = __ldg(reinterpret_cast<const float *>(jb.in) + off);
         else
-            v = (float)__ldg(reinterpret_cast<const uint8_t *>(p.img.in) + off);
+            v = (float)__ldg(reinterpret_cast<const uint8_t *>(jb.in) + off);
         Fs[i * G::SF + j] = v;
     }
 
@@ -168,11 +181,11 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT)
 #pragma unroll
     for (int k = 0; k < TWT; ++k) acc[k] = 0.f;
 
-    const int n_terms = p.terms.n_terms;
+    const int n_terms = jb.n_terms;
     for (int m = 0; m < n_terms; ++m) {
         __syncthreads();
-        const float am = p.terms.a[m];
-        const float tm = p.terms.t[m];
+        const float am = jb.a[m];
+        const float tm = jb.t[m];
         // ---- phase 1: vertical filtering of the four auxiliary images
         for (int item = tid; item < 2 * EW; item += G::NT) {
             const int q = item >= EW ? 1 : 0;  // 0: cos, 1: sin
@@ -187,13 +200,13 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT)
                 for (int i = 0; i < TH; ++i) cdst[i * G::SC] = am * x[i + HALO];
             }
             float y[TH];
-            Filt<KIND, RAD, EH>::run(x, y, p.taps.w);
+            Filt<KIND, RAD, EH>::run(x, y, jb.w);
             float *vdst = V + q * TH * G::SV + j;
 #pragma unroll
             for (int i = 0; i < TH; ++i) vdst[i * G::SV] = y[i];
 #pragma unroll
             for (int i = 0; i < EH; ++i) x[i] *= Fs[i * G::SF + j];
-            Filt<KIND, RAD, EH>::run(x, y, p.taps.w);
+            Filt<KIND, RAD, EH>::run(x, y, jb.w);
             vdst += 2 * TH * G::SV;
 #pragma unroll
             for (int i = 0; i < TH; ++i) vdst[i * G::SV] = y[i];
@@ -218,7 +231,7 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT)
 #pragma unroll
             for (int k = 0; k < G::LN; ++k) yin[k] = yv[k];
             float z[TWT];
-            Filt<KIND, RAD, G::LN>::run(yin, z, p.taps.w);
+            Filt<KIND, RAD, G::LN>::run(yin, z, jb.w);
             const float4 *cs =
                 reinterpret_cast<const float4 *>(Cc + qq * TH * G::SC + pi * G::SC + ps * TWT);
 #pragma unroll
@@ -249,12 +262,36 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT)
                 if (gx < W) {
                     const float qv = Xq[pi * G::SV + ps * TWT + k];
                     const long long o = ((long long)gy * W + gx) * C + ch;
-                    p.img.out[o] = acc[k] / qv;
-                    if (p.img.q_out) p.img.q_out[o] = qv * p.img.q_scale;
+                    jb.out[o] = acc[k] / qv;
+                    if (jb.q_out) jb.q_out[o] = qv * jb.q_scale;
                 }
             }
         }
     }
+}
+
+template <int KIND, int RAD, int TH, int TW, int TWT>
+__global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT)
+    bf_tile_fwd(const __grid_constant__ TileParams p) {
+    extern __shared__ float4 smem4[];
+    TileJob jb;
+    jb.in = p.img.in;
+    jb.out = p.img.out;
+    jb.q_out = p.img.q_out;
+    jb.in_row_stride = p.img.in_row_stride;
+    jb.H = p.img.H;
+    jb.W = p.img.W;
+    jb.C = p.img.C;
+    jb.ch = blockIdx.z;
+    jb.dtype = p.img.dtype;
+    jb.q_scale = p.img.q_scale;
+    jb.a = p.terms.a;
+    jb.t = p.terms.t;
+    jb.n_terms = p.terms.n_terms;
+    jb.w = p.taps.w;
+    jb.x0 = blockIdx.x * TW;
+    jb.y0 = blockIdx.y * TH;
+    tile_body<KIND, RAD, TH, TW, TWT>(jb, reinterpret_cast<float *>(smem4));
 }
 
 // Host-side launcher for one instantiation.

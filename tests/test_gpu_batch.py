@@ -1,0 +1,111 @@
+"""GPU parity of the batched persistent launch: every image against the
+single-image fused path (bit-for-bit where both run the same tile body,
+r <= 8) and against the FP64 oracle on sampled pixels."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 0.05
+
+
+@pytest.fixture(scope="module")
+def bf():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_4204_gb300 import build
+    build.build()
+    import paper_1105_4204_gb300 as pkg
+    return pkg
+
+
+def _setup(bf, specs, seed):
+    import torch
+    imgs = synth.batch_images(specs, noise=10.0, seed=seed)
+    plans = [bf.Plan(ss, sr, 255.0, kind="box") for (_, _, ss, sr) in specs]
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.empty_like(t) for t in ins]
+    b = bf.Batch(plans, [(h, w) for (h, w, _, _) in specs])
+    b.bind(ins, outs)
+    return imgs, plans, ins, outs, b
+
+
+def test_small_batch_against_single_and_oracle(bf, oracle):
+    import torch
+    specs = synth.batch_specs(12, seed=7, w_range=(40, 300), h_range=(30, 200))
+    imgs, plans, ins, outs, b = _setup(bf, specs, seed=7)
+    b.forward()
+    assert b.check() == 0
+    for i, (h, w, ss, sr) in enumerate(specs):
+        got = outs[i].cpu().numpy()
+        single = bf.forward(plans[i], ins[i]).cpu().numpy()
+        r = plans[i].radius // 3
+        if r <= 8:
+            np.testing.assert_array_equal(got, single)
+        else:
+            # r > 8: the single-image path runs the streaming sweeps, a different
+            # FP32 summation order; both are held to the oracle below, and to
+            # each other within a fifth of the oracle tolerance
+            assert np.abs(got - single).max() <= TOL / 5
+        idx = synth.sample_indices(h, w, 300, seed=i)
+        w1 = oracle.spatial_w1("box", ss)
+        ref = oracle.bf_brute_at(imgs[i].astype(np.float64), idx, sigma_r=sr, w1=w1, N=plans[i].N)
+        assert np.abs(got.ravel()[idx] - ref).max() <= TOL, (i, r, plans[i].N)
+
+
+def test_config4_batch_matches_single_image_path(bf, oracle):
+    # 64 images, W ~ U[128, 1920], H ~ U[128, 1080], sigma_s ~ U[2, 16],
+    # sigma_r ~ U[15, 60]; rectangles + noise 10
+    import torch
+    specs = synth.batch_specs(64, seed=0)
+    imgs, plans, ins, outs, b = _setup(bf, specs, seed=0)
+    Ns = sorted(p.N for p in plans)
+    assert Ns[0] >= 8 and Ns[-1] <= 118
+    b.forward()
+    torch.cuda.synchronize()
+    assert b.check() == 0
+    worst = 0.0
+    for i, (h, w, ss, sr) in enumerate(specs):
+        got = outs[i]
+        single = bf.forward(plans[i], ins[i])
+        worst = max(worst, float((got - single).abs().max()))
+        if i % 16 == 0:  # oracle on a sample of a few images
+            idx = synth.sample_indices(h, w, 64, seed=i, border=False)
+            ref = oracle.bf_brute_at(imgs[i].astype(np.float64), idx, sigma_r=sr,
+                                     w1=oracle.spatial_w1("box", ss), N=plans[i].N)
+            assert np.abs(got.cpu().numpy().ravel()[idx] - ref).max() <= TOL
+    assert worst <= TOL / 5
+
+
+def test_replay_tune_and_rebind(bf):
+    import torch
+    specs = synth.batch_specs(10, seed=3, w_range=(64, 256), h_range=(64, 256))
+    imgs, plans, ins, outs, b = _setup(bf, specs, seed=3)
+    b.forward()
+    first = [o.clone() for o in outs]
+    info = b.tune(reps=2)
+    assert info["grid"] >= 1 and info["ms"] > 0
+    for o in outs:
+        o.zero_()
+    b.forward()
+    b.forward()  # replays are idempotent
+    assert b.check() == 0
+    for a, c in zip(first, outs):
+        torch.testing.assert_close(a, c, rtol=0, atol=0)
+    # rebinding to new buffers
+    outs2 = [torch.empty_like(t) for t in ins]
+    b.bind(ins, outs2)
+    b.forward()
+    torch.cuda.synchronize()
+    for a, c in zip(first, outs2):
+        torch.testing.assert_close(a, c, rtol=0, atol=0)
+
+
+def test_batch_rejects_unsupported_plans(bf):
+    from paper_1105_4204_gb300._lib import BfError
+    with pytest.raises(BfError):
+        bf.Batch([bf.Plan(3.0, 30.0, kind="gauss")], [(32, 32)])
+    with pytest.raises(BfError):
+        bf.Batch([bf.Plan(20.0, 30.0, kind="box")], [(32, 32)])  # r = 20 > 16
