@@ -183,6 +183,34 @@ bf_status bf_backward(const bf_plan *plan, const float *f, const float *out,
                       size_t workspace_bytes, cudaStream_t stream);
 
 /*
+ * bf_backward for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this is a deployment variant of the adjoint above.  Some
+ * callers cannot call cudaMalloc: code in a real-time loop, where an
+ * allocation may synchronise the device and stall the frame; applications
+ * whose memory pool is sized once at start-up and must not grow; plug-in
+ * hosts (image editors, game engines) that own every device allocation and
+ * hand the plug-in only its input and output buffers.  This entry point takes
+ * the same arguments and gives the same results as bf_backward without the
+ * workspace: the per-block partial sums of dL/dsigma_r go to a fixed array of
+ * 16384 doubles (128 KiB) that is part of the library and stays resident on
+ * every GPU that loads it until the process exits.
+ *   Limit: with grad_sigma_r not NULL, ceil(W/64) * ceil(H/32) <= 16384
+ *          (every image up to 4096 x 4096 fits); larger images return
+ *          BF_EUNSUPPORTED with a message naming the limit.  With
+ *          grad_sigma_r NULL no scratch is used and there is no limit.
+ *   The first call on a device asks the runtime for the array's device
+ *   address and caches it; make that first call before any stream capture.
+ *   All calls share the array.  Each call writes every partial it reads
+ *   before reading it, so nothing has to be cleared between calls, but calls
+ *   whose work overlaps on the GPU (other streams, other host threads) race
+ *   on the array: serialise them.
+ *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ */
+bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, const float *out,
+                              const float *q, const float *grad_out, float *grad_in,
+                              double *grad_sigma_r, int H, int W, cudaStream_t stream);
+
+/*
  * Batched forward: many f32 single-channel images of uneven sizes, each with
  * its own plan (own sigma_s, sigma_r and hence N), in ONE persistent launch
  * that pulls tiles from a device work queue, largest cost first.  The launch
