@@ -5,8 +5,9 @@
 // images passing through device memory once (small enough to stay in L2
 // between the two sweeps for images up to about 2048 x 2048):
 //
-//   lr_vert : one thread per image column and plane, walking down a band of
-//             rows (f loaded a few rows ahead).  The four auxiliary
+//   lr_vert : one thread per image column and term (four terms per block,
+//             sharing a ring of f), walking down a band of rows (f loaded a
+//             few rows ahead).  The four auxiliary
 //             images of the term (cos, sin, f cos, f sin of omega f,
 //             Section 2.3) are generated on the fly and filtered by the three
 //             cascaded boxes with running sums; written transposed
@@ -38,9 +39,6 @@ namespace bf {
 
 namespace {
 
-constexpr int kLvCols = 32;   // columns per lr_vert block; one warp per plane
-constexpr int kLvStage = 8;   // lr_vert: output rows staged before a transposed flush
-constexpr int kLhRows = 32;   // rows per lr_horz block; one warp per plane
 
 struct LrParams {
     const void *in;
@@ -48,9 +46,14 @@ struct LrParams {
     int dtype, C, ch;
     int H, W, r;
     int band_h, band_w;
-    float a, t;           // weight and turns per gray level of this term
-    float *Vt;            // [4][W][H]: vertically filtered planes, column-major
-    float *Acc;           // [4][W][H]: sum over terms of a cos|sin(w f(x)) W[plane](x)
+    float a, t;           // lr_horz: weight and turns per gray level of its term
+    int slot;             // lr_horz: which of lr_vert's term slots it reads
+    int n_terms;          // lr_vert: terms in this group (<= 4)
+    float tv[4];          // lr_vert: turns per gray level of the group's terms
+    int Hp;               // column length of the column-major arrays (H rounded up to 8)
+    float *Vt;            // [4 terms][4 planes][W][Hp]: vertically filtered planes, column-major
+    float *Acc;           // [4][W][Hp]: sum over terms of a cos|sin(w f(x)) W[plane](x)
+    float *ft;            // [W][Hp]: the channel's f, column-major
     int first;
 };
 
@@ -60,30 +63,15 @@ __device__ __forceinline__ float load_f(const LrParams &p, int y, int x) {
     return (float)__ldg(reinterpret_cast<const uint8_t *>(p.in) + off);
 }
 
-// Plane q of the auxiliary images at one pixel value fv:
-// q = 0: cos, 1: sin, 2: f cos, 3: f sin (cos(t) = sin(t + quarter turn)).
-__device__ __forceinline__ float aux_plane(int q, float tm, float fv) {
-    const float v = sin_turns(fmaf(tm, fv, (q & 1) ? 0.f : 0.25f));
-    return q >= 2 ? v * fv : v;
+// Power-of-two size of lr_vert's shared f ring: the 3L + 1 values a stream
+// needs, plus slack for the warps sharing it to be up to two chunks apart
+// (they meet at a barrier every chunk) without overwriting a value another
+// warp still has to read.
+__host__ __device__ __forceinline__ int ring_size(int r) {
+    int n = 1;
+    while (n < 3 * (2 * r + 1) + 1 + 16) n <<= 1;
+    return n;
 }
-
-// Ring of the last 3L + 1 input values of one running-sum stream per thread,
-// in shared memory, [slot][lane] so that a warp's accesses are conflict-free.
-struct Ring {
-    float *base;
-    int n;      // slots (3L + 1)
-    int head;   // slot of the newest value
-    __device__ __forceinline__ void push(float v, int lane) {
-        head = head + 1 == n ? 0 : head + 1;
-        base[head * 32 + lane] = v;
-    }
-    // value k*L positions behind the newest (k = 1..3)
-    __device__ __forceinline__ float back(int off, int lane) const {
-        int s = head - off;
-        s = s < 0 ? s + n : s;
-        return base[s * 32 + lane];
-    }
-};
 
 template <int DT>
 __device__ __forceinline__ float load_px(const LrParams &p, int y, int x) {
@@ -92,63 +80,115 @@ __device__ __forceinline__ float load_px(const LrParams &p, int y, int x) {
     else return (float)__ldg(reinterpret_cast<const uint8_t *>(p.in) + off);
 }
 
-constexpr int kChunk = 16;  // steps whose global loads are issued together
+constexpr int kVCols = 64;    // lr_vert: columns per block
+constexpr int kVG = 4;        // lr_vert: terms per block (they share the f ring)
+constexpr int kChunk = 8;     // lr_vert: steps between barriers / whose loads are issued together
+constexpr int kChunkH = 16;   // lr_horz: steps whose loads are issued together, one chunk ahead
 
-// grid: (ceil(W / kLvCols), bands); block: 4 warps (warp q = plane q), lanes =
-// columns.  Dynamic smem: one ring of 3L + 1 generated values per thread.
+// The four auxiliary planes of one pixel value (cos, sin, f cos, f sin).
+__device__ __forceinline__ void aux4(float tm, float fv, float (&x)[4]) {
+    float r = tm * fv;
+    r = r - rintf(r);
+    float sn, cs;
+    __sincosf(kTwoPi * r, &sn, &cs);
+    x[0] = cs;
+    x[1] = sn;
+    x[2] = fv * cs;
+    x[3] = fv * sn;
+}
+
+// grid: (ceil(W / kVCols), bands); block: kVCols x kVG threads, thread
+// (column, term g) computes the four planes of term g for one column.  The
+// kVG terms share one ring of the last ring_size(r) values of f per column
+// (every thread writes the same value into it; a barrier per chunk keeps the
+// warps within kChunk steps of each other, far less than the ring's slack).
+// Dynamic smem: the f ring, then an 8-row output stage per thread and plane.
 template <int DT>
-__global__ void __launch_bounds__(4 * kLvCols) lr_vert(const __grid_constant__ LrParams p) {
+__global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ LrParams p) {
     extern __shared__ float lv_sm[];
-    const int lane = threadIdx.x & 31;
-    const int q = threadIdx.x >> 5;
-    const int xb = blockIdx.x * kLvCols;
-    const int xc = min(xb + lane, p.W - 1);
-    const float tm = p.t;
+    const int tid = threadIdx.x;
+    const int col = tid % kVCols;
+    const int g = tid / kVCols;
+    const int xb = blockIdx.x * kVCols;
+    const int xc = min(xb + col, p.W - 1);
+    const bool term_ok = g < p.n_terms;
+    const float tm = p.tv[g];
     const int y0 = blockIdx.y * p.band_h;
     const int y1 = min(y0 + p.band_h, p.H);
     const int r = p.r, L = 2 * r + 1;
-    const int p0 = y0 - 3 * r;  // first position whose input is taken as real
+    const int p0 = y0 - 3 * r;  // inputs before p0 count as zero
     const int e_end = y1 + 3 * r;
-    Ring ring{lv_sm + (size_t)q * (3 * L + 1) * 32, 3 * L + 1, 0};
-    for (int k = 0; k < ring.n; ++k) ring.base[k * 32 + lane] = 0.f;  // zero input before p0
-    float s1a = 0.f, s1b = 0.f, s1c = 0.f, s2a = 0.f, s2b = 0.f, s3 = 0.f;
-    float *dst_col = p.Vt + (size_t)q * p.W * p.H + (size_t)(xb + lane) * p.H;
-    const bool col_ok = xb + lane < p.W;
-    float stage[kLvStage];
-    // f of the next chunk of rows is loaded while the current one is used
+    const int RS = ring_size(r), M = RS - 1;
+    float *ring = lv_sm + col;                             // slot k at ring[k * kVCols]
+    float *stage = lv_sm + RS * kVCols + tid;              // [plane * 8 + row] at stage[i * blockDim]
+    const bool col_ok = xb + col < p.W && term_ok;
+    const size_t plane = (size_t)p.W * p.Hp;
+    float *dst = p.Vt + (size_t)g * 4 * plane + (size_t)(xb + col) * p.Hp;
+    float s1[4][3], s2[4][2], s3[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        s1[q][0] = s1[q][1] = s1[q][2] = 0.f;
+        s2[q][0] = s2[q][1] = 0.f;
+        s3[q] = 0.f;
+    }
     float cur[kChunk], nxt[kChunk];
 #pragma unroll
     for (int d = 0; d < kChunk; ++d) cur[d] = load_px<DT>(p, min(max(p0 + d, 0), p.H - 1), xc);
     for (int e0 = p0; e0 < e_end; e0 += kChunk) {
+        __syncthreads();  // bounds the skew between the warps sharing the ring
 #pragma unroll
         for (int d = 0; d < kChunk; ++d)
             nxt[d] = load_px<DT>(p, min(max(e0 + kChunk + d, 0), p.H - 1), xc);
 #pragma unroll
         for (int d = 0; d < kChunk; ++d) {
             const int e = e0 + d;
-            if (e < e_end) {
-                const float x0 = aux_plane(q, tm, cur[d]);
-                const float x1 = ring.back(L - 1, lane);      // position e - L
-                const float x2 = ring.back(2 * L - 1, lane);  // e - 2L
-                const float x3 = ring.back(3 * L - 1, lane);  // e - 3L
-                ring.push(x0, lane);
-                s1a += x0 - x1;
-                s1b += x1 - x2;
-                s1c += x2 - x3;
-                s2a += s1a - s1b;
-                s2b += s1b - s1c;
-                s3 += s2a - s2b;
-                const int t = e - 3 * r;  // output row of this step
-                if (t >= y0) {
-                    const int j = (t - y0) & (kLvStage - 1);
+            if (e >= e_end) break;
+            const float fv = cur[d];
+            ring[(e & M) * kVCols] = fv;
+            float x0[4], x1[4], x2[4], x3[4];
+            aux4(tm, fv, x0);
+            if (e >= p0 + 3 * L) {  // uniform: every trailing position is real
+                aux4(tm, ring[((e - L) & M) * kVCols], x1);
+                aux4(tm, ring[((e - 2 * L) & M) * kVCols], x2);
+                aux4(tm, ring[((e - 3 * L) & M) * kVCols], x3);
+            } else {
 #pragma unroll
-                    for (int jj = 0; jj < kLvStage; ++jj)
-                        if (jj == j) stage[jj] = s3;
-                    if ((j == kLvStage - 1 || t == y1 - 1) && col_ok) {
-                        const int yb = t - j;
+                for (int q = 0; q < 4; ++q) x1[q] = x2[q] = x3[q] = 0.f;
+                if (e >= p0 + L) aux4(tm, ring[((e - L) & M) * kVCols], x1);
+                if (e >= p0 + 2 * L) aux4(tm, ring[((e - 2 * L) & M) * kVCols], x2);
+            }
 #pragma unroll
-                        for (int jj = 0; jj < kLvStage; ++jj)
-                            if (jj <= j) dst_col[yb + jj] = stage[jj];
+            for (int q = 0; q < 4; ++q) {
+                s1[q][0] += x0[q] - x1[q];
+                s1[q][1] += x1[q] - x2[q];
+                s1[q][2] += x2[q] - x3[q];
+                s2[q][0] += s1[q][0] - s1[q][1];
+                s2[q][1] += s1[q][1] - s1[q][2];
+                s3[q] += s2[q][0] - s2[q][1];
+            }
+            const int t = e - 3 * r;  // output row of this step
+            if (t >= y0) {
+                const int j = (t - y0) & 7;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) stage[(q * 8 + j) * (kVCols * kVG)] = s3[q];
+                if (col_ok && (j == 7 || t == y1 - 1)) {
+                    const int yb = t - j;  // a multiple of 8: bands start at multiples of 8
+                    if (j == 7) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float *sq = stage + q * 8 * (kVCols * kVG);
+                            float4 lo = make_float4(sq[0], sq[kVCols * kVG], sq[2 * kVCols * kVG],
+                                                    sq[3 * kVCols * kVG]);
+                            float4 hi = make_float4(sq[4 * kVCols * kVG], sq[5 * kVCols * kVG],
+                                                    sq[6 * kVCols * kVG], sq[7 * kVCols * kVG]);
+                            float4 *d4 = reinterpret_cast<float4 *>(dst + q * plane + yb);
+                            d4[0] = lo;
+                            d4[1] = hi;
+                        }
+                    } else {
+                        for (int q = 0; q < 4; ++q)
+                            for (int jj = 0; jj <= j; ++jj)
+                                dst[q * plane + yb + jj] = stage[(q * 8 + jj) * (kVCols * kVG)];
                     }
                 }
             }
@@ -158,68 +198,103 @@ __global__ void __launch_bounds__(4 * kLvCols) lr_vert(const __grid_constant__ L
     }
 }
 
-// grid: (ceil(H / kLhRows), bands along x); block: 4 warps (warp q = plane q),
-// lanes = rows.  Dynamic smem: one ring of 3L + 1 values per thread.
+// grid: (ceil(H / 32), bands along x, 4 planes); block: one warp, lanes =
+// rows.  Dynamic smem: a ring of exactly 3L + 1 values per thread.
+// f of one channel, row-major -> column-major (32 x 33 shared tile).
+// grid: (ceil(W / 32), ceil(H / 32)); block: (32, 8)
 template <int DT>
-__global__ void __launch_bounds__(4 * kLhRows) lr_horz(const __grid_constant__ LrParams p) {
+__global__ void lr_transpose(const __grid_constant__ LrParams p) {
+    __shared__ float tile[32][33];
+    const int xb = blockIdx.x * 32, yb = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int y = yb + i, x = xb + threadIdx.x;
+        if (x < p.W && y < p.H) tile[i][threadIdx.x] = load_px<DT>(p, y, x);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int x = xb + i, y = yb + threadIdx.x;
+        if (x < p.W && y < p.H) p.ft[(size_t)x * p.Hp + y] = tile[threadIdx.x][i];
+    }
+}
+
+// grid: (ceil(H / 32), bands along x, 4 planes); block: one warp, lanes =
+// rows.  Dynamic smem: a ring of exactly 3L + 1 values per thread.
+__global__ void __launch_bounds__(32) lr_horz(const __grid_constant__ LrParams p) {
     extern __shared__ float lh_sm[];
-    const int lane = threadIdx.x & 31;
-    const int q = threadIdx.x >> 5;
-    const int y = blockIdx.x * kLhRows + lane;
+    const int lane = threadIdx.x;
+    const int q = blockIdx.z;
+    const int y = blockIdx.x * 32 + lane;
     const int yc = min(y, p.H - 1);
     const int x0 = blockIdx.y * p.band_w;
     const int x1 = min(x0 + p.band_w, p.W);
     const int r = p.r, L = 2 * r + 1;
     const int p0 = x0 - 3 * r;
-    const size_t plane = (size_t)p.W * p.H;
-    const float *V = p.Vt + q * plane + yc;
-    float *A = p.Acc + q * plane;
+    const int RN = 3 * L + 1;
+    float *ring = lh_sm + lane;  // slot k at ring[k * 32]
+    const size_t plane = (size_t)p.W * p.Hp;
+    const float *V = p.Vt + (size_t)p.slot * 4 * plane + q * plane + yc;
+    const float *F = p.ft + yc;
+    float *A = p.Acc + q * plane + yc;
     const int e_end = x1 + 3 * r;
-    Ring ring{lh_sm + (size_t)q * (3 * L + 1) * 32, 3 * L + 1, 0};
-    for (int k = 0; k < ring.n; ++k) ring.base[k * 32 + lane] = 0.f;
-    float s1a = 0.f, s1b = 0.f, s1c = 0.f, s2a = 0.f, s2b = 0.f, s3 = 0.f;
     const float ph0 = (q & 1) ? 0.f : 0.25f;  // cos for planes 0 and 2, sin for 1 and 3
-    // the plane at the positions of the next chunk, and the pixel values and
-    // running accumulators of the chunk's outputs, loaded one chunk ahead
-    float cv[kChunk], cf[kChunk], ca[kChunk];
-    float nv[kChunk], nf[kChunk], na[kChunk];
-    auto fetch = [&](int eb, float (&v)[kChunk], float (&f)[kChunk], float (&a)[kChunk]) {
+    const float am = p.a, tm = p.t;
+    const bool row_ok = y < p.H;
+    const bool first = p.first;
+    float s1a = 0.f, s1b = 0.f, s1c = 0.f, s2a = 0.f, s2b = 0.f, s3 = 0.f;
+    // ring slots of positions e, e - L, e - 2L, e - 3L, advanced with wrap
+    int h0 = 0, h1 = RN - L, h2 = RN - 2 * L, h3 = RN - 3 * L;
+    float cv[kChunkH], cf[kChunkH], ca[kChunkH], nv[kChunkH], nf[kChunkH], na[kChunkH];
+    // loads of a chunk: the plane at its positions, and at its outputs the
+    // pixel value and this plane's running accumulator (all column-major,
+    // consecutive lanes read consecutive rows)
+    auto fetch = [&](int eb, float (&v)[kChunkH], float (&f)[kChunkH], float (&a)[kChunkH]) {
 #pragma unroll
-        for (int d = 0; d < kChunk; ++d) {
+        for (int d = 0; d < kChunkH; ++d) {
             const int e = eb + d;
-            v[d] = __ldg(V + (size_t)min(max(e, 0), p.W - 1) * p.H);
-            const int t = min(max(e - 3 * r, 0), p.W - 1);
-            f[d] = load_px<DT>(p, yc, t);
-            a[d] = p.first ? 0.f : A[(size_t)t * p.H + yc];
+            v[d] = __ldg(V + (size_t)min(max(e, 0), p.W - 1) * p.Hp);
+            const size_t t = (size_t)min(max(e - 3 * r, 0), p.W - 1) * p.Hp;
+            f[d] = __ldg(F + t);
+            a[d] = first ? 0.f : A[t];
         }
     };
     fetch(p0, cv, cf, ca);
-    for (int e0 = p0; e0 < e_end; e0 += kChunk) {
-        fetch(e0 + kChunk, nv, nf, na);
+    for (int e0 = p0; e0 < e_end; e0 += kChunkH) {
+        fetch(e0 + kChunkH, nv, nf, na);
+        const bool steady = e0 >= p0 + 3 * L && e0 + kChunkH <= e_end;  // uniform
 #pragma unroll
-        for (int d = 0; d < kChunk; ++d) {
+        for (int d = 0; d < kChunkH; ++d) {
             const int e = e0 + d;
-            if (e < e_end) {
-                const float xin = cv[d];
-                const float x1v = ring.back(L - 1, lane);
-                const float x2v = ring.back(2 * L - 1, lane);
-                const float x3v = ring.back(3 * L - 1, lane);
-                ring.push(xin, lane);
-                s1a += xin - x1v;
-                s1b += x1v - x2v;
-                s1c += x2v - x3v;
-                s2a += s1a - s1b;
-                s2b += s1b - s1c;
-                s3 += s2a - s2b;
-                const int t = e - 3 * r;  // output column of this step
-                if (t >= x0 && y < p.H) {
-                    const float coef = p.a * sin_turns(fmaf(p.t, cf[d], ph0));
-                    A[(size_t)t * p.H + y] = fmaf(coef, s3, ca[d]);
-                }
+            if (!steady && e >= e_end) break;
+            const float xin = cv[d];
+            ring[h0 * 32] = xin;
+            float x1v, x2v, x3v;
+            if (steady) {
+                x1v = ring[h1 * 32];
+                x2v = ring[h2 * 32];
+                x3v = ring[h3 * 32];
+            } else {
+                x1v = e >= p0 + L ? ring[h1 * 32] : 0.f;
+                x2v = e >= p0 + 2 * L ? ring[h2 * 32] : 0.f;
+                x3v = e >= p0 + 3 * L ? ring[h3 * 32] : 0.f;
+            }
+            h0 = h0 + 1 == RN ? 0 : h0 + 1;
+            h1 = h1 + 1 == RN ? 0 : h1 + 1;
+            h2 = h2 + 1 == RN ? 0 : h2 + 1;
+            h3 = h3 + 1 == RN ? 0 : h3 + 1;
+            s1a += xin - x1v;
+            s1b += x1v - x2v;
+            s1c += x2v - x3v;
+            s2a += s1a - s1b;
+            s2b += s1b - s1c;
+            s3 += s2a - s2b;
+            const int t = e - 3 * r;  // output column of this step
+            if (t >= x0 && row_ok) {
+                const float coef = am * sin_turns(fmaf(tm, cf[d], ph0));
+                A[(size_t)t * p.Hp] = fmaf(coef, s3, ca[d]);
             }
         }
 #pragma unroll
-        for (int d = 0; d < kChunk; ++d) {
+        for (int d = 0; d < kChunkH; ++d) {
             cv[d] = nv[d];
             cf[d] = nf[d];
             ca[d] = na[d];
@@ -231,15 +306,16 @@ __global__ void __launch_bounds__(4 * kLhRows) lr_horz(const __grid_constant__ L
 // cos, sin planes), column-major -> row-major through a 32 x 33 shared tile.
 // grid: (ceil(W / 32), ceil(H / 32)); block: (32, 8)
 __global__ void lr_final(const float *__restrict__ Acc, float *__restrict__ out,
-                         float *__restrict__ q_out, int H, int W, int C, int ch, float q_scale) {
+                         float *__restrict__ q_out, int H, int W, int Hp, int C, int ch,
+                         float q_scale) {
     __shared__ float tp[32][33];
     __shared__ float tq[32][33];
-    const size_t plane = (size_t)W * H;
+    const size_t plane = (size_t)W * Hp;
     const int xb = blockIdx.x * 32, yb = blockIdx.y * 32;
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int x = xb + i, y = yb + threadIdx.x;
         if (x < W && y < H) {
-            const size_t o = (size_t)x * H + y;
+            const size_t o = (size_t)x * Hp + y;
             tq[i][threadIdx.x] = Acc[o] + Acc[plane + o];
             tp[i][threadIdx.x] = Acc[2 * plane + o] + Acc[3 * plane + o];
         }
@@ -259,57 +335,71 @@ __global__ void lr_final(const float *__restrict__ Acc, float *__restrict__ out,
 }  // namespace
 
 size_t large_workspace(int H, int W) {
-    return (size_t)8 * (size_t)H * (size_t)W * sizeof(float) + 256;
+    const size_t Hp = ((size_t)H + 7) / 8 * 8;
+    return (size_t)(4 * kVG + 5) * Hp * (size_t)W * sizeof(float) + 256;
 }
 
 cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cudaStream_t s) {
     const int H = img.H, W = img.W;
     char *base = reinterpret_cast<char *>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    LrParams p;
+    LrParams p{};
     p.in = img.in;
     p.in_stride = img.in_row_stride;
     p.dtype = img.dtype;
     p.C = img.C;
     p.H = H;
     p.W = W;
+    p.Hp = (H + 7) / 8 * 8;
     p.r = pl->r_box;
     p.Vt = reinterpret_cast<float *>(base);
-    p.Acc = p.Vt + (size_t)4 * H * W;
-    // bands: long enough to amortise the 6r warm-up, short enough to fill the GPU
+    p.Acc = p.Vt + (size_t)4 * kVG * p.Hp * W;
+    p.ft = p.Acc + (size_t)4 * p.Hp * W;
+    // bands (multiples of 8 rows): long enough to amortise the 6r warm-up,
+    // short enough to fill the GPU
     p.band_h = std::max(256, 8 * p.r);
     p.band_w = std::max(256, 8 * p.r);
     const int nbh = (H + p.band_h - 1) / p.band_h;
     const int nbw = (W + p.band_w - 1) / p.band_w;
-    // one ring of 3L + 1 values per thread, 128 threads per block
-    const size_t sm_ring = sizeof(float) * (size_t)4 * 32 * (3 * (2 * p.r + 1) + 1);
-    if (sm_ring > 227 * 1024) return cudaErrorInvalidValue;
+    const int RS = ring_size(p.r);
+    const size_t sm_v = sizeof(float) * ((size_t)kVCols * RS + (size_t)kVCols * kVG * 32);
+    const size_t sm_h = sizeof(float) * (size_t)32 * (3 * (2 * p.r + 1) + 1);
+    if (sm_v > 227 * 1024 || sm_h > 227 * 1024) return cudaErrorInvalidValue;
     auto kv = img.dtype == 0 ? lr_vert<0> : lr_vert<1>;
-    auto kh = img.dtype == 0 ? lr_horz<0> : lr_horz<1>;
+    auto kt = img.dtype == 0 ? lr_transpose<0> : lr_transpose<1>;
     static bool attr[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attr[dev]) {
-        for (auto k : {lr_vert<0>, lr_vert<1>, lr_horz<0>, lr_horz<1>}) {
+        for (auto k : {lr_vert<0>, lr_vert<1>}) {
             e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
             if (e != cudaSuccess) return e;
         }
+        e = cudaFuncSetAttribute(lr_horz, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr[dev] = true;
     }
     const int nt = (int)pl->a32.size();
     for (int ch = 0; ch < img.C; ++ch) {
         p.ch = ch;
-        for (int m = 0; m < nt; ++m) {
-            p.a = pl->a32[m];
-            p.t = pl->turns32[m];
-            p.first = m == 0;
-            dim3 gv((W + kLvCols - 1) / kLvCols, nbh);
-            kv<<<gv, 4 * kLvCols, sm_ring, s>>>(p);
-            dim3 gh((H + kLhRows - 1) / kLhRows, nbw);
-            kh<<<gh, 4 * kLhRows, sm_ring, s>>>(p);
+        dim3 gt((W + 31) / 32, (H + 31) / 32);
+        kt<<<gt, dim3(32, 8), 0, s>>>(p);
+        for (int m0 = 0; m0 < nt; m0 += kVG) {
+            p.n_terms = std::min(kVG, nt - m0);
+            for (int g = 0; g < kVG; ++g) p.tv[g] = pl->turns32[std::min(m0 + g, nt - 1)];
+            dim3 gv((W + kVCols - 1) / kVCols, nbh);
+            kv<<<gv, kVCols * kVG, sm_v, s>>>(p);
+            for (int g = 0; g < p.n_terms; ++g) {
+                p.slot = g;
+                p.a = pl->a32[m0 + g];
+                p.t = pl->turns32[m0 + g];
+                p.first = m0 + g == 0;
+                dim3 gh((H + 31) / 32, nbw, 4);
+                lr_horz<<<gh, 32, sm_h, s>>>(p);
+            }
         }
         dim3 gf((W + 31) / 32, (H + 31) / 32);
-        lr_final<<<gf, dim3(32, 8), 0, s>>>(p.Acc, img.out, img.q_out, H, W, img.C, ch,
+        lr_final<<<gf, dim3(32, 8), 0, s>>>(p.Acc, img.out, img.q_out, H, W, p.Hp, img.C, ch,
                                             img.q_scale);
     }
     return cudaGetLastError();
