@@ -195,3 +195,34 @@ def test_config2_full_size_sampled(bf, oracle, sigma_s):
     err = np.abs(out.ravel()[idx] - ref).max()
     print("config2 sigma_s=%g max abs err %.3e on %d px" % (sigma_s, err, len(idx)))
     assert err <= TOL
+
+
+@pytest.mark.parametrize("kind,ss,r", [("box", 2.0, None), ("gauss", 3.0, None), ("box", 8.0, None),
+                                       ("box", 12.0, 12)])
+def test_unfused_baseline_matches_oracle(bf, oracle, kind, ss, r):
+    import torch
+    img = synth.smooth_field(70, 96, noise=5.0, seed=21)
+    plan = bf.Plan(ss, 20.0, kind=kind, radius=r or 0)
+    t = torch.from_numpy(img).cuda()
+    out = bf.forward_unfused(plan, t).cpu().numpy()
+    ref = _oracle_full(oracle, img, plan)
+    assert np.abs(out - ref).max() <= TOL
+    fused = bf.forward(plan, t).cpu().numpy()
+    assert np.abs(out - fused).max() <= TOL / 5
+
+
+def test_row_strips_with_halo_match_full_image(bf):
+    # multi-GPU partitioning: each rank filters its strip plus a read-only halo
+    import torch
+    from paper_1105_4204_gb300 import shard
+    img = synth.rectangles(301, 157, seed=8)
+    t = torch.from_numpy(img).cuda()
+    for kind, ss in [("gauss", 3.0), ("box", 4.0)]:
+        plan = bf.Plan(ss, 25.0, kind=kind)
+        full = bf.forward(plan, t).cpu().numpy()
+        parts = []
+        for st in shard.row_strips(img.shape[0], 3, plan.radius):
+            sub = bf.forward(plan, t[st.r0:st.r1].contiguous()).cpu().numpy()
+            c0, c1 = st.crop
+            parts.append(sub[c0:c1])
+        assert np.abs(np.concatenate(parts) - full).max() <= TOL / 5
