@@ -271,7 +271,7 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
 }
 
 template <int KIND, int RAD, int TH, int TW, int TWT>
-__global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT)
+__global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT, 2)
     bf_tile_fwd(const __grid_constant__ TileParams p) {
     extern __shared__ float4 smem4[];
     TileJob jb;
