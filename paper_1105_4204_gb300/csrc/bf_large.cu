@@ -12,12 +12,12 @@
 //             Section 2.3) are generated on the fly and filtered by the three
 //             cascaded boxes with running sums; written transposed
 //             (column-major) so that the second sweep reads coalesced.
-//   lr_horz : one thread per image row and plane, walking along a band of columns of the
-//             transposed planes (loads issued a few steps ahead): the same
-//             three cascaded boxes horizontally, then the per-pixel combine of
-//             eq. (final-form), accumulated per plane (column-major).
-//   lr_final: out = P / Q, with P and Q the sums of the plane accumulators,
-//             transposed back to row-major.
+//   lr_horz : one thread per image row and plane pair, walking along a band
+//             of columns of the transposed planes (loads issued a chunk
+//             ahead): the same three cascaded boxes horizontally on the
+//             (cos, sin) or the (f cos, f sin) pair, then the per-pixel
+//             combine of eq. (final-form) into Q or P (column-major).
+//   lr_final: out = P / Q, transposed back to row-major.
 //
 // Running sums with one history buffer.  Box k of the cascade at position q
 // needs its input at q + r and q - r - 1.  Keeping one running sum per
@@ -31,6 +31,7 @@
 // at zero 3r positions before the first output with the input taken as zero
 // before that point, so the first 6r steps of a band are warm-up.
 #include <algorithm>
+#include <type_traits>
 
 #include "bf_internal.h"
 #include "bf_tile.cuh"
@@ -52,7 +53,7 @@ struct LrParams {
     float tv[4];          // lr_vert: turns per gray level of the group's terms
     int Hp;               // column length of the column-major arrays (H rounded up to 8)
     float *Vt;            // [4 terms][4 planes][W][Hp]: vertically filtered planes, column-major
-    float *Acc;           // [4][W][Hp]: sum over terms of a cos|sin(w f(x)) W[plane](x)
+    float *Acc;           // [2][W][Hp]: Q and P, column-major
     float *ft;            // [W][Hp]: the channel's f, column-major
     int first;
 };
@@ -102,7 +103,9 @@ __device__ __forceinline__ void aux4(float tm, float fv, float (&x)[4]) {
 // kVG terms share one ring of the last ring_size(r) values of f per column
 // (every thread writes the same value into it; a barrier per chunk keeps the
 // warps within kChunk steps of each other, far less than the ring's slack).
-// Dynamic smem: the f ring, then an 8-row output stage per thread and plane.
+// Chunks are aligned so that step d of a chunk produces output row
+// 8k + d of the band: the eight outputs of a chunk stay in registers and
+// leave as two 16-byte stores per plane.  Dynamic smem: the f ring.
 template <int DT>
 __global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ LrParams p) {
     extern __shared__ float lv_sm[];
@@ -118,9 +121,10 @@ __global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ 
     const int r = p.r, L = 2 * r + 1;
     const int p0 = y0 - 3 * r;  // inputs before p0 count as zero
     const int e_end = y1 + 3 * r;
+    // first step: output row y0 falls on d = 0 of a chunk, and e_s <= p0
+    const int e_s = p0 + 6 * r - kChunk * ((6 * r + kChunk - 1) / kChunk);
     const int RS = ring_size(r), M = RS - 1;
-    float *ring = lv_sm + col;                             // slot k at ring[k * kVCols]
-    float *stage = lv_sm + RS * kVCols + tid;              // [plane * 8 + row] at stage[i * blockDim]
+    float *ring = lv_sm + col;  // slot k at ring[k * kVCols]
     const bool col_ok = xb + col < p.W && term_ok;
     const size_t plane = (size_t)p.W * p.Hp;
     float *dst = p.Vt + (size_t)g * 4 * plane + (size_t)(xb + col) * p.Hp;
@@ -133,64 +137,71 @@ __global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ 
     }
     float cur[kChunk], nxt[kChunk];
 #pragma unroll
-    for (int d = 0; d < kChunk; ++d) cur[d] = load_px<DT>(p, min(max(p0 + d, 0), p.H - 1), xc);
-    for (int e0 = p0; e0 < e_end; e0 += kChunk) {
+    for (int d = 0; d < kChunk; ++d) cur[d] = load_px<DT>(p, min(max(e_s + d, 0), p.H - 1), xc);
+    float st[4][kChunk];
+    // one step; CHECKED covers steps before p0 + 3L (inputs before p0 are
+    // zero) and the band's last chunk
+    auto step = [&](int e, int d, auto checked) {
+        constexpr bool CHECKED = decltype(checked)::value;
+        const float fv = cur[d];
+        ring[(e & M) * kVCols] = fv;
+        float x0[4], x1[4], x2[4], x3[4];
+        aux4(tm, fv, x0);
+        if (!CHECKED) {
+            aux4(tm, ring[((e - L) & M) * kVCols], x1);
+            aux4(tm, ring[((e - 2 * L) & M) * kVCols], x2);
+            aux4(tm, ring[((e - 3 * L) & M) * kVCols], x3);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x1[q] = x2[q] = x3[q] = 0.f;
+            if (e < p0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) x0[q] = 0.f;
+            }
+            if (e >= p0 + L) aux4(tm, ring[((e - L) & M) * kVCols], x1);
+            if (e >= p0 + 2 * L) aux4(tm, ring[((e - 2 * L) & M) * kVCols], x2);
+            if (e >= p0 + 3 * L) aux4(tm, ring[((e - 3 * L) & M) * kVCols], x3);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            s1[q][0] += x0[q] - x1[q];
+            s1[q][1] += x1[q] - x2[q];
+            s1[q][2] += x2[q] - x3[q];
+            s2[q][0] += s1[q][0] - s1[q][1];
+            s2[q][1] += s1[q][1] - s1[q][2];
+            s3[q] += s2[q][0] - s2[q][1];
+            st[q][d] = s3[q];
+        }
+    };
+    for (int e0 = e_s; e0 < e_end; e0 += kChunk) {
         __syncthreads();  // bounds the skew between the warps sharing the ring
 #pragma unroll
         for (int d = 0; d < kChunk; ++d)
             nxt[d] = load_px<DT>(p, min(max(e0 + kChunk + d, 0), p.H - 1), xc);
+        const int tb = e0 - 3 * r;  // output row of step d = 0 (tb - y0 is a multiple of 8)
+        const bool fast = e0 >= p0 + 3 * L && e0 + kChunk <= e_end;  // uniform
+        if (fast) {
 #pragma unroll
-        for (int d = 0; d < kChunk; ++d) {
-            const int e = e0 + d;
-            if (e >= e_end) break;
-            const float fv = cur[d];
-            ring[(e & M) * kVCols] = fv;
-            float x0[4], x1[4], x2[4], x3[4];
-            aux4(tm, fv, x0);
-            if (e >= p0 + 3 * L) {  // uniform: every trailing position is real
-                aux4(tm, ring[((e - L) & M) * kVCols], x1);
-                aux4(tm, ring[((e - 2 * L) & M) * kVCols], x2);
-                aux4(tm, ring[((e - 3 * L) & M) * kVCols], x3);
+            for (int d = 0; d < kChunk; ++d) step(e0 + d, d, std::false_type{});
+        } else {
+#pragma unroll
+            for (int d = 0; d < kChunk; ++d)
+                if (e0 + d < e_end) step(e0 + d, d, std::true_type{});
+        }
+        if (col_ok && tb >= y0) {
+            if (tb + kChunk <= y1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 *d4 = reinterpret_cast<float4 *>(dst + q * plane + tb);
+                    d4[0] = make_float4(st[q][0], st[q][1], st[q][2], st[q][3]);
+                    d4[1] = make_float4(st[q][4], st[q][5], st[q][6], st[q][7]);
+                }
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) x1[q] = x2[q] = x3[q] = 0.f;
-                if (e >= p0 + L) aux4(tm, ring[((e - L) & M) * kVCols], x1);
-                if (e >= p0 + 2 * L) aux4(tm, ring[((e - 2 * L) & M) * kVCols], x2);
-            }
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                s1[q][0] += x0[q] - x1[q];
-                s1[q][1] += x1[q] - x2[q];
-                s1[q][2] += x2[q] - x3[q];
-                s2[q][0] += s1[q][0] - s1[q][1];
-                s2[q][1] += s1[q][1] - s1[q][2];
-                s3[q] += s2[q][0] - s2[q][1];
-            }
-            const int t = e - 3 * r;  // output row of this step
-            if (t >= y0) {
-                const int j = (t - y0) & 7;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) stage[(q * 8 + j) * (kVCols * kVG)] = s3[q];
-                if (col_ok && (j == 7 || t == y1 - 1)) {
-                    const int yb = t - j;  // a multiple of 8: bands start at multiples of 8
-                    if (j == 7) {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float *sq = stage + q * 8 * (kVCols * kVG);
-                            float4 lo = make_float4(sq[0], sq[kVCols * kVG], sq[2 * kVCols * kVG],
-                                                    sq[3 * kVCols * kVG]);
-                            float4 hi = make_float4(sq[4 * kVCols * kVG], sq[5 * kVCols * kVG],
-                                                    sq[6 * kVCols * kVG], sq[7 * kVCols * kVG]);
-                            float4 *d4 = reinterpret_cast<float4 *>(dst + q * plane + yb);
-                            d4[0] = lo;
-                            d4[1] = hi;
-                        }
-                    } else {
-                        for (int q = 0; q < 4; ++q)
-                            for (int jj = 0; jj <= j; ++jj)
-                                dst[q * plane + yb + jj] = stage[(q * 8 + jj) * (kVCols * kVG)];
-                    }
-                }
+                    for (int d = 0; d < kChunk; ++d)
+                        if (tb + d < y1) dst[q * plane + tb + d] = st[q][d];
             }
         }
 #pragma unroll
@@ -198,8 +209,6 @@ __global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ 
     }
 }
 
-// grid: (ceil(H / 32), bands along x, 4 planes); block: one warp, lanes =
-// rows.  Dynamic smem: a ring of exactly 3L + 1 values per thread.
 // f of one channel, row-major -> column-major (32 x 33 shared tile).
 // grid: (ceil(W / 32), ceil(H / 32)); block: (32, 8)
 template <int DT>
@@ -217,12 +226,15 @@ __global__ void lr_transpose(const __grid_constant__ LrParams p) {
     }
 }
 
-// grid: (ceil(H / 32), bands along x, 4 planes); block: one warp, lanes =
-// rows.  Dynamic smem: a ring of exactly 3L + 1 values per thread.
+// grid: (ceil(H / 32), bands along x, 2); block: one warp, lanes = rows.
+// blockIdx.z = 0: the (cos, sin) planes, accumulated into Q;
+// blockIdx.z = 1: the (f cos, f sin) planes, accumulated into P.  Both planes
+// of a pair share the pixel's sincos and one accumulator.
+// Dynamic smem: two rings of exactly 3L + 1 values per thread.
 __global__ void __launch_bounds__(32) lr_horz(const __grid_constant__ LrParams p) {
     extern __shared__ float lh_sm[];
     const int lane = threadIdx.x;
-    const int q = blockIdx.z;
+    const int pr = blockIdx.z;  // 0: Q pair, 1: P pair
     const int y = blockIdx.x * 32 + lane;
     const int yc = min(y, p.H - 1);
     const int x0 = blockIdx.y * p.band_w;
@@ -230,80 +242,107 @@ __global__ void __launch_bounds__(32) lr_horz(const __grid_constant__ LrParams p
     const int r = p.r, L = 2 * r + 1;
     const int p0 = x0 - 3 * r;
     const int RN = 3 * L + 1;
-    float *ring = lh_sm + lane;  // slot k at ring[k * 32]
+    float *ringc = lh_sm + lane;            // slot k at ringc[k * 64]
+    float *rings = lh_sm + 32 + lane;       // interleaved with ringc
     const size_t plane = (size_t)p.W * p.Hp;
-    const float *V = p.Vt + (size_t)p.slot * 4 * plane + q * plane + yc;
+    const float *Vc = p.Vt + (size_t)p.slot * 4 * plane + (size_t)(2 * pr) * plane + yc;
+    const float *Vs = Vc + plane;
     const float *F = p.ft + yc;
-    float *A = p.Acc + q * plane + yc;
+    float *A = p.Acc + (size_t)pr * plane + yc;
     const int e_end = x1 + 3 * r;
-    const float ph0 = (q & 1) ? 0.f : 0.25f;  // cos for planes 0 and 2, sin for 1 and 3
     const float am = p.a, tm = p.t;
     const bool row_ok = y < p.H;
     const bool first = p.first;
-    float s1a = 0.f, s1b = 0.f, s1c = 0.f, s2a = 0.f, s2b = 0.f, s3 = 0.f;
+    float c1a = 0.f, c1b = 0.f, c1c = 0.f, c2a = 0.f, c2b = 0.f, c3 = 0.f;
+    float z1a = 0.f, z1b = 0.f, z1c = 0.f, z2a = 0.f, z2b = 0.f, z3 = 0.f;
     // ring slots of positions e, e - L, e - 2L, e - 3L, advanced with wrap
     int h0 = 0, h1 = RN - L, h2 = RN - 2 * L, h3 = RN - 3 * L;
-    float cv[kChunkH], cf[kChunkH], ca[kChunkH], nv[kChunkH], nf[kChunkH], na[kChunkH];
-    // loads of a chunk: the plane at its positions, and at its outputs the
-    // pixel value and this plane's running accumulator (all column-major,
+    float cvc[kChunkH], cvs[kChunkH], cf[kChunkH], ca[kChunkH];
+    float nvc[kChunkH], nvs[kChunkH], nf[kChunkH], na[kChunkH];
+    // loads of a chunk: both planes at its positions, and at its outputs the
+    // pixel value and the pair's running accumulator (all column-major,
     // consecutive lanes read consecutive rows)
-    auto fetch = [&](int eb, float (&v)[kChunkH], float (&f)[kChunkH], float (&a)[kChunkH]) {
+    auto fetch = [&](int eb, float (&vc)[kChunkH], float (&vs)[kChunkH], float (&f)[kChunkH],
+                     float (&a)[kChunkH]) {
 #pragma unroll
         for (int d = 0; d < kChunkH; ++d) {
             const int e = eb + d;
-            v[d] = __ldg(V + (size_t)min(max(e, 0), p.W - 1) * p.Hp);
+            const size_t pos = (size_t)min(max(e, 0), p.W - 1) * p.Hp;
+            vc[d] = __ldg(Vc + pos);
+            vs[d] = __ldg(Vs + pos);
             const size_t t = (size_t)min(max(e - 3 * r, 0), p.W - 1) * p.Hp;
             f[d] = __ldg(F + t);
             a[d] = first ? 0.f : A[t];
         }
     };
-    fetch(p0, cv, cf, ca);
+    fetch(p0, cvc, cvs, cf, ca);
+    // one step of both running-sum cascades; CHECKED handles the band's first
+    // 3L steps (inputs before p0 are zero), its warm-up and its end
+    auto step = [&](int e, int d, auto checked) {
+        constexpr bool CHECKED = decltype(checked)::value;
+        const float xc0 = cvc[d], xs0 = cvs[d];
+        ringc[h0 * 64] = xc0;
+        rings[h0 * 64] = xs0;
+        float xc1 = ringc[h1 * 64], xc2 = ringc[h2 * 64], xc3 = ringc[h3 * 64];
+        float xs1 = rings[h1 * 64], xs2 = rings[h2 * 64], xs3 = rings[h3 * 64];
+        if (CHECKED) {
+            const bool v1 = e >= p0 + L, v2 = e >= p0 + 2 * L, v3 = e >= p0 + 3 * L;
+            xc1 = v1 ? xc1 : 0.f;
+            xs1 = v1 ? xs1 : 0.f;
+            xc2 = v2 ? xc2 : 0.f;
+            xs2 = v2 ? xs2 : 0.f;
+            xc3 = v3 ? xc3 : 0.f;
+            xs3 = v3 ? xs3 : 0.f;
+        }
+        h0 = h0 + 1 == RN ? 0 : h0 + 1;
+        h1 = h1 + 1 == RN ? 0 : h1 + 1;
+        h2 = h2 + 1 == RN ? 0 : h2 + 1;
+        h3 = h3 + 1 == RN ? 0 : h3 + 1;
+        c1a += xc0 - xc1;
+        c1b += xc1 - xc2;
+        c1c += xc2 - xc3;
+        c2a += c1a - c1b;
+        c2b += c1b - c1c;
+        c3 += c2a - c2b;
+        z1a += xs0 - xs1;
+        z1b += xs1 - xs2;
+        z1c += xs2 - xs3;
+        z2a += z1a - z1b;
+        z2b += z1b - z1c;
+        z3 += z2a - z2b;
+        const int t = e - 3 * r;  // output column of this step
+        if (CHECKED ? (t >= x0 && row_ok) : row_ok) {
+            float rr = tm * cf[d];
+            rr = rr - rintf(rr);
+            float sn, cs;
+            __sincosf(kTwoPi * rr, &sn, &cs);
+            A[(size_t)t * p.Hp] = fmaf(am * cs, c3, fmaf(am * sn, z3, ca[d]));
+        }
+    };
     for (int e0 = p0; e0 < e_end; e0 += kChunkH) {
-        fetch(e0 + kChunkH, nv, nf, na);
-        const bool steady = e0 >= p0 + 3 * L && e0 + kChunkH <= e_end;  // uniform
+        fetch(e0 + kChunkH, nvc, nvs, nf, na);
+        // uniform: every trailing position is real, every output is in the band
+        const bool fast = e0 >= p0 + 3 * L && e0 + kChunkH <= e_end && e0 - 3 * r >= x0;
+        if (fast) {
 #pragma unroll
-        for (int d = 0; d < kChunkH; ++d) {
-            const int e = e0 + d;
-            if (!steady && e >= e_end) break;
-            const float xin = cv[d];
-            ring[h0 * 32] = xin;
-            float x1v, x2v, x3v;
-            if (steady) {
-                x1v = ring[h1 * 32];
-                x2v = ring[h2 * 32];
-                x3v = ring[h3 * 32];
-            } else {
-                x1v = e >= p0 + L ? ring[h1 * 32] : 0.f;
-                x2v = e >= p0 + 2 * L ? ring[h2 * 32] : 0.f;
-                x3v = e >= p0 + 3 * L ? ring[h3 * 32] : 0.f;
-            }
-            h0 = h0 + 1 == RN ? 0 : h0 + 1;
-            h1 = h1 + 1 == RN ? 0 : h1 + 1;
-            h2 = h2 + 1 == RN ? 0 : h2 + 1;
-            h3 = h3 + 1 == RN ? 0 : h3 + 1;
-            s1a += xin - x1v;
-            s1b += x1v - x2v;
-            s1c += x2v - x3v;
-            s2a += s1a - s1b;
-            s2b += s1b - s1c;
-            s3 += s2a - s2b;
-            const int t = e - 3 * r;  // output column of this step
-            if (t >= x0 && row_ok) {
-                const float coef = am * sin_turns(fmaf(tm, cf[d], ph0));
-                A[(size_t)t * p.Hp] = fmaf(coef, s3, ca[d]);
-            }
+            for (int d = 0; d < kChunkH; ++d) step(e0 + d, d, std::false_type{});
+        } else {
+#pragma unroll
+            for (int d = 0; d < kChunkH; ++d)
+                if (e0 + d < e_end) step(e0 + d, d, std::true_type{});
         }
 #pragma unroll
         for (int d = 0; d < kChunkH; ++d) {
-            cv[d] = nv[d];
+            cvc[d] = nvc[d];
+            cvs[d] = nvs[d];
             cf[d] = nf[d];
             ca[d] = na[d];
         }
     }
 }
 
-// out = (A2 + A3) / (A0 + A1) (numerator: f cos, f sin planes; normaliser:
-// cos, sin planes), column-major -> row-major through a 32 x 33 shared tile.
+// out = P / Q (accumulator 1 / accumulator 0), column-major -> row-major
+// through a 32 x 33 shared tile.
 // grid: (ceil(W / 32), ceil(H / 32)); block: (32, 8)
 __global__ void lr_final(const float *__restrict__ Acc, float *__restrict__ out,
                          float *__restrict__ q_out, int H, int W, int Hp, int C, int ch,
@@ -316,8 +355,8 @@ __global__ void lr_final(const float *__restrict__ Acc, float *__restrict__ out,
         const int x = xb + i, y = yb + threadIdx.x;
         if (x < W && y < H) {
             const size_t o = (size_t)x * Hp + y;
-            tq[i][threadIdx.x] = Acc[o] + Acc[plane + o];
-            tp[i][threadIdx.x] = Acc[2 * plane + o] + Acc[3 * plane + o];
+            tq[i][threadIdx.x] = Acc[o];
+            tp[i][threadIdx.x] = Acc[plane + o];
         }
     }
     __syncthreads();
@@ -336,7 +375,7 @@ __global__ void lr_final(const float *__restrict__ Acc, float *__restrict__ out,
 
 size_t large_workspace(int H, int W) {
     const size_t Hp = ((size_t)H + 7) / 8 * 8;
-    return (size_t)(4 * kVG + 5) * Hp * (size_t)W * sizeof(float) + 256;
+    return (size_t)(4 * kVG + 3) * Hp * (size_t)W * sizeof(float) + 256;
 }
 
 cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cudaStream_t s) {
@@ -353,7 +392,7 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     p.r = pl->r_box;
     p.Vt = reinterpret_cast<float *>(base);
     p.Acc = p.Vt + (size_t)4 * kVG * p.Hp * W;
-    p.ft = p.Acc + (size_t)4 * p.Hp * W;
+    p.ft = p.Acc + (size_t)2 * p.Hp * W;
     // bands (multiples of 8 rows): long enough to amortise the 6r warm-up,
     // short enough to fill the GPU
     p.band_h = std::max(256, 8 * p.r);
@@ -361,8 +400,8 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     const int nbh = (H + p.band_h - 1) / p.band_h;
     const int nbw = (W + p.band_w - 1) / p.band_w;
     const int RS = ring_size(p.r);
-    const size_t sm_v = sizeof(float) * ((size_t)kVCols * RS + (size_t)kVCols * kVG * 32);
-    const size_t sm_h = sizeof(float) * (size_t)32 * (3 * (2 * p.r + 1) + 1);
+    const size_t sm_v = sizeof(float) * (size_t)kVCols * RS;
+    const size_t sm_h = sizeof(float) * (size_t)64 * (3 * (2 * p.r + 1) + 1);
     if (sm_v > 227 * 1024 || sm_h > 227 * 1024) return cudaErrorInvalidValue;
     auto kv = img.dtype == 0 ? lr_vert<0> : lr_vert<1>;
     auto kt = img.dtype == 0 ? lr_transpose<0> : lr_transpose<1>;
@@ -394,7 +433,7 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
                 p.a = pl->a32[m0 + g];
                 p.t = pl->turns32[m0 + g];
                 p.first = m0 + g == 0;
-                dim3 gh((H + 31) / 32, nbw, 4);
+                dim3 gh((H + 31) / 32, nbw, 2);
                 lr_horz<<<gh, 32, sm_h, s>>>(p);
             }
         }
