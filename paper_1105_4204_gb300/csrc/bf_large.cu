@@ -14,9 +14,10 @@
 //             (column-major) so that the second sweep reads coalesced.
 //   lr_horz : one thread per image row and plane pair, walking along a band
 //             of columns of the transposed planes (loads issued a chunk
-//             ahead): the same three cascaded boxes horizontally on the
-//             (cos, sin) or the (f cos, f sin) pair, then the per-pixel
-//             combine of eq. (final-form) into Q or P (column-major).
+//             ahead; the trailing inputs are read again from L2 instead of
+//             being kept on chip): the same three cascaded boxes horizontally
+//             on the (cos, sin) or the (f cos, f sin) pair, then the
+//             per-pixel combine of eq. (final-form) into Q or P.
 //   lr_final: out = P / Q, transposed back to row-major.
 //
 // Running sums with one history buffer.  Box k of the cascade at position q
@@ -25,7 +26,9 @@
 // second, one for the third, spaced L = 2r + 1 apart) makes every update read
 // only the raw input at the four positions e, e - L, e - 2L, e - 3L: the
 // newest is generated (or loaded), the other three come from a ring of the
-// last 3L + 1 inputs in shared memory.  Each running sum is a plain sliding
+// last 3L + 1 inputs (lr_vert: a shared-memory ring of f, the planes being
+// regenerated; lr_horz: the transposed planes in L2).  Each running sum is a
+// plain sliding
 // sum (add the incoming, subtract the outgoing), so rounding grows like the
 // usual running sum, and the half-width r is a run-time value.  The sums start
 // at zero 3r positions before the first output with the input taken as zero
@@ -226,24 +229,23 @@ __global__ void lr_transpose(const __grid_constant__ LrParams p) {
     }
 }
 
-// grid: (ceil(H / 32), bands along x, 2); block: one warp, lanes = rows.
-// blockIdx.z = 0: the (cos, sin) planes, accumulated into Q;
-// blockIdx.z = 1: the (f cos, f sin) planes, accumulated into P.  Both planes
-// of a pair share the pixel's sincos and one accumulator.
-// Dynamic smem: two rings of exactly 3L + 1 values per thread.
-__global__ void __launch_bounds__(32) lr_horz(const __grid_constant__ LrParams p) {
-    extern __shared__ float lh_sm[];
-    const int lane = threadIdx.x;
+// grid: (ceil(H / 32), bands along x, 2); block: 64 threads = two warps of
+// 32 rows each, lanes = rows.  blockIdx.z = 0: the (cos, sin) planes,
+// accumulated into Q; blockIdx.z = 1: the (f cos, f sin) planes,
+// accumulated into P.  Both planes of a pair share the pixel's sincos and
+// one accumulator.  The inputs at e - L, e - 2L, e - 3L are read again from
+// the transposed planes (L2) rather than kept, so no shared memory limits
+// the number of resident warps.
+constexpr int kChunkG = 8;
+__global__ void __launch_bounds__(64) lr_horz(const __grid_constant__ LrParams p) {
+    const int lane = threadIdx.x & 31;
     const int pr = blockIdx.z;  // 0: Q pair, 1: P pair
-    const int y = blockIdx.x * 32 + lane;
+    const int y = (blockIdx.x * 2 + (threadIdx.x >> 5)) * 32 + lane;
     const int yc = min(y, p.H - 1);
     const int x0 = blockIdx.y * p.band_w;
     const int x1 = min(x0 + p.band_w, p.W);
     const int r = p.r, L = 2 * r + 1;
     const int p0 = x0 - 3 * r;
-    const int RN = 3 * L + 1;
-    float *ringc = lh_sm + lane;            // slot k at ringc[k * 64]
-    float *rings = lh_sm + 32 + lane;       // interleaved with ringc
     const size_t plane = (size_t)p.W * p.Hp;
     const float *Vc = p.Vt + (size_t)p.slot * 4 * plane + (size_t)(2 * pr) * plane + yc;
     const float *Vs = Vc + plane;
@@ -255,86 +257,61 @@ __global__ void __launch_bounds__(32) lr_horz(const __grid_constant__ LrParams p
     const bool first = p.first;
     float c1a = 0.f, c1b = 0.f, c1c = 0.f, c2a = 0.f, c2b = 0.f, c3 = 0.f;
     float z1a = 0.f, z1b = 0.f, z1c = 0.f, z2a = 0.f, z2b = 0.f, z3 = 0.f;
-    // ring slots of positions e, e - L, e - 2L, e - 3L, advanced with wrap
-    int h0 = 0, h1 = RN - L, h2 = RN - 2 * L, h3 = RN - 3 * L;
-    float cvc[kChunkH], cvs[kChunkH], cf[kChunkH], ca[kChunkH];
-    float nvc[kChunkH], nvs[kChunkH], nf[kChunkH], na[kChunkH];
-    // loads of a chunk: both planes at its positions, and at its outputs the
-    // pixel value and the pair's running accumulator (all column-major,
-    // consecutive lanes read consecutive rows)
-    auto fetch = [&](int eb, float (&vc)[kChunkH], float (&vs)[kChunkH], float (&f)[kChunkH],
-                     float (&a)[kChunkH]) {
+    // per chunk: both planes at e, e-L, e-2L, e-3L (0 before p0), and at the
+    // chunk's outputs the pixel value and the pair's running accumulator
+    float cv[kChunkG][8], cf[kChunkG], ca[kChunkG];
+    float nv[kChunkG][8], nf[kChunkG], na[kChunkG];
+    auto fetch = [&](int eb, float (&v)[kChunkG][8], float (&f)[kChunkG], float (&a)[kChunkG]) {
 #pragma unroll
-        for (int d = 0; d < kChunkH; ++d) {
+        for (int d = 0; d < kChunkG; ++d) {
             const int e = eb + d;
-            const size_t pos = (size_t)min(max(e, 0), p.W - 1) * p.Hp;
-            vc[d] = __ldg(Vc + pos);
-            vs[d] = __ldg(Vs + pos);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int pos = e - k * L;
+                const size_t o = (size_t)min(max(pos, 0), p.W - 1) * p.Hp;
+                const bool ok = pos >= p0;
+                v[d][2 * k] = ok ? __ldg(Vc + o) : 0.f;
+                v[d][2 * k + 1] = ok ? __ldg(Vs + o) : 0.f;
+            }
             const size_t t = (size_t)min(max(e - 3 * r, 0), p.W - 1) * p.Hp;
             f[d] = __ldg(F + t);
             a[d] = first ? 0.f : A[t];
         }
     };
-    fetch(p0, cvc, cvs, cf, ca);
-    // one step of both running-sum cascades; CHECKED handles the band's first
-    // 3L steps (inputs before p0 are zero), its warm-up and its end
-    auto step = [&](int e, int d, auto checked) {
-        constexpr bool CHECKED = decltype(checked)::value;
-        const float xc0 = cvc[d], xs0 = cvs[d];
-        ringc[h0 * 64] = xc0;
-        rings[h0 * 64] = xs0;
-        float xc1 = ringc[h1 * 64], xc2 = ringc[h2 * 64], xc3 = ringc[h3 * 64];
-        float xs1 = rings[h1 * 64], xs2 = rings[h2 * 64], xs3 = rings[h3 * 64];
-        if (CHECKED) {
-            const bool v1 = e >= p0 + L, v2 = e >= p0 + 2 * L, v3 = e >= p0 + 3 * L;
-            xc1 = v1 ? xc1 : 0.f;
-            xs1 = v1 ? xs1 : 0.f;
-            xc2 = v2 ? xc2 : 0.f;
-            xs2 = v2 ? xs2 : 0.f;
-            xc3 = v3 ? xc3 : 0.f;
-            xs3 = v3 ? xs3 : 0.f;
-        }
-        h0 = h0 + 1 == RN ? 0 : h0 + 1;
-        h1 = h1 + 1 == RN ? 0 : h1 + 1;
-        h2 = h2 + 1 == RN ? 0 : h2 + 1;
-        h3 = h3 + 1 == RN ? 0 : h3 + 1;
-        c1a += xc0 - xc1;
-        c1b += xc1 - xc2;
-        c1c += xc2 - xc3;
-        c2a += c1a - c1b;
-        c2b += c1b - c1c;
-        c3 += c2a - c2b;
-        z1a += xs0 - xs1;
-        z1b += xs1 - xs2;
-        z1c += xs2 - xs3;
-        z2a += z1a - z1b;
-        z2b += z1b - z1c;
-        z3 += z2a - z2b;
-        const int t = e - 3 * r;  // output column of this step
-        if (CHECKED ? (t >= x0 && row_ok) : row_ok) {
-            float rr = tm * cf[d];
-            rr = rr - rintf(rr);
-            float sn, cs;
-            __sincosf(kTwoPi * rr, &sn, &cs);
-            A[(size_t)t * p.Hp] = fmaf(am * cs, c3, fmaf(am * sn, z3, ca[d]));
-        }
-    };
-    for (int e0 = p0; e0 < e_end; e0 += kChunkH) {
-        fetch(e0 + kChunkH, nvc, nvs, nf, na);
-        // uniform: every trailing position is real, every output is in the band
-        const bool fast = e0 >= p0 + 3 * L && e0 + kChunkH <= e_end && e0 - 3 * r >= x0;
-        if (fast) {
+    fetch(p0, cv, cf, ca);
+    for (int e0 = p0; e0 < e_end; e0 += kChunkG) {
+        fetch(e0 + kChunkG, nv, nf, na);
+        const bool full = e0 + kChunkG <= e_end && e0 - 3 * r >= x0;  // uniform
 #pragma unroll
-            for (int d = 0; d < kChunkH; ++d) step(e0 + d, d, std::false_type{});
-        } else {
-#pragma unroll
-            for (int d = 0; d < kChunkH; ++d)
-                if (e0 + d < e_end) step(e0 + d, d, std::true_type{});
+        for (int d = 0; d < kChunkG; ++d) {
+            const int e = e0 + d;
+            if (!full && e >= e_end) break;
+            const float *v = cv[d];
+            c1a += v[0] - v[2];
+            c1b += v[2] - v[4];
+            c1c += v[4] - v[6];
+            c2a += c1a - c1b;
+            c2b += c1b - c1c;
+            c3 += c2a - c2b;
+            z1a += v[1] - v[3];
+            z1b += v[3] - v[5];
+            z1c += v[5] - v[7];
+            z2a += z1a - z1b;
+            z2b += z1b - z1c;
+            z3 += z2a - z2b;
+            const int t = e - 3 * r;  // output column of this step
+            if (full ? row_ok : (t >= x0 && row_ok)) {
+                float rr = tm * cf[d];
+                rr = rr - rintf(rr);
+                float sn, cs;
+                __sincosf(kTwoPi * rr, &sn, &cs);
+                A[(size_t)t * p.Hp] = fmaf(am * cs, c3, fmaf(am * sn, z3, ca[d]));
+            }
         }
 #pragma unroll
-        for (int d = 0; d < kChunkH; ++d) {
-            cvc[d] = nvc[d];
-            cvs[d] = nvs[d];
+        for (int d = 0; d < kChunkG; ++d) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cv[d][k] = nv[d][k];
             cf[d] = nf[d];
             ca[d] = na[d];
         }
@@ -401,8 +378,7 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     const int nbw = (W + p.band_w - 1) / p.band_w;
     const int RS = ring_size(p.r);
     const size_t sm_v = sizeof(float) * (size_t)kVCols * RS;
-    const size_t sm_h = sizeof(float) * (size_t)64 * (3 * (2 * p.r + 1) + 1);
-    if (sm_v > 227 * 1024 || sm_h > 227 * 1024) return cudaErrorInvalidValue;
+    if (sm_v > 227 * 1024) return cudaErrorInvalidValue;
     auto kv = img.dtype == 0 ? lr_vert<0> : lr_vert<1>;
     auto kt = img.dtype == 0 ? lr_transpose<0> : lr_transpose<1>;
     static bool attr[64] = {};
@@ -414,8 +390,6 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
             e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
             if (e != cudaSuccess) return e;
         }
-        e = cudaFuncSetAttribute(lr_horz, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr[dev] = true;
     }
     const int nt = (int)pl->a32.size();
@@ -433,8 +407,8 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
                 p.a = pl->a32[m0 + g];
                 p.t = pl->turns32[m0 + g];
                 p.first = m0 + g == 0;
-                dim3 gh((H + 31) / 32, nbw, 2);
-                lr_horz<<<gh, 32, sm_h, s>>>(p);
+                dim3 gh((H + 63) / 64, nbw, 2);
+                lr_horz<<<gh, 64, 0, s>>>(p);
             }
         }
         dim3 gf((W + 31) / 32, (H + 31) / 32);
