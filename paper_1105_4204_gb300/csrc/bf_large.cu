@@ -20,15 +20,14 @@
 //             per-pixel combine of eq. (final-form) into Q or P.
 //   lr_final: out = P / Q, transposed back to row-major.
 //
-// Running sums with one history buffer.  Box k of the cascade at position q
+// Running sums without per-pass history.  Box k of the cascade at position q
 // needs its input at q + r and q - r - 1.  Keeping one running sum per
 // position that a later box needs (three for the first box, two for the
 // second, one for the third, spaced L = 2r + 1 apart) makes every update read
 // only the raw input at the four positions e, e - L, e - 2L, e - 3L: the
-// newest is generated (or loaded), the other three come from a ring of the
-// last 3L + 1 inputs (lr_vert: a shared-memory ring of f, the planes being
-// regenerated; lr_horz: the transposed planes in L2).  Each running sum is a
-// plain sliding
+// newest is generated (or loaded); the other three come from a shared-memory
+// ring of f, the planes being regenerated (lr_vert), or are read again from
+// the transposed planes in L2 (lr_horz).  Each running sum is a plain sliding
 // sum (add the incoming, subtract the outgoing), so rounding grows like the
 // usual running sum, and the half-width r is a run-time value.  The sums start
 // at zero 3r positions before the first output with the input taken as zero
