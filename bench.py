@@ -416,13 +416,11 @@ def measure_fwd_bwd(bf, torch, dev, stream):
     ws = torch.empty(64 * 1024, dtype=torch.float64, device=dev)
 
     def fwd():
-        for b in range(B):
-            bf.forward(plan, imgs[b], return_q=True, out=outs[b], q=qs[b])
+        bf.forward_stack(plan, imgs, return_q=True, out=outs, q=qs)
 
     def fwd_bwd():
         fwd()
-        for b in range(B):
-            bf.backward(plan, imgs[b], outs[b], qs[b], u[b], grad_in=grads[b], workspace=ws)
+        bf.backward_stack(plan, imgs, outs, qs, u, grad_in=grads, workspace=ws)
 
     t_f = _time(fwd, torch, stream, 5)
     t_fb = _time(fwd_bwd, torch, stream, 5)

@@ -142,6 +142,16 @@ bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *ou
                      int H, int W, int C, long long row_stride_elems, float *q_out,
                      cudaStream_t stream);
 
+/*
+ * bf_forward over a stack of `count` single-channel images of one size, laid
+ * out contiguously (image k at in + k*H*W elements, out + k*H*W floats),
+ * all filtered with the same plan in one launch (channels are independent,
+ * Section 3).  q_out, when not NULL, is a stack of the same shape.  Same
+ * kernels, limits and errors as bf_forward; 1 <= count <= 65535.
+ */
+bf_status bf_forward_stack(const bf_plan *plan, const void *in, bf_dtype dt, float *out,
+                           int H, int W, int count, float *q_out, cudaStream_t stream);
+
 /* Frees the scratch buffers bf_forward allocated (all devices).  Call only
  * when no work that uses them is in flight. */
 void bf_release_scratch(void);
@@ -181,6 +191,19 @@ bf_status bf_backward(const bf_plan *plan, const float *f, const float *out,
                       const float *q, const float *grad_out, float *grad_in,
                       double *grad_sigma_r, int H, int W, void *workspace,
                       size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * bf_backward over a contiguous stack of `count` H x W images (layout as in
+ * bf_forward_stack) in one launch; grad_sigma_r receives the sum over the
+ * stack of dL/dsigma_r (the images share sigma_r).  workspace needs
+ * bf_backward_stack_workspace(plan, H, W, count) bytes, 8-byte aligned, when
+ * grad_sigma_r is not NULL.
+ */
+size_t bf_backward_stack_workspace(const bf_plan *plan, int H, int W, int count);
+bf_status bf_backward_stack(const bf_plan *plan, const float *f, const float *out,
+                            const float *q, const float *grad_out, float *grad_in,
+                            double *grad_sigma_r, int H, int W, int count, void *workspace,
+                            size_t workspace_bytes, cudaStream_t stream);
 
 /*
  * bf_backward for callers that cannot allocate device memory.  The paper has

@@ -48,6 +48,11 @@ def _declare(lib):
         "bf_plan_weights": (c_int, [c_void_p, _dp, c_int, _ip]),
         "bf_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_int, c_int, c_ll,
                                c_void_p, c_void_p]),
+        "bf_forward_stack": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_int, c_int,
+                                     c_void_p, c_void_p]),
+        "bf_backward_stack_workspace": (c_size_t, [c_void_p, c_int, c_int, c_int]),
+        "bf_backward_stack": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p, c_int, c_int, c_int, c_void_p, c_size_t, c_void_p]),
         "bf_forward_unfused_workspace": (c_size_t, [c_int, c_int]),
         "bf_forward_unfused": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p,
                                        c_size_t, c_void_p]),

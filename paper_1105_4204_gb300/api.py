@@ -181,6 +181,55 @@ def backward(plan: Plan, f: torch.Tensor, out: torch.Tensor, q: torch.Tensor,
     return grad_in, gs
 
 
+def forward_stack(plan: Plan, imgs: torch.Tensor, return_q: bool = False,
+                  out: torch.Tensor | None = None, q: torch.Tensor | None = None, stream=None):
+    """Filter a contiguous B x H x W stack (float32 or uint8) in one launch."""
+    if not imgs.is_cuda or imgs.dim() != 3 or not imgs.is_contiguous():
+        raise ValueError("stack must be a contiguous B x H x W CUDA tensor")
+    dt = {torch.float32: 0, torch.uint8: 1}.get(imgs.dtype)
+    if dt is None:
+        raise ValueError("stack dtype must be float32 or uint8")
+    B, H, W = imgs.shape
+    if out is None:
+        out = torch.empty((B, H, W), dtype=torch.float32, device=imgs.device)
+    if return_q and q is None:
+        q = torch.empty((B, H, W), dtype=torch.float32, device=imgs.device)
+    check(lib().bf_forward_stack(plan.handle, ctypes.c_void_p(imgs.data_ptr()), dt,
+                                 ctypes.c_void_p(out.data_ptr()), H, W, B,
+                                 ctypes.c_void_p(q.data_ptr() if return_q else 0),
+                                 _stream_ptr(stream)))
+    return (out, q) if return_q else out
+
+
+def backward_stack(plan: Plan, f: torch.Tensor, out: torch.Tensor, q: torch.Tensor,
+                   grad_out: torch.Tensor, need_sigma: bool = True,
+                   grad_in: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                   stream=None):
+    """Adjoint over a contiguous B x H x W float32 stack in one launch; returns
+    (dL/df, sum over the stack of dL/dsigma_r or None)."""
+    for t in (f, out, q, grad_out):
+        if not t.is_cuda or t.dtype != torch.float32 or t.dim() != 3 or not t.is_contiguous():
+            raise ValueError("backward_stack takes contiguous B x H x W float32 CUDA tensors")
+    B, H, W = f.shape
+    if grad_in is None:
+        grad_in = torch.empty_like(f)
+    gs = None
+    ws_ptr, nbytes = 0, 0
+    if need_sigma:
+        gs = torch.empty((), dtype=torch.float64, device=f.device)
+        nbytes = lib().bf_backward_stack_workspace(plan.handle, H, W, B)
+        if workspace is None or workspace.numel() * workspace.element_size() < nbytes:
+            workspace = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=f.device)
+        ws_ptr = workspace.data_ptr()
+    check(lib().bf_backward_stack(plan.handle, ctypes.c_void_p(f.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                  ctypes.c_void_p(grad_out.data_ptr()),
+                                  ctypes.c_void_p(grad_in.data_ptr()),
+                                  ctypes.c_void_p(gs.data_ptr() if gs is not None else 0), H, W, B,
+                                  ctypes.c_void_p(ws_ptr), nbytes, _stream_ptr(stream)))
+    return grad_in, gs
+
+
 class BilateralFunction(torch.autograd.Function):
     """Differentiable filter: forward through the fused kernel, backward through
     the fused adjoint kernel (gradients w.r.t. the image and sigma_r; N is held
@@ -190,14 +239,8 @@ class BilateralFunction(torch.autograd.Function):
     def forward(ctx, f, sigma_r, sigma_s, T, kind, radius):
         sr = float(sigma_r)
         plan = Plan(sigma_s, sr, T, kind=kind, radius=radius)
-        imgs = f if f.dim() == 3 else f.unsqueeze(0)
-        outs, qs = [], []
-        for b in range(imgs.shape[0]):
-            o, q = forward(plan, imgs[b].contiguous(), return_q=True)
-            outs.append(o)
-            qs.append(q)
-        out = torch.stack(outs)
-        q = torch.stack(qs)
+        imgs = (f if f.dim() == 3 else f.unsqueeze(0)).contiguous()
+        out, q = forward_stack(plan, imgs, return_q=True)
         ctx.plan = plan
         ctx.squeeze = f.dim() == 2
         ctx.sigma_is_tensor = isinstance(sigma_r, torch.Tensor)
@@ -207,20 +250,12 @@ class BilateralFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         imgs, out, q = ctx.saved_tensors
-        g = grad_out if grad_out.dim() == 3 else grad_out.unsqueeze(0)
+        g = (grad_out if grad_out.dim() == 3 else grad_out.unsqueeze(0)).contiguous()
         need_sigma = ctx.sigma_is_tensor and ctx.needs_input_grad[1]
-        grads = []
-        gsum = None
-        for b in range(imgs.shape[0]):
-            gf, gs = backward(ctx.plan, imgs[b].contiguous(), out[b], q[b], g[b].contiguous(),
-                              need_sigma=need_sigma)
-            grads.append(gf)
-            if gs is not None:
-                gsum = gs if gsum is None else gsum + gs
-        gf = torch.stack(grads)
+        gf, gs = backward_stack(ctx.plan, imgs, out, q, g, need_sigma=need_sigma)
         if ctx.squeeze:
             gf = gf[0]
-        gsig = gsum.to(torch.float32) if gsum is not None else None
+        gsig = gs.to(torch.float32) if gs is not None else None
         return gf, gsig, None, None, None, None
 
 

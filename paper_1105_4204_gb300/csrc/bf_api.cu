@@ -79,6 +79,9 @@ extern "C" const char *bf_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int bf_version(void) { return 100; }
 
+static bf_status forward_planes(const bf_plan *plan, const BfImage &img, cudaStream_t stream,
+                                const char *who);
+
 extern "C" bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *out,
                                 int H, int W, int C, long long row_stride_elems, float *q_out,
                                 cudaStream_t stream) {
@@ -102,17 +105,55 @@ extern "C" bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt
     img.C = C;
     img.dtype = (int)dt;
     img.q_scale = plan->q_scale;
+    img.in_px = C;
+    img.out_px = C;
+    img.in_z = 1;
+    img.out_z = 1;
+    return forward_planes(plan, img, stream, "bf_forward");
+}
+
+// Runs one BfImage description (interleaved channels or a stack).
+static bf_status forward_planes(const bf_plan *plan, const BfImage &img, cudaStream_t stream,
+                                const char *who) {
+    const int H = img.H, W = img.W;
     if (tile_supported(plan))
-        return cuda_check(launch_tile_forward(plan, img, stream), "bf_forward launch");
+        return cuda_check(launch_tile_forward(plan, img, stream), who);
     if (plan->kind == BF_SPATIAL_BOX_ITER) {
         void *ws = nullptr;
         cudaError_t e = get_scratch(large_workspace(H, W), &ws);
         if (e == cudaErrorMemoryAllocation)
-            return fail(BF_ENOMEM, "bf_forward: cannot allocate the large-radius scratch");
-        if (e != cudaSuccess) return cuda_check(e, "bf_forward scratch");
-        return cuda_check(launch_large_box(plan, img, ws, stream), "bf_forward launch");
+            return fail(BF_ENOMEM, std::string(who) + ": cannot allocate the large-radius scratch");
+        if (e != cudaSuccess) return cuda_check(e, who);
+        return cuda_check(launch_large_box(plan, img, ws, stream), who);
     }
-    return fail(BF_EUNSUPPORTED, "bf_forward: no kernel for this spatial support");
+    return fail(BF_EUNSUPPORTED, std::string(who) + ": no kernel for this spatial support");
+}
+
+extern "C" bf_status bf_forward_stack(const bf_plan *plan, const void *in, bf_dtype dt,
+                                      float *out, int H, int W, int count, float *q_out,
+                                      cudaStream_t stream) {
+    if (!plan) return fail(BF_EINVAL, "bf_forward_stack: plan is NULL");
+    if (!in || !out) return fail(BF_EINVAL, "bf_forward_stack: in/out is NULL");
+    if (H < 1 || W < 1 || count < 1)
+        return fail(BF_EINVAL, "bf_forward_stack: H, W and count must be >= 1");
+    if (dt != BF_F32 && dt != BF_U8) return fail(BF_EINVAL, "bf_forward_stack: unknown dtype");
+    if ((long long)H * W > (1LL << 31) / 4 || count > 65535)
+        return fail(BF_EUNSUPPORTED, "bf_forward_stack: image or stack too large");
+    BfImage img;
+    img.in = in;
+    img.out = out;
+    img.q_out = q_out;
+    img.in_row_stride = W;
+    img.H = H;
+    img.W = W;
+    img.C = count;
+    img.dtype = (int)dt;
+    img.q_scale = plan->q_scale;
+    img.in_px = 1;
+    img.out_px = 1;
+    img.in_z = (long long)H * W;
+    img.out_z = (long long)H * W;
+    return forward_planes(plan, img, stream, "bf_forward_stack");
 }
 
 extern "C" void bf_release_scratch(void) {
@@ -169,11 +210,48 @@ size_t bwd_blocks(int H, int W);
 cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, const float *q,
                             const float *u, float *grad, double *grad_sigma_r, double *partials,
                             int H, int W, cudaStream_t s);
+cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, const float *q,
+                            const float *u, float *grad, double *grad_sigma_r, double *partials,
+                            int H, int W, cudaStream_t s, int count);
 }  // namespace bf
 
 extern "C" size_t bf_backward_workspace(const bf_plan *plan, int H, int W) {
     if (!plan || H < 1 || W < 1) return 0;
     return bwd_blocks(H, W) * sizeof(double);
+}
+
+extern "C" size_t bf_backward_stack_workspace(const bf_plan *plan, int H, int W, int count) {
+    if (!plan || H < 1 || W < 1 || count < 1) return 0;
+    return bwd_blocks(H, W) * (size_t)count * sizeof(double);
+}
+
+extern "C" bf_status bf_backward_stack(const bf_plan *plan, const float *f, const float *out,
+                                       const float *q, const float *grad_out, float *grad_in,
+                                       double *grad_sigma_r, int H, int W, int count,
+                                       void *workspace, size_t workspace_bytes,
+                                       cudaStream_t stream) {
+    if (!plan) return fail(BF_EINVAL, "bf_backward_stack: plan is NULL");
+    if (!f || !out || !q || !grad_out || !grad_in)
+        return fail(BF_EINVAL, "bf_backward_stack: a data pointer is NULL");
+    if (H < 1 || W < 1 || count < 1)
+        return fail(BF_EINVAL, "bf_backward_stack: H, W and count must be >= 1");
+    if ((long long)H * W > (1LL << 31) / 4 || count > 65535)
+        return fail(BF_EUNSUPPORTED, "bf_backward_stack: image or stack too large");
+    if (!bwd_supported(plan))
+        return fail(BF_EUNSUPPORTED, "bf_backward_stack: no kernel for this spatial support "
+                                     "(Gaussian R <= 24 or box r <= 8)");
+    const size_t need = bwd_blocks(H, W) * (size_t)count * sizeof(double);
+    if (grad_sigma_r) {
+        if (!workspace) return fail(BF_EINVAL, "bf_backward_stack: workspace is NULL");
+        if (workspace_bytes < need)
+            return fail(BF_EINVAL, "bf_backward_stack: workspace too small (need " +
+                                       std::to_string(need) + " bytes)");
+        if ((uintptr_t)workspace % 8 != 0)
+            return fail(BF_EINVAL, "bf_backward_stack: workspace must be 8-byte aligned");
+    }
+    return cuda_check(launch_backward(plan, f, out, q, grad_out, grad_in, grad_sigma_r,
+                                      reinterpret_cast<double *>(workspace), H, W, stream, count),
+                      "bf_backward_stack launch");
 }
 
 extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const float *out,

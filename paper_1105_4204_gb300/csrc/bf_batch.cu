@@ -67,8 +67,8 @@ __device__ __forceinline__ void run_tile(const BatchParams &p, const ImgDesc &d,
     jb.in_row_stride = d.W;
     jb.H = d.H;
     jb.W = d.W;
-    jb.C = 1;
-    jb.ch = 0;
+    jb.in_px = 1;
+    jb.out_px = 1;
     jb.dtype = 0;
     jb.q_scale = d.q_scale;
     jb.a = p.ta + d.term_off;

@@ -46,8 +46,9 @@ size_t bwd_blocks(int H, int W) {
 
 cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, const float *q,
                             const float *u, float *grad, double *grad_sigma_r, double *partials,
-                            int H, int W, cudaStream_t s) {
+                            int H, int W, cudaStream_t s, int count) {
     BwdParams prm;
+    prm.img_stride = (long long)H * W;
     prm.f = f;
     prm.o = o;
     prm.q = q;
@@ -92,34 +93,41 @@ cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, c
     cudaError_t e;
     if (pl->kind == BF_SPATIAL_GAUSS_TRUNC) {
         switch (gauss_bwd_radius(pl->R)) {
-            case 2: e = launch_bwd<0, 2, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 4: e = launch_bwd<0, 4, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 6: e = launch_bwd<0, 6, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 9: e = launch_bwd<0, 9, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 12: e = launch_bwd<0, 12, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 18: e = launch_bwd<0, 18, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 24: e = launch_bwd<0, 24, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
+            case 2: e = launch_bwd<0, 2, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 4: e = launch_bwd<0, 4, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 6: e = launch_bwd<0, 6, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 9: e = launch_bwd<0, 9, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 12: e = launch_bwd<0, 12, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 18: e = launch_bwd<0, 18, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 24: e = launch_bwd<0, 24, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
             default: return cudaErrorInvalidValue;
         }
     } else {
         switch (pl->r_box) {
-            case 1: e = launch_bwd<1, 1, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 2: e = launch_bwd<1, 2, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 3: e = launch_bwd<1, 3, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 4: e = launch_bwd<1, 4, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 5: e = launch_bwd<1, 5, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 6: e = launch_bwd<1, 6, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 7: e = launch_bwd<1, 7, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
-            case 8: e = launch_bwd<1, 8, kBwdTH, kBwdTW, kBwdTWT>(prm, s); break;
+            case 1: e = launch_bwd<1, 1, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 2: e = launch_bwd<1, 2, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 3: e = launch_bwd<1, 3, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 4: e = launch_bwd<1, 4, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 5: e = launch_bwd<1, 5, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 6: e = launch_bwd<1, 6, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 7: e = launch_bwd<1, 7, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
+            case 8: e = launch_bwd<1, 8, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
             default: return cudaErrorInvalidValue;
         }
     }
     if (e != cudaSuccess) return e;
     if (grad_sigma_r) {
-        bwd_reduce<<<1, 256, 0, s>>>(partials, (int)bwd_blocks(H, W), grad_sigma_r);
+        bwd_reduce<<<1, 256, 0, s>>>(partials, (int)(bwd_blocks(H, W) * count), grad_sigma_r);
         e = cudaGetLastError();
     }
     return e;
+}
+
+// Single-image form.
+cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, const float *q,
+                            const float *u, float *grad, double *grad_sigma_r, double *partials,
+                            int H, int W, cudaStream_t s) {
+    return launch_backward(pl, f, o, q, u, grad, grad_sigma_r, partials, H, W, s, 1);
 }
 
 }  // namespace bf

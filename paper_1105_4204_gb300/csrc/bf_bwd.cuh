@@ -32,9 +32,10 @@ namespace bf {
 
 struct BwdParams {
     const float *f, *o, *q, *u;
-    float *grad;         // dL/df, H x W
+    float *grad;         // dL/df, H x W per image; blockIdx.z selects the image of a stack
     double *partials;    // one dL/dsigma_r partial per block, or nullptr
     int H, W;
+    long long img_stride;  // elements between consecutive images of a stack
     float scale;         // filter normalisation (box filters run unnormalised)
     float inv_sigma_r;
     BfTerms terms;       // a_m and turns per gray level
@@ -85,6 +86,9 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
     const int x0 = blockIdx.x * TW;
     const int y0 = blockIdx.y * TH;
     const int H = p.H, W = p.W;
+    const long long zoff = (long long)blockIdx.z * p.img_stride;
+    const float *pf = p.f + zoff, *po = p.o + zoff, *pq = p.q + zoff, *pu = p.u + zoff;
+    float *pg = p.grad + zoff;
 
     for (int idx = tid; idx < EH * EW; idx += G::NT) {
         const int i = idx / EW;
@@ -94,9 +98,9 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
         const int gx = min(max(gxr, 0), W - 1);
         const size_t off = (size_t)gy * W + gx;
         const bool inside = gyr >= 0 && gyr < H && gxr >= 0 && gxr < W;
-        Fs[i * G::SF + j] = __ldg(p.f + off);
-        Os[i * G::SF + j] = __ldg(p.o + off);
-        As[i * G::SF + j] = inside ? __ldg(p.u + off) / __ldg(p.q + off) : 0.f;
+        Fs[i * G::SF + j] = __ldg(pf + off);
+        Os[i * G::SF + j] = __ldg(po + off);
+        As[i * G::SF + j] = inside ? __ldg(pu + off) / __ldg(pq + off) : 0.f;
     }
 
     const int pi = tid % TH;  // phase-2 row
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
                 for (int i = 0; i < TH; ++i) cd[i * G::SC] = x[i + HALO];
             }
             float y[TH];
-#pragma unroll
+#pragma unroll 1
             for (int pw = 0; pw < 3; ++pw) {
                 if (pw > 0) {
 #pragma unroll
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
                 fp[k] = Fs[ti];
                 op[k] = Os[ti];
             }
-#pragma unroll
+#pragma unroll 1
             for (int pl = 0; pl < 6; ++pl) {
                 const float4 *src = reinterpret_cast<const float4 *>(V + pl * TH * G::SV +
                                                                      pi * G::SV + cx0);
@@ -175,33 +179,56 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
                 for (int k = 0; k < G::LN; ++k) yin[k] = yv[k];
                 float z[TWT];
                 Filt<KIND, RAD, G::LN>::run(yin, z, p.taps.w);
+                // this plane's weights in dL/df (gc) and dL/dsigma_r (sc)
+                float gc[TWT], sc[TWT];
+                switch (pl) {
+                    case 0:  // W[c]
+#pragma unroll
+                        for (int k = 0; k < TWT; ++k) {
+                            gc[k] = ks[k] * op[k];
+                            sc[k] = -ks[k] * fp[k] * op[k];
+                        }
+                        break;
+                    case 1:  // W[s]
+#pragma unroll
+                        for (int k = 0; k < TWT; ++k) {
+                            gc[k] = -kc[k] * op[k];
+                            sc[k] = kc[k] * fp[k] * op[k];
+                        }
+                        break;
+                    case 2:  // W[f c]
+#pragma unroll
+                        for (int k = 0; k < TWT; ++k) {
+                            gc[k] = -ks[k];
+                            sc[k] = ks[k] * (fp[k] + op[k]);
+                        }
+                        break;
+                    case 3:  // W[f s]
+#pragma unroll
+                        for (int k = 0; k < TWT; ++k) {
+                            gc[k] = kc[k];
+                            sc[k] = -kc[k] * (fp[k] + op[k]);
+                        }
+                        break;
+                    case 4:  // W[f^2 c]
+#pragma unroll
+                        for (int k = 0; k < TWT; ++k) {
+                            gc[k] = 0.f;
+                            sc[k] = -ks[k];
+                        }
+                        break;
+                    default:  // W[f^2 s]
+#pragma unroll
+                        for (int k = 0; k < TWT; ++k) {
+                            gc[k] = 0.f;
+                            sc[k] = kc[k];
+                        }
+                        break;
+                }
 #pragma unroll
                 for (int k = 0; k < TWT; ++k) {
-                    const float fo = fp[k] * op[k], fpo = fp[k] + op[k];
-                    switch (pl) {
-                        case 0:  // W[c]
-                            gacc[k] = fmaf(ks[k] * op[k], z[k], gacc[k]);
-                            sacc[k] = fmaf(-ks[k] * fo, z[k], sacc[k]);
-                            break;
-                        case 1:  // W[s]
-                            gacc[k] = fmaf(-kc[k] * op[k], z[k], gacc[k]);
-                            sacc[k] = fmaf(kc[k] * fo, z[k], sacc[k]);
-                            break;
-                        case 2:  // W[f c]
-                            gacc[k] = fmaf(-ks[k], z[k], gacc[k]);
-                            sacc[k] = fmaf(ks[k] * fpo, z[k], sacc[k]);
-                            break;
-                        case 3:  // W[f s]
-                            gacc[k] = fmaf(kc[k], z[k], gacc[k]);
-                            sacc[k] = fmaf(-kc[k] * fpo, z[k], sacc[k]);
-                            break;
-                        case 4:  // W[f^2 c]
-                            sacc[k] = fmaf(-ks[k], z[k], sacc[k]);
-                            break;
-                        default:  // W[f^2 s]
-                            sacc[k] = fmaf(kc[k], z[k], sacc[k]);
-                            break;
-                    }
+                    gacc[k] = fmaf(gc[k], z[k], gacc[k]);
+                    sacc[k] = fmaf(sc[k], z[k], sacc[k]);
                 }
             }
         }
@@ -216,7 +243,7 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
             for (int i = 0; i < EH; ++i)
                 x[i] = As[i * G::SF + j] * sin_turns(fmaf(tm, Fs[i * G::SF + j], ph0));
             float y[TH];
-#pragma unroll
+#pragma unroll 1
             for (int pw = 0; pw < 2; ++pw) {
                 if (pw > 0) {
 #pragma unroll
@@ -264,7 +291,7 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
                 cc[k] = aw * s;                // W^T[alpha o c]
                 cd[k] = -aw * c;               // W^T[alpha o s]
             }
-#pragma unroll
+#pragma unroll 1
             for (int pl = 0; pl < 4; ++pl) {
                 const float *row = V + pl * TH * G::SV + pi * G::SV;
                 const float4 *src = reinterpret_cast<const float4 *>(row + cx0);
@@ -314,7 +341,7 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
     for (int k = 0; k < TWT; ++k) {
         const int gx = x0 + cx0 + k;
         if (gy < H && gx < W) {
-            p.grad[(size_t)gy * W + gx] = gacc[k] * p.scale;
+            pg[(size_t)gy * W + gx] = gacc[k] * p.scale;
             sl += (double)sacc[k];
         }
     }
@@ -326,13 +353,13 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
             __syncthreads();
         }
         if (tid == 0)
-            p.partials[blockIdx.y * gridDim.x + blockIdx.x] =
+            p.partials[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] =
                 red[0] * (double)p.scale * (double)p.inv_sigma_r;
     }
 }
 
 template <int KIND, int RAD, int TH, int TW, int TWT>
-cudaError_t launch_bwd(const BwdParams &prm, cudaStream_t s) {
+cudaError_t launch_bwd(const BwdParams &prm, int count, cudaStream_t s) {
     using G = BwdGeom<KIND, RAD, TH, TW, TWT>;
     static_assert(G::SMEM <= 227 * 1024, "shared memory");
     static_assert((G::NT & (G::NT - 1)) == 0, "reduction needs a power-of-two block");
@@ -346,7 +373,7 @@ cudaError_t launch_bwd(const BwdParams &prm, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    dim3 grid((prm.W + TW - 1) / TW, (prm.H + TH - 1) / TH, 1);
+    dim3 grid((prm.W + TW - 1) / TW, (prm.H + TH - 1) / TH, count);
     kern<<<grid, G::NT, G::SMEM, s>>>(prm);
     return cudaGetLastError();
 }

@@ -44,6 +44,9 @@ struct BfTaps {
     float w[2 * BF_MAX_TAPS_R + 1];
 };
 
+// One launch covers C planes (z): interleaved channels of one image
+// (px_stride = C, z_stride = 1) or a stack of single-channel images
+// (px_stride = 1, z_stride = image size).
 struct BfImage {
     const void *in;
     float *out;
@@ -52,6 +55,8 @@ struct BfImage {
     int H, W, C;
     int dtype;                // 0 f32, 1 u8
     float q_scale;
+    int in_px, out_px;        // elements between horizontally adjacent pixels
+    long long in_z, out_z;    // elements between consecutive planes z
 };
 
 namespace bf {

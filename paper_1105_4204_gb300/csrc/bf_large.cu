@@ -44,9 +44,9 @@ namespace {
 
 
 struct LrParams {
-    const void *in;
-    long long in_stride;  // elements
-    int dtype, C, ch;
+    const void *in;       // first pixel of the plane being filtered
+    long long in_stride;  // elements between rows
+    int dtype, in_px;     // element type; elements between adjacent pixels
     int H, W, r;
     int band_h, band_w;
     float a, t;           // lr_horz: weight and turns per gray level of its term
@@ -60,12 +60,6 @@ struct LrParams {
     int first;
 };
 
-__device__ __forceinline__ float load_f(const LrParams &p, int y, int x) {
-    const long long off = (long long)y * p.in_stride + (long long)x * p.C + p.ch;
-    if (p.dtype == 0) return __ldg(reinterpret_cast<const float *>(p.in) + off);
-    return (float)__ldg(reinterpret_cast<const uint8_t *>(p.in) + off);
-}
-
 // Power-of-two size of lr_vert's shared f ring: the 3L + 1 values a stream
 // needs, plus slack for the warps sharing it to be up to two chunks apart
 // (they meet at a barrier every chunk) without overwriting a value another
@@ -78,7 +72,7 @@ __host__ __device__ __forceinline__ int ring_size(int r) {
 
 template <int DT>
 __device__ __forceinline__ float load_px(const LrParams &p, int y, int x) {
-    const long long off = (long long)y * p.in_stride + (long long)x * p.C + p.ch;
+    const long long off = (long long)y * p.in_stride + (long long)x * p.in_px;
     if constexpr (DT == 0) return __ldg(reinterpret_cast<const float *>(p.in) + off);
     else return (float)__ldg(reinterpret_cast<const uint8_t *>(p.in) + off);
 }
@@ -321,7 +315,7 @@ __global__ void __launch_bounds__(64) lr_horz(const __grid_constant__ LrParams p
 // through a 32 x 33 shared tile.
 // grid: (ceil(W / 32), ceil(H / 32)); block: (32, 8)
 __global__ void lr_final(const float *__restrict__ Acc, float *__restrict__ out,
-                         float *__restrict__ q_out, int H, int W, int Hp, int C, int ch,
+                         float *__restrict__ q_out, int H, int W, int Hp, int out_px,
                          float q_scale) {
     __shared__ float tp[32][33];
     __shared__ float tq[32][33];
@@ -340,7 +334,7 @@ __global__ void lr_final(const float *__restrict__ Acc, float *__restrict__ out,
         const int y = yb + i, x = xb + threadIdx.x;
         if (x < W && y < H) {
             const float q = tq[threadIdx.x][i];
-            const size_t o = ((size_t)y * W + x) * C + ch;
+            const size_t o = ((size_t)y * W + x) * out_px;
             out[o] = tp[threadIdx.x][i] / q;
             if (q_out) q_out[o] = q * q_scale;
         }
@@ -358,10 +352,9 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     const int H = img.H, W = img.W;
     char *base = reinterpret_cast<char *>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     LrParams p{};
-    p.in = img.in;
     p.in_stride = img.in_row_stride;
     p.dtype = img.dtype;
-    p.C = img.C;
+    p.in_px = img.in_px;
     p.H = H;
     p.W = W;
     p.Hp = (H + 7) / 8 * 8;
@@ -392,8 +385,9 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
         if (dev >= 0 && dev < 64) attr[dev] = true;
     }
     const int nt = (int)pl->a32.size();
+    const int esz = img.dtype == 0 ? 4 : 1;
     for (int ch = 0; ch < img.C; ++ch) {
-        p.ch = ch;
+        p.in = reinterpret_cast<const char *>(img.in) + (long long)ch * img.in_z * esz;
         dim3 gt((W + 31) / 32, (H + 31) / 32);
         kt<<<gt, dim3(32, 8), 0, s>>>(p);
         for (int m0 = 0; m0 < nt; m0 += kVG) {
@@ -411,8 +405,10 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
             }
         }
         dim3 gf((W + 31) / 32, (H + 31) / 32);
-        lr_final<<<gf, dim3(32, 8), 0, s>>>(p.Acc, img.out, img.q_out, H, W, p.Hp, img.C, ch,
-                                            img.q_scale);
+        lr_final<<<gf, dim3(32, 8), 0, s>>>(
+            p.Acc, img.out + (long long)ch * img.out_z,
+            img.q_out ? img.q_out + (long long)ch * img.out_z : nullptr, H, W, p.Hp, img.out_px,
+            img.q_scale);
     }
     return cudaGetLastError();
 }

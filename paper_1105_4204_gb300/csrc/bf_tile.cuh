@@ -132,11 +132,11 @@ struct TileParams {
 // origin.  The term and tap arrays may live in kernel parameter space or in
 // global memory.
 struct TileJob {
-    const void *in;
-    float *out;
+    const void *in;   // this plane's first pixel
+    float *out;       // this plane's first pixel
     float *q_out;
     long long in_row_stride;
-    int H, W, C, ch, dtype;
+    int H, W, in_px, out_px, dtype;
     float q_scale;
     const float *a;
     const float *t;
@@ -154,8 +154,8 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
     float *Cc = V + G::V_FLOATS;
 
     const int tid = threadIdx.x;
-    const int x0 = jb.x0, y0 = jb.y0, ch = jb.ch;
-    const int H = jb.H, W = jb.W, C = jb.C;
+    const int x0 = jb.x0, y0 = jb.y0;
+    const int H = jb.H, W = jb.W;
 
     // ---- tile + halo of f, clamp-to-edge, converted to float
     for (int idx = tid; idx < EH * EW; idx += G::NT) {
@@ -163,7 +163,7 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
         const int j = idx - i * EW;
         const int gy = min(max(y0 - HALO + i, 0), H - 1);
         const int gx = min(max(x0 - HALO + j, 0), W - 1);
-        const long long off = (long long)gy * jb.in_row_stride + (long long)gx * C + ch;
+        const long long off = (long long)gy * jb.in_row_stride + (long long)gx * jb.in_px;
         float v;
         if (jb.dtype == 0)
             v = __ldg(reinterpret_cast<const float *>(jb.in) + off);
@@ -261,7 +261,7 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
                 const int gx = x0 + ps * TWT + k;
                 if (gx < W) {
                     const float qv = Xq[pi * G::SV + ps * TWT + k];
-                    const long long o = ((long long)gy * W + gx) * C + ch;
+                    const long long o = ((long long)gy * W + gx) * jb.out_px;
                     jb.out[o] = acc[k] / qv;
                     if (jb.q_out) jb.q_out[o] = qv * jb.q_scale;
                 }
@@ -275,14 +275,16 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT, 2)
     bf_tile_fwd(const __grid_constant__ TileParams p) {
     extern __shared__ float4 smem4[];
     TileJob jb;
-    jb.in = p.img.in;
-    jb.out = p.img.out;
-    jb.q_out = p.img.q_out;
+    const int z = blockIdx.z;
+    const int esz = p.img.dtype == 0 ? 4 : 1;
+    jb.in = reinterpret_cast<const char *>(p.img.in) + (long long)z * p.img.in_z * esz;
+    jb.out = p.img.out + (long long)z * p.img.out_z;
+    jb.q_out = p.img.q_out ? p.img.q_out + (long long)z * p.img.out_z : nullptr;
     jb.in_row_stride = p.img.in_row_stride;
     jb.H = p.img.H;
     jb.W = p.img.W;
-    jb.C = p.img.C;
-    jb.ch = blockIdx.z;
+    jb.in_px = p.img.in_px;
+    jb.out_px = p.img.out_px;
     jb.dtype = p.img.dtype;
     jb.q_scale = p.img.q_scale;
     jb.a = p.terms.a;

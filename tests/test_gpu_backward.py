@@ -140,3 +140,25 @@ def test_backward_is_deterministic(bf):
     b = _gpu_grad(bf, img, u, plan)
     np.testing.assert_array_equal(a[0], b[0])
     assert a[1] == b[1]
+
+
+def test_stack_calls_match_per_image_calls(bf):
+    import torch
+    imgs = torch.from_numpy(np.stack([synth.rectangles(70, 130, seed=s) for s in range(5)])).cuda()
+    u = torch.from_numpy(synth.upstream(tuple(imgs.shape), seed=4)).cuda()
+    for kind, ss, sr in [("gauss", 4.0, 25.0), ("box", 3.0, 30.0), ("box", 12.0, 20.0)]:
+        plan = bf.Plan(ss, sr, kind=kind)
+        out, q = bf.forward_stack(plan, imgs, return_q=True)
+        for b in range(imgs.shape[0]):
+            ob, qb = bf.forward(plan, imgs[b], return_q=True)
+            torch.testing.assert_close(out[b], ob, rtol=0, atol=0)
+            torch.testing.assert_close(q[b], qb, rtol=0, atol=0)
+        if plan.radius // 3 > 8 and kind == "box":
+            continue  # no backward kernel for box r > 8
+        g, gs = bf.backward_stack(plan, imgs, out, q, u)
+        total = 0.0
+        for b in range(imgs.shape[0]):
+            gb, gsb = bf.backward(plan, imgs[b].contiguous(), out[b], q[b], u[b].contiguous())
+            torch.testing.assert_close(g[b], gb, rtol=0, atol=0)
+            total += float(gsb)
+        assert float(gs) == pytest.approx(total, rel=1e-9, abs=1e-12)
