@@ -152,6 +152,20 @@ bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *ou
 bf_status bf_forward_stack(const bf_plan *plan, const void *in, bf_dtype dt, float *out,
                            int H, int W, int count, float *q_out, cudaStream_t stream);
 
+/*
+ * Tile-shape autotuner for bf_forward (not in the paper).  Runs each tile
+ * shape the fused kernel has for this plan's spatial support (32 x 64 tiles
+ * always; 32 x 96 tiles with wider row segments for small radii) `reps`
+ * times on the given buffers (out is overwritten), and keeps the fastest for
+ * later bf_forward calls with the same kind, radius, degree, H, W and C
+ * (process-wide, thread-safe).  Synchronises `stream`.  *shape receives the
+ * choice (-1 when the support runs on the streaming kernels, which have no
+ * shape to choose), *ms its time per call; either may be NULL.
+ */
+bf_status bf_forward_tune(const bf_plan *plan, const void *in, bf_dtype dt, float *out, int H,
+                          int W, int C, long long row_stride_elems, int reps,
+                          cudaStream_t stream, int *shape, float *ms);
+
 /* Frees the scratch buffers bf_forward allocated (all devices).  Call only
  * when no work that uses them is in flight. */
 void bf_release_scratch(void);

@@ -4,8 +4,8 @@ The compute path is the CUDA library ``libbf.so`` (built from ``csrc/`` for
 sm_103a by ``build.build()``); this package is its thin Python binding.
 """
 from .api import (BOX, GAUSS, Batch, BilateralFunction, Plan, backward, bilateral,  # noqa: F401
-                  backward_stack, forward, forward_host, forward_stack, forward_unfused)
+                  backward_stack, forward, forward_host, forward_stack, forward_unfused, tune)
 
 __all__ = ["Plan", "forward", "forward_stack", "forward_host", "forward_unfused", "backward",
-           "backward_stack", "bilateral",
+           "backward_stack", "bilateral", "tune",
            "BilateralFunction", "Batch", "GAUSS", "BOX"]

@@ -120,6 +120,18 @@ def forward(plan: Plan, img: torch.Tensor, return_q: bool = False, out: torch.Te
     return (out, q) if return_q else out
 
 
+def tune(plan: Plan, img: torch.Tensor, reps: int = 3, stream=None):
+    """Pick the fused kernel's tile shape for this plan and image size by
+    timing the candidates on ``img`` (cached for later ``forward`` calls)."""
+    dt, H, W, C, rs = _image_args(img)
+    out = torch.empty(tuple(img.shape), dtype=torch.float32, device=img.device)
+    shape, ms = ctypes.c_int(), ctypes.c_float()
+    check(lib().bf_forward_tune(plan.handle, ctypes.c_void_p(img.data_ptr()), dt,
+                                ctypes.c_void_p(out.data_ptr()), H, W, C, rs, int(reps),
+                                _stream_ptr(stream), ctypes.byref(shape), ctypes.byref(ms)))
+    return {"shape": {-1: "streaming", 0: "32x64", 1: "32x96"}[shape.value], "ms": ms.value}
+
+
 def forward_host(plan: Plan, img_host: torch.Tensor, out_host: torch.Tensor | None = None,
                  stream=None) -> torch.Tensor:
     """End-to-end call for host images: copy in (pinned host -> device), filter,

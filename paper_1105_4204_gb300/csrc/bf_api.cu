@@ -1,8 +1,10 @@
 // C-ABI entry points of libbf: argument checks, kernel selection, error text.
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 
 #include "bf_internal.h"
 
@@ -24,9 +26,30 @@ bf_status cuda_check(cudaError_t e, const char *what) {
 }
 
 int gauss_tile_radius(int R);
+int gauss_tile_shapes(int R);
 int box_tile_max_r();
-cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s);
-cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img, cudaStream_t s);
+int box_tile_shapes(int r);
+cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape);
+cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape);
+
+// Tile shapes picked by bf_forward_tune, per (kind, radius, N, H, W, planes).
+using TuneKey = std::tuple<int, int, int, int, int, int>;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tuned;
+
+static TuneKey tune_key(const bf_plan *p, const BfImage &img) {
+    return TuneKey(p->kind, p->R, p->N, img.H, img.W, img.C);
+}
+
+static int tile_shapes(const bf_plan *p) {
+    return p->kind == BF_SPATIAL_GAUSS_TRUNC ? gauss_tile_shapes(p->R) : box_tile_shapes(p->r_box);
+}
+
+static cudaError_t launch_tile_shape(const bf_plan *p, const BfImage &img, cudaStream_t s,
+                                     int shape) {
+    if (p->kind == BF_SPATIAL_GAUSS_TRUNC) return launch_tile_gauss(p, img, s, shape);
+    return launch_tile_box(p, img, s, shape);
+}
 
 size_t large_workspace(int H, int W);
 cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cudaStream_t s);
@@ -67,8 +90,13 @@ bool tile_supported(const bf_plan *p) {
 }
 
 cudaError_t launch_tile_forward(const bf_plan *p, const BfImage &img, cudaStream_t s) {
-    if (p->kind == BF_SPATIAL_GAUSS_TRUNC) return launch_tile_gauss(p, img, s);
-    return launch_tile_box(p, img, s);
+    int shape = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key(p, img));
+        if (it != g_tuned.end()) shape = it->second;
+    }
+    return launch_tile_shape(p, img, s, shape);
 }
 
 }  // namespace bf
@@ -279,4 +307,66 @@ extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const floa
     return cuda_check(launch_backward(plan, f, out, q, grad_out, grad_in, grad_sigma_r,
                                       reinterpret_cast<double *>(workspace), H, W, stream),
                       "bf_backward launch");
+}
+
+// ---- tile-shape autotuner ----------------------------------------------------
+
+extern "C" bf_status bf_forward_tune(const bf_plan *plan, const void *in, bf_dtype dt, float *out,
+                                     int H, int W, int C, long long row_stride_elems, int reps,
+                                     cudaStream_t stream, int *shape_out, float *ms_out) {
+    if (!plan || !in || !out) return fail(BF_EINVAL, "bf_forward_tune: NULL argument");
+    if (H < 1 || W < 1 || C < 1 || C > 4 || row_stride_elems < (long long)W * C)
+        return fail(BF_EINVAL, "bf_forward_tune: bad image description");
+    if (dt != BF_F32 && dt != BF_U8) return fail(BF_EINVAL, "bf_forward_tune: unknown dtype");
+    if (reps < 1) reps = 3;
+    BfImage img;
+    img.in = in;
+    img.out = out;
+    img.q_out = nullptr;
+    img.in_row_stride = row_stride_elems;
+    img.H = H;
+    img.W = W;
+    img.C = C;
+    img.dtype = (int)dt;
+    img.q_scale = plan->q_scale;
+    img.in_px = C;
+    img.out_px = C;
+    img.in_z = 1;
+    img.out_z = 1;
+    if (!tile_supported(plan)) {  // one kernel only: nothing to choose
+        if (shape_out) *shape_out = -1;
+        if (ms_out) *ms_out = 0.f;
+        return BF_OK;
+    }
+    const int n = tile_shapes(plan);
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_check(e, "bf_forward_tune");
+    float best = 1e30f;
+    int best_shape = 0;
+    for (int sh = 0; sh < n && e == cudaSuccess; ++sh) {
+        e = launch_tile_shape(plan, img, stream, sh);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+        for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch_tile_shape(plan, img, stream, sh);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            best_shape = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_check(e, "bf_forward_tune");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[tune_key(plan, img)] = best_shape;
+    }
+    if (shape_out) *shape_out = best_shape;
+    if (ms_out) *ms_out = best;
+    return BF_OK;
 }

@@ -5,11 +5,24 @@ namespace bf {
 
 int box_tile_max_r() { return 8; }
 
-cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t s) {
+// Shape 0: 32 x 64 tiles, 16-pixel segments; shape 1 (r <= 4): 32 x 96
+// tiles, 24-pixel segments.
+int box_tile_shapes(int r) { return r >= 1 && r <= 4 ? 2 : 1; }
+
+cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t s, int shape) {
     TileParams prm;
     prm.img = img0;
     fill_terms(pl, &prm.terms);
     for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) prm.taps.w[k] = 0.f;
+    if (shape == 1) {
+        switch (pl->r_box) {
+            case 1: return launch_tile<1, 1, 32, 96, 24>(prm, s);
+            case 2: return launch_tile<1, 2, 32, 96, 24>(prm, s);
+            case 3: return launch_tile<1, 3, 32, 96, 24>(prm, s);
+            case 4: return launch_tile<1, 4, 32, 96, 24>(prm, s);
+            default: break;
+        }
+    }
     switch (pl->r_box) {
         case 1: return launch_tile<1, 1, 32, 64, 16>(prm, s);
         case 2: return launch_tile<1, 2, 32, 64, 16>(prm, s);

@@ -14,13 +14,30 @@ int gauss_tile_radius(int R) {
     return -1;
 }
 
-cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s) {
+// Shape 0: 32 x 64 tiles, 16-pixel segments; shape 1 (small radii only):
+// 32 x 96 tiles, 24-pixel segments (more phase-1 work items per block and
+// less halo, at the cost of registers).
+int gauss_tile_shapes(int R) {
+    const int Ri = gauss_tile_radius(R);
+    return Ri > 0 && Ri <= 9 ? 2 : 1;
+}
+
+cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape) {
     const int Ri = gauss_tile_radius(pl->R);
     TileParams prm;
     prm.img = img;
     fill_terms(pl, &prm.terms);
     for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) prm.taps.w[k] = 0.f;
     for (int k = 0; k < 2 * pl->R + 1; ++k) prm.taps.w[k + Ri - pl->R] = pl->w1f[k];
+    if (shape == 1) {
+        switch (Ri) {
+            case 2: return launch_tile<0, 2, 32, 96, 24>(prm, s);
+            case 4: return launch_tile<0, 4, 32, 96, 24>(prm, s);
+            case 6: return launch_tile<0, 6, 32, 96, 24>(prm, s);
+            case 9: return launch_tile<0, 9, 32, 96, 24>(prm, s);
+            default: break;
+        }
+    }
     switch (Ri) {
         case 2: return launch_tile<0, 2, 32, 64, 16>(prm, s);
         case 4: return launch_tile<0, 4, 32, 64, 16>(prm, s);

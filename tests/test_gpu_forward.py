@@ -226,3 +226,19 @@ def test_row_strips_with_halo_match_full_image(bf):
             c0, c1 = st.crop
             parts.append(sub[c0:c1])
         assert np.abs(np.concatenate(parts) - full).max() <= TOL / 5
+
+
+@pytest.mark.parametrize("kind,ss", [("box", 2.0), ("gauss", 3.0), ("box", 8.0), ("box", 20.0)])
+def test_tuned_tile_shape_stays_correct(bf, oracle, kind, ss):
+    import torch
+    img = synth.smooth_field(150, 230, noise=5.0, seed=31)
+    t = torch.from_numpy(img).cuda()
+    plan = bf.Plan(ss, 25.0, kind=kind)
+    before = bf.forward(plan, t).cpu().numpy()
+    info = bf.tune(plan, t, reps=2)
+    assert info["shape"] in ("32x64", "32x96", "streaming")
+    after = bf.forward(plan, t).cpu().numpy()
+    ref = _oracle_full(oracle, img, plan) if plan.radius <= 24 else None
+    if ref is not None:
+        assert np.abs(after - ref).max() <= TOL
+    assert np.abs(after - before).max() <= TOL / 5
