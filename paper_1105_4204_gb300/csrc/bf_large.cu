@@ -1,24 +1,23 @@
 // Forward filter for the 3-pass box at large half-widths r (support 3r > 24).
 //
 // A tile plus a 3r halo no longer fits on chip, so the separable filter is
-// run as two streaming sweeps per term, with the term's filtered auxiliary
-// images passing through device memory once (small enough to stay in L2
-// between the two sweeps for images up to about 2048 x 2048):
+// run as two streaming sweeps per group of four terms, the terms' filtered
+// auxiliary images passing through device memory once:
 //
 //   lr_vert : one thread per image column and term (four terms per block,
 //             sharing a ring of f), walking down a band of rows (f loaded a
-//             few rows ahead).  The four auxiliary
-//             images of the term (cos, sin, f cos, f sin of omega f,
-//             Section 2.3) are generated on the fly and filtered by the three
-//             cascaded boxes with running sums; written transposed
-//             (column-major) so that the second sweep reads coalesced.
-//   lr_horz : one thread per image row and plane pair, walking along a band
-//             of columns of the transposed planes (loads issued a chunk
-//             ahead; the trailing inputs are read again from L2 instead of
-//             being kept on chip): the same three cascaded boxes horizontally
-//             on the (cos, sin) or the (f cos, f sin) pair, then the
-//             per-pixel combine of eq. (final-form) into Q or P.
-//   lr_final: out = P / Q, transposed back to row-major.
+//             few rows ahead).  The four auxiliary images of the term (cos,
+//             sin, f cos, f sin of omega f, Section 2.3) are generated on the
+//             fly and filtered by the three cascaded boxes with running sums;
+//             written in a blocked column layout (rows in blocks of 16, a
+//             column's 16 rows contiguous) so that the second sweep reads
+//             coalesced.
+//   lr_horz : one thread per image row, plane and term of the group, walking
+//             along a band of columns of the blocked planes: the same three
+//             cascaded boxes horizontally, then the per-pixel combine of eq.
+//             (final-form) into the term's own Q or P accumulator slot.
+//   lr_final: out = P / Q with P and Q summed over the slots, back to
+//             row-major.
 //
 // Running sums without per-pass history.  Box k of the cascade at position q
 // needs its input at q + r and q - r - 1.  Keeping one running sum per
@@ -27,7 +26,7 @@
 // only the raw input at the four positions e, e - L, e - 2L, e - 3L: the
 // newest is generated (or loaded); the other three come from a shared-memory
 // ring of f, the planes being regenerated (lr_vert), or are read again from
-// the transposed planes in L2 (lr_horz).  Each running sum is a plain sliding
+// the blocked planes (lr_horz).  Each running sum is a plain sliding
 // sum (add the incoming, subtract the outgoing), so rounding grows like the
 // usual running sum, and the half-width r is a run-time value.  The sums start
 // at zero 3r positions before the first output with the input taken as zero
@@ -43,21 +42,22 @@ namespace bf {
 namespace {
 
 
+constexpr int kVG = 8;  // terms per group: lr_vert block (they share the f ring), lr_horz launch
+
 struct LrParams {
     const void *in;       // first pixel of the plane being filtered
     long long in_stride;  // elements between rows
     int dtype, in_px;     // element type; elements between adjacent pixels
     int H, W, r;
     int band_h, band_w;
-    float a, t;           // lr_horz: weight and turns per gray level of its term
-    int slot;             // lr_horz: which of lr_vert's term slots it reads
-    int n_terms;          // lr_vert: terms in this group (<= 4)
-    float tv[4];          // lr_vert: turns per gray level of the group's terms
-    int Hp;               // column length of the column-major arrays (H rounded up to 8)
-    float *Vt;            // [4 terms][4 planes][W][Hp]: vertically filtered planes, column-major
-    float *Acc;           // [2][W][Hp]: Q and P, column-major
-    float *ft;            // [W][Hp]: the channel's f, column-major
-    int first;
+    int n_terms;          // terms in this group (<= kVG)
+    float tv[kVG];        // turns per gray level of the group's terms
+    float av[kVG];        // lr_horz: weights of the group's terms
+    int nyb;              // row blocks of the blocked column layout: ceil(H / kYB)
+    float *Vt;            // [kVG terms][4 planes] blocked planes: vertically filtered
+    float *Acc;           // [kVG slots][2] blocked planes: Q and P per term slot
+    float *ft;            // blocked plane: the channel's f
+    int first;            // lr_horz: first group (the slots start from zero)
 };
 
 // Power-of-two size of lr_vert's shared f ring: the 3L + 1 values a stream
@@ -70,6 +70,23 @@ __host__ __device__ __forceinline__ int ring_size(int r) {
     return n;
 }
 
+// Blocked column layout of the intermediate planes: rows in blocks of kYB;
+// within a block, column x holds its kYB rows contiguously and the columns
+// follow each other, so pixel (x, y) sits at
+//   (y / kYB) * W * kYB + x * kYB + y % kYB.
+// A warp of the horizontal sweep (kYB rows of one block) then finds the
+// column c of its rows at a fixed offset c * kYB from its row block: every
+// step of a chunk is an immediate offset from one pointer.
+constexpr int kYB = 16;
+
+__host__ __device__ __forceinline__ size_t blocked_plane(int H, int W) {
+    return (size_t)((H + kYB - 1) / kYB) * (size_t)W * kYB;
+}
+
+__device__ __forceinline__ size_t blocked_at(int W, int x, int y) {
+    return (size_t)(y / kYB) * (size_t)W * kYB + (size_t)x * kYB + (y % kYB);
+}
+
 template <int DT>
 __device__ __forceinline__ float load_px(const LrParams &p, int y, int x) {
     const long long off = (long long)y * p.in_stride + (long long)x * p.in_px;
@@ -77,10 +94,8 @@ __device__ __forceinline__ float load_px(const LrParams &p, int y, int x) {
     else return (float)__ldg(reinterpret_cast<const uint8_t *>(p.in) + off);
 }
 
-constexpr int kVCols = 64;    // lr_vert: columns per block
-constexpr int kVG = 4;        // lr_vert: terms per block (they share the f ring)
+constexpr int kVCols = 32;    // lr_vert: columns per block
 constexpr int kChunk = 8;     // lr_vert: steps between barriers / whose loads are issued together
-constexpr int kChunkH = 16;   // lr_horz: steps whose loads are issued together, one chunk ahead
 
 // The four auxiliary planes of one pixel value (cos, sin, f cos, f sin).
 __device__ __forceinline__ void aux4(float tm, float fv, float (&x)[4]) {
@@ -122,8 +137,8 @@ __global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ 
     const int RS = ring_size(r), M = RS - 1;
     float *ring = lv_sm + col;  // slot k at ring[k * kVCols]
     const bool col_ok = xb + col < p.W && term_ok;
-    const size_t plane = (size_t)p.W * p.Hp;
-    float *dst = p.Vt + (size_t)g * 4 * plane + (size_t)(xb + col) * p.Hp;
+    const size_t plane = blocked_plane(p.H, p.W);
+    float *dst = p.Vt + (size_t)g * 4 * plane;
     float s1[4][3], s2[4][2], s3[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -185,10 +200,12 @@ __global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ 
                 if (e0 + d < e_end) step(e0 + d, d, std::true_type{});
         }
         if (col_ok && tb >= y0) {
+            // tb is a multiple of 8: the chunk's rows lie in one row block
+            float *dc = dst + blocked_at(p.W, xb + col, tb);
             if (tb + kChunk <= y1) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    float4 *d4 = reinterpret_cast<float4 *>(dst + q * plane + tb);
+                    float4 *d4 = reinterpret_cast<float4 *>(dc + q * plane);
                     d4[0] = make_float4(st[q][0], st[q][1], st[q][2], st[q][3]);
                     d4[1] = make_float4(st[q][4], st[q][5], st[q][6], st[q][7]);
                 }
@@ -197,7 +214,7 @@ __global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ 
                 for (int q = 0; q < 4; ++q)
 #pragma unroll
                     for (int d = 0; d < kChunk; ++d)
-                        if (tb + d < y1) dst[q * plane + tb + d] = st[q][d];
+                        if (tb + d < y1) dc[q * plane + d] = st[q][d];
             }
         }
 #pragma unroll
@@ -205,7 +222,7 @@ __global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ 
     }
 }
 
-// f of one channel, row-major -> column-major (32 x 33 shared tile).
+// f of one channel, row-major -> blocked column layout (32 x 33 shared tile).
 // grid: (ceil(W / 32), ceil(H / 32)); block: (32, 8)
 template <int DT>
 __global__ void lr_transpose(const __grid_constant__ LrParams p) {
@@ -218,115 +235,161 @@ __global__ void lr_transpose(const __grid_constant__ LrParams p) {
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int x = xb + i, y = yb + threadIdx.x;
-        if (x < p.W && y < p.H) p.ft[(size_t)x * p.Hp + y] = tile[threadIdx.x][i];
+        if (x < p.W && y < p.H) p.ft[blocked_at(p.W, x, y)] = tile[threadIdx.x][i];
     }
 }
 
-// grid: (ceil(H / 32), bands along x, 2); block: 64 threads = two warps of
-// 32 rows each, lanes = rows.  blockIdx.z = 0: the (cos, sin) planes,
-// accumulated into Q; blockIdx.z = 1: the (f cos, f sin) planes,
-// accumulated into P.  Both planes of a pair share the pixel's sincos and
-// one accumulator.  The inputs at e - L, e - 2L, e - 3L are read again from
-// the transposed planes (L2) rather than kept, so no shared memory limits
-// the number of resident warps.
+// grid: (ceil(nyb / 4), bands along x, 2 * terms of the group); block: 128
+// threads = four warps, one row block (kYB = 16 rows) each.  blockIdx.z =
+// 2 * slot + pair: pair 0 filters the (cos, sin) planes of the group's term
+// `slot` into Q, pair 1 the (f cos, f sin) planes into P.  In a warp, lanes
+// 0-15 carry the first plane of the pair and lanes 16-31 the second, for the
+// same 16 rows; at an output the two halves meet through one shuffle.  Each
+// term of the group accumulates into its own slot of Acc (summed by
+// lr_final), so the group's terms run concurrently without sharing an
+// accumulator.  The inputs at e - L, e - 2L, e - 3L are read again from the
+// blocked planes (L2) rather than kept, so no shared memory limits the
+// number of resident warps.
 constexpr int kChunkG = 8;
-__global__ void __launch_bounds__(64) lr_horz(const __grid_constant__ LrParams p) {
+__global__ void __launch_bounds__(128) lr_horz(const __grid_constant__ LrParams p) {
     const int lane = threadIdx.x & 31;
-    const int pr = blockIdx.z;  // 0: Q pair, 1: P pair
-    const int y = (blockIdx.x * 2 + (threadIdx.x >> 5)) * 32 + lane;
-    const int yc = min(y, p.H - 1);
+    const int half = lane >> 4;  // 0: cos-like plane, 1: sin-like plane
+    const int pr = blockIdx.z & 1;
+    const int slot = blockIdx.z >> 1;
+    const int yb = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (yb >= p.nyb) return;  // whole warp
+    const int y = yb * kYB + (lane & (kYB - 1));
+    const int W = p.W;
+    const size_t plane = blocked_plane(p.H, W);
+    const size_t row = blocked_at(W, 0, min(y, p.H - 1));  // column 0 of this lane's row
+    const float *V = p.Vt + ((size_t)slot * 4 + 2 * pr + half) * plane + row;
+    const float *F = p.ft + row;
+    float *A = p.Acc + ((size_t)slot * 2 + pr) * plane + row;
     const int x0 = blockIdx.y * p.band_w;
-    const int x1 = min(x0 + p.band_w, p.W);
+    const int x1 = min(x0 + p.band_w, W);
     const int r = p.r, L = 2 * r + 1;
-    const int p0 = x0 - 3 * r;
-    const size_t plane = (size_t)p.W * p.Hp;
-    const float *Vc = p.Vt + (size_t)p.slot * 4 * plane + (size_t)(2 * pr) * plane + yc;
-    const float *Vs = Vc + plane;
-    const float *F = p.ft + yc;
-    float *A = p.Acc + (size_t)pr * plane + yc;
+    const int p0 = x0 - 3 * r;  // inputs before p0 count as zero
     const int e_end = x1 + 3 * r;
-    const float am = p.a, tm = p.t;
-    const bool row_ok = y < p.H;
+    const float am = p.av[slot], tm = p.tv[slot];
+    // cos(x) = sin(x + quarter turn): each half evaluates one sine
+    const float ph = half ? 0.f : 0.25f;
+    const bool store = half == 0 && y < p.H;
     const bool first = p.first;
-    float c1a = 0.f, c1b = 0.f, c1c = 0.f, c2a = 0.f, c2b = 0.f, c3 = 0.f;
-    float z1a = 0.f, z1b = 0.f, z1c = 0.f, z2a = 0.f, z2b = 0.f, z3 = 0.f;
-    // per chunk: both planes at e, e-L, e-2L, e-3L (0 before p0), and at the
-    // chunk's outputs the pixel value and the pair's running accumulator
-    float cv[kChunkG][8], cf[kChunkG], ca[kChunkG];
-    float nv[kChunkG][8], nf[kChunkG], na[kChunkG];
-    auto fetch = [&](int eb, float (&v)[kChunkG][8], float (&f)[kChunkG], float (&a)[kChunkG]) {
-#pragma unroll
-        for (int d = 0; d < kChunkG; ++d) {
-            const int e = eb + d;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int pos = e - k * L;
-                const size_t o = (size_t)min(max(pos, 0), p.W - 1) * p.Hp;
-                const bool ok = pos >= p0;
-                v[d][2 * k] = ok ? __ldg(Vc + o) : 0.f;
-                v[d][2 * k + 1] = ok ? __ldg(Vs + o) : 0.f;
-            }
-            const size_t t = (size_t)min(max(e - 3 * r, 0), p.W - 1) * p.Hp;
-            f[d] = __ldg(F + t);
-            a[d] = first ? 0.f : A[t];
-        }
-    };
-    fetch(p0, cv, cf, ca);
+    float s1a = 0.f, s1b = 0.f, s1c = 0.f, s2a = 0.f, s2b = 0.f, s3 = 0.f;
     for (int e0 = p0; e0 < e_end; e0 += kChunkG) {
-        fetch(e0 + kChunkG, nv, nf, na);
-        const bool full = e0 + kChunkG <= e_end && e0 - 3 * r >= x0;  // uniform
+        // the plane at e, e - L, e - 2L, e - 3L for the chunk's steps (0 before p0)
+        float cv[kChunkG][4];
+        const bool edge = max(e0 - 3 * L, p0) < 0 || e0 + kChunkG > W;  // uniform
+        if (!edge) {
+            const float *v0 = V + (ptrdiff_t)e0 * kYB;
+#pragma unroll
+            for (int d = 0; d < kChunkG; ++d) cv[d][0] = __ldg(v0 + d * kYB);
+#pragma unroll
+            for (int k = 1; k < 4; ++k) {
+                const int rel = e0 - k * L - p0;  // step d valid iff rel + d >= 0
+                const float *vk = v0 - (ptrdiff_t)k * L * kYB;
+                if (rel >= 0) {
+#pragma unroll
+                    for (int d = 0; d < kChunkG; ++d) cv[d][k] = __ldg(vk + d * kYB);
+                } else if (rel > -kChunkG) {
+#pragma unroll
+                    for (int d = 0; d < kChunkG; ++d) {
+                        const float v = __ldg(vk + max(d, -rel) * kYB);
+                        cv[d][k] = rel + d >= 0 ? v : 0.f;
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < kChunkG; ++d) cv[d][k] = 0.f;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < kChunkG; ++d) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int pos = e0 + d - k * L;
+                    const float v = __ldg(V + (ptrdiff_t)min(max(pos, 0), W - 1) * kYB);
+                    cv[d][k] = pos >= p0 ? v : 0.f;
+                }
+            }
+        }
+        const int t0 = e0 - 3 * r;  // output column of step 0
+        if (t0 + kChunkG <= x0) {
+            // warm-up chunk: no outputs
+#pragma unroll
+            for (int d = 0; d < kChunkG; ++d) {
+                s1a += cv[d][0] - cv[d][1];
+                s1b += cv[d][1] - cv[d][2];
+                s1c += cv[d][2] - cv[d][3];
+                s2a += s1a - s1b;
+                s2b += s1b - s1c;
+                s3 += s2a - s2b;
+            }
+            continue;
+        }
+        // the pixel value and the slot's accumulator at the chunk's outputs
+        float cf[kChunkG], ca[kChunkG];
+        if (t0 >= x0 && t0 + kChunkG <= x1) {  // uniform
+            const float *f0 = F + (ptrdiff_t)t0 * kYB;
+            const float *a0 = A + (ptrdiff_t)t0 * kYB;
+#pragma unroll
+            for (int d = 0; d < kChunkG; ++d) {
+                cf[d] = __ldg(f0 + d * kYB);
+                ca[d] = first ? 0.f : a0[d * kYB];
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < kChunkG; ++d) {
+                const ptrdiff_t o = (ptrdiff_t)min(max(t0 + d, 0), W - 1) * kYB;
+                cf[d] = __ldg(F + o);
+                ca[d] = first ? 0.f : A[o];
+            }
+        }
+        // steps past e_end (last chunk) run on clamped inputs and store nothing
+        float o3[kChunkG];
 #pragma unroll
         for (int d = 0; d < kChunkG; ++d) {
-            const int e = e0 + d;
-            if (!full && e >= e_end) break;
-            const float *v = cv[d];
-            c1a += v[0] - v[2];
-            c1b += v[2] - v[4];
-            c1c += v[4] - v[6];
-            c2a += c1a - c1b;
-            c2b += c1b - c1c;
-            c3 += c2a - c2b;
-            z1a += v[1] - v[3];
-            z1b += v[3] - v[5];
-            z1c += v[5] - v[7];
-            z2a += z1a - z1b;
-            z2b += z1b - z1c;
-            z3 += z2a - z2b;
-            const int t = e - 3 * r;  // output column of this step
-            if (full ? row_ok : (t >= x0 && row_ok)) {
-                float rr = tm * cf[d];
-                rr = rr - rintf(rr);
-                float sn, cs;
-                __sincosf(kTwoPi * rr, &sn, &cs);
-                A[(size_t)t * p.Hp] = fmaf(am * cs, c3, fmaf(am * sn, z3, ca[d]));
-            }
+            s1a += cv[d][0] - cv[d][1];
+            s1b += cv[d][1] - cv[d][2];
+            s1c += cv[d][2] - cv[d][3];
+            s2a += s1a - s1b;
+            s2b += s1b - s1c;
+            s3 += s2a - s2b;
+            o3[d] = s3;
         }
 #pragma unroll
         for (int d = 0; d < kChunkG; ++d) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) cv[d][k] = nv[d][k];
-            cf[d] = nf[d];
-            ca[d] = na[d];
+            float rr = fmaf(tm, cf[d], ph);
+            rr = rr - rintf(rr);
+            const float mine = am * __sinf(kTwoPi * rr) * o3[d];
+            const float other = __shfl_down_sync(0xffffffffu, mine, 16);
+            const int t = t0 + d;
+            if (store && t >= x0 && t < x1) A[(ptrdiff_t)t * kYB] = ca[d] + (mine + other);
         }
     }
 }
 
-// out = P / Q (accumulator 1 / accumulator 0), column-major -> row-major
-// through a 32 x 33 shared tile.
+// out = P / Q, with Q and P the sums over the used term slots of Acc (in
+// slot order), blocked column layout -> row-major through a 32 x 33 shared
+// tile.
 // grid: (ceil(W / 32), ceil(H / 32)); block: (32, 8)
-__global__ void lr_final(const float *__restrict__ Acc, float *__restrict__ out,
-                         float *__restrict__ q_out, int H, int W, int Hp, int out_px,
-                         float q_scale) {
+__global__ void lr_final(const float *__restrict__ Acc, int n_slots, float *__restrict__ out,
+                         float *__restrict__ q_out, int H, int W, int out_px, float q_scale) {
     __shared__ float tp[32][33];
     __shared__ float tq[32][33];
-    const size_t plane = (size_t)W * Hp;
+    const size_t plane = blocked_plane(H, W);
     const int xb = blockIdx.x * 32, yb = blockIdx.y * 32;
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int x = xb + i, y = yb + threadIdx.x;
         if (x < W && y < H) {
-            const size_t o = (size_t)x * Hp + y;
-            tq[i][threadIdx.x] = Acc[o];
-            tp[i][threadIdx.x] = Acc[plane + o];
+            const size_t o = blocked_at(W, x, y);
+            float q = Acc[o], pp = Acc[plane + o];
+            for (int s = 1; s < n_slots; ++s) {
+                q += Acc[2 * s * plane + o];
+                pp += Acc[(2 * s + 1) * plane + o];
+            }
+            tq[i][threadIdx.x] = q;
+            tp[i][threadIdx.x] = pp;
         }
     }
     __syncthreads();
@@ -344,8 +407,7 @@ __global__ void lr_final(const float *__restrict__ Acc, float *__restrict__ out,
 }  // namespace
 
 size_t large_workspace(int H, int W) {
-    const size_t Hp = ((size_t)H + 7) / 8 * 8;
-    return (size_t)(4 * kVG + 3) * Hp * (size_t)W * sizeof(float) + 256;
+    return (size_t)(4 * kVG + 2 * kVG + 1) * blocked_plane(H, W) * sizeof(float) + 256;
 }
 
 cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cudaStream_t s) {
@@ -357,17 +419,12 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     p.in_px = img.in_px;
     p.H = H;
     p.W = W;
-    p.Hp = (H + 7) / 8 * 8;
+    p.nyb = (H + kYB - 1) / kYB;
     p.r = pl->r_box;
     p.Vt = reinterpret_cast<float *>(base);
-    p.Acc = p.Vt + (size_t)4 * kVG * p.Hp * W;
-    p.ft = p.Acc + (size_t)2 * p.Hp * W;
-    // bands (multiples of 8 rows): long enough to amortise the 6r warm-up,
-    // short enough to fill the GPU
-    p.band_h = std::max(256, 8 * p.r);
-    p.band_w = std::max(256, 8 * p.r);
-    const int nbh = (H + p.band_h - 1) / p.band_h;
-    const int nbw = (W + p.band_w - 1) / p.band_w;
+    const size_t plane = blocked_plane(H, W);
+    p.Acc = p.Vt + (size_t)4 * kVG * plane;
+    p.ft = p.Acc + (size_t)2 * kVG * plane;
     const int RS = ring_size(p.r);
     const size_t sm_v = sizeof(float) * (size_t)kVCols * RS;
     if (sm_v > 227 * 1024) return cudaErrorInvalidValue;
@@ -384,7 +441,27 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
         }
         if (dev >= 0 && dev < 64) attr[dev] = true;
     }
+    int n_sm = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv, kVCols * kVG, sm_v);
+    if (e != cudaSuccess) return e;
+    const int resident_vert = std::max(1, n_sm * per_sm);
+    // Bands.  lr_vert's (multiples of 8 rows): as many as one wave of
+    // resident blocks holds (a partial second wave costs a whole band's time).
+    // lr_horz's: about 2048 warps in all, which keeps the working set of the
+    // trailing reads in L2.  Both stay at least 12r long (the 6r warm-up at
+    // most half a band).
+    const int min_band = 12 * p.r;
+    const int ncb = (W + kVCols - 1) / kVCols;
+    const int nbh_max = std::max(1, std::min(resident_vert / ncb, H / min_band));
+    p.band_h = ((H + nbh_max - 1) / nbh_max + 7) / 8 * 8;
+    const int nbh = (H + p.band_h - 1) / p.band_h;
     const int nt = (int)pl->a32.size();
+    const int g_warps = p.nyb * 2 * std::min(kVG, nt);
+    const int nbw_max = std::max(1, std::min((2048 + g_warps / 2) / g_warps, W / min_band));
+    p.band_w = ((W + nbw_max - 1) / nbw_max + 7) / 8 * 8;
+    const int nbw = (W + p.band_w - 1) / p.band_w;
     const int esz = img.dtype == 0 ? 4 : 1;
     for (int ch = 0; ch < img.C; ++ch) {
         p.in = reinterpret_cast<const char *>(img.in) + (long long)ch * img.in_z * esz;
@@ -392,22 +469,20 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
         kt<<<gt, dim3(32, 8), 0, s>>>(p);
         for (int m0 = 0; m0 < nt; m0 += kVG) {
             p.n_terms = std::min(kVG, nt - m0);
-            for (int g = 0; g < kVG; ++g) p.tv[g] = pl->turns32[std::min(m0 + g, nt - 1)];
+            for (int g = 0; g < kVG; ++g) {
+                p.tv[g] = pl->turns32[std::min(m0 + g, nt - 1)];
+                p.av[g] = pl->a32[std::min(m0 + g, nt - 1)];
+            }
+            p.first = m0 == 0;
             dim3 gv((W + kVCols - 1) / kVCols, nbh);
             kv<<<gv, kVCols * kVG, sm_v, s>>>(p);
-            for (int g = 0; g < p.n_terms; ++g) {
-                p.slot = g;
-                p.a = pl->a32[m0 + g];
-                p.t = pl->turns32[m0 + g];
-                p.first = m0 + g == 0;
-                dim3 gh((H + 63) / 64, nbw, 2);
-                lr_horz<<<gh, 64, 0, s>>>(p);
-            }
+            dim3 gh((p.nyb + 3) / 4, nbw, 2 * p.n_terms);
+            lr_horz<<<gh, 128, 0, s>>>(p);
         }
         dim3 gf((W + 31) / 32, (H + 31) / 32);
         lr_final<<<gf, dim3(32, 8), 0, s>>>(
-            p.Acc, img.out + (long long)ch * img.out_z,
-            img.q_out ? img.q_out + (long long)ch * img.out_z : nullptr, H, W, p.Hp, img.out_px,
+            p.Acc, std::min(kVG, nt), img.out + (long long)ch * img.out_z,
+            img.q_out ? img.q_out + (long long)ch * img.out_z : nullptr, H, W, img.out_px,
             img.q_scale);
     }
     return cudaGetLastError();

@@ -170,6 +170,19 @@ def test_box_large_radius(bf, oracle, r, H, W):
     np.testing.assert_allclose(q, qref, rtol=2e-4, atol=1e-7)
 
 
+@pytest.mark.parametrize("N", [1, 2, 11, 17, 18])
+def test_box_large_radius_term_groups(bf, oracle, N):
+    # the streaming sweeps take the terms in groups of eight, one accumulator
+    # slot per term of a group: 1, 2, 6, 9 and 10 terms leave slots unused or
+    # a partial last group
+    sigma_r = 1.001 * 2 * 255.0 / (np.pi * np.sqrt(N))
+    img = synth.rectangles(45, 83, n_rect=6, noise=8.0, seed=N)
+    plan = bf.Plan(12.0, sigma_r, kind="box", radius=12, N=N)
+    out = _run(bf, img, plan)
+    ref = _oracle_full(oracle, img, plan)
+    assert np.abs(out - ref).max() <= TOL
+
+
 def test_box_large_radius_u8_channels(bf, oracle):
     img = synth.rect_disk_u8(60, 75, C=3, n_shapes=8, seed=12)
     plan = bf.Plan(12.0, 30.0, kind="box")
