@@ -130,9 +130,10 @@ bf_status bf_plan_weights(const bf_plan *plan, double *w1, int cap, int *count);
  *   stream           : CUDA stream
  * Kernels: the fused tile kernel serves the truncated Gaussian (R <= 24) and
  * the box with r <= 8.  For the box with 8 < r <= 64 the support does not fit
- * on chip and the filter runs as streaming sweeps (vertical, then horizontal,
- * eight terms at a time) through a scratch buffer of about 49 * H * W floats
- * that the library allocates on the current device the first time it is needed,
+ * on chip and the filter runs as streaming sweeps (vertical, then horizontal)
+ * through a scratch buffer of about (4 * terms + 17) * H * W floats (terms
+ * capped so that the vertical sweep's output stays within 4 GiB) that the
+ * library allocates on the current device the first time it is needed,
  * and keeps for reuse until bf_release_scratch().  The first such call on a
  * device must therefore not happen during stream capture.
  * Errors: BF_EINVAL (NULL pointers, sizes), BF_EUNSUPPORTED (C > 4),

@@ -51,7 +51,7 @@ static cudaError_t launch_tile_shape(const bf_plan *p, const BfImage &img, cudaS
     return launch_tile_box(p, img, s, shape);
 }
 
-size_t large_workspace(int H, int W);
+size_t large_workspace(const bf_plan *pl, int H, int W);
 cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cudaStream_t s);
 
 // Library-owned scratch for the large-radius box path, one buffer per device,
@@ -148,7 +148,7 @@ static bf_status forward_planes(const bf_plan *plan, const BfImage &img, cudaStr
         return cuda_check(launch_tile_forward(plan, img, stream), who);
     if (plan->kind == BF_SPATIAL_BOX_ITER) {
         void *ws = nullptr;
-        cudaError_t e = get_scratch(large_workspace(H, W), &ws);
+        cudaError_t e = get_scratch(large_workspace(plan, H, W), &ws);
         if (e == cudaErrorMemoryAllocation)
             return fail(BF_ENOMEM, std::string(who) + ": cannot allocate the large-radius scratch");
         if (e != cudaSuccess) return cuda_check(e, who);

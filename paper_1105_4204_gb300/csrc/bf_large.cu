@@ -1,21 +1,23 @@
 // Forward filter for the 3-pass box at large half-widths r (support 3r > 24).
 //
 // A tile plus a 3r halo no longer fits on chip, so the separable filter is
-// run as two streaming sweeps per group of four terms, the terms' filtered
-// auxiliary images passing through device memory once:
+// run as two streaming sweeps, the terms' filtered auxiliary images passing
+// through device memory once:
 //
 //   lr_vert : one thread per image column and term (four terms per block,
-//             sharing a ring of f), walking down a band of rows (f loaded a
-//             few rows ahead).  The four auxiliary images of the term (cos,
-//             sin, f cos, f sin of omega f, Section 2.3) are generated on the
-//             fly and filtered by the three cascaded boxes with running sums;
+//             sharing a ring of f; all terms in one launch while their planes
+//             fit 4 GiB), walking down a band of rows (f loaded a few rows
+//             ahead).  The four auxiliary images of the term (cos, sin,
+//             f cos, f sin of omega f, Section 2.3) are generated on the fly
+//             and filtered by the three cascaded boxes with running sums;
 //             written in a blocked column layout (rows in blocks of 16, a
 //             column's 16 rows contiguous) so that the second sweep reads
 //             coalesced.
-//   lr_horz : one thread per image row, plane and term of the group, walking
-//             along a band of columns of the blocked planes: the same three
-//             cascaded boxes horizontally, then the per-pixel combine of eq.
-//             (final-form) into the term's own Q or P accumulator slot.
+//   lr_horz : one thread per image row, plane and term of a launch of at most
+//             eight terms, walking along a band of columns of the blocked
+//             planes: the same three cascaded boxes horizontally, then the
+//             per-pixel combine of eq. (final-form) into the term's own Q or P
+//             accumulator slot.
 //   lr_final: out = P / Q with P and Q summed over the slots, back to
 //             row-major.
 //
@@ -32,6 +34,7 @@
 // at zero 3r positions before the first output with the input taken as zero
 // before that point, so the first 6r steps of a band are warm-up.
 #include <algorithm>
+#include <vector>
 #include <type_traits>
 
 #include "bf_internal.h"
@@ -42,7 +45,9 @@ namespace bf {
 namespace {
 
 
-constexpr int kVG = 8;  // terms per group: lr_vert block (they share the f ring), lr_horz launch
+constexpr int kVB = 4;     // lr_vert: terms per block (they share the f ring)
+constexpr int kVMax = 64;  // most terms one lr_vert launch filters
+constexpr int kHG = 8;     // most terms one lr_horz launch filters (accumulator slots)
 
 struct LrParams {
     const void *in;       // first pixel of the plane being filtered
@@ -50,14 +55,15 @@ struct LrParams {
     int dtype, in_px;     // element type; elements between adjacent pixels
     int H, W, r;
     int band_h, band_w;
-    int n_terms;          // terms in this group (<= kVG)
-    float tv[kVG];        // turns per gray level of the group's terms
-    float av[kVG];        // lr_horz: weights of the group's terms
+    int n_terms;          // terms of this launch (lr_vert <= kVMax, lr_horz <= kHG)
+    float tv[kVMax];      // lr_vert: turns per gray level of its terms
+    float th[kHG], ah[kHG];  // lr_horz: turns and weights of its terms
+    int h0;               // lr_horz: Vt slot of its first term
     int nyb;              // row blocks of the blocked column layout: ceil(H / kYB)
-    float *Vt;            // [kVG terms][4 planes] blocked planes: vertically filtered
-    float *Acc;           // [kVG slots][2] blocked planes: Q and P per term slot
+    float *Vt;            // [lr_vert's terms][4 planes] blocked planes: vertically filtered
+    float *Acc;           // [kHG slots][2] blocked planes: Q and P per term slot
     float *ft;            // blocked plane: the channel's f
-    int first;            // lr_horz: first group (the slots start from zero)
+    int first;            // lr_horz: first launch of the channel (the slots start from zero)
 };
 
 // Power-of-two size of lr_vert's shared f ring: the 3L + 1 values a stream
@@ -109,24 +115,25 @@ __device__ __forceinline__ void aux4(float tm, float fv, float (&x)[4]) {
     x[3] = fv * sn;
 }
 
-// grid: (ceil(W / kVCols), bands); block: kVCols x kVG threads, thread
-// (column, term g) computes the four planes of term g for one column.  The
-// kVG terms share one ring of the last ring_size(r) values of f per column
+// grid: (ceil(W / kVCols), bands, ceil(terms / kVB)); block: kVCols x kVB
+// threads, thread (column, term g) computes the four planes of term g for one
+// column.  The kVB terms of a block share one ring of the last ring_size(r)
+// values of f per column
 // (every thread writes the same value into it; a barrier per chunk keeps the
 // warps within kChunk steps of each other, far less than the ring's slack).
 // Chunks are aligned so that step d of a chunk produces output row
 // 8k + d of the band: the eight outputs of a chunk stay in registers and
 // leave as two 16-byte stores per plane.  Dynamic smem: the f ring.
 template <int DT>
-__global__ void __launch_bounds__(kVCols * kVG) lr_vert(const __grid_constant__ LrParams p) {
+__global__ void __launch_bounds__(kVCols * kVB) lr_vert(const __grid_constant__ LrParams p) {
     extern __shared__ float lv_sm[];
     const int tid = threadIdx.x;
     const int col = tid % kVCols;
-    const int g = tid / kVCols;
+    const int g = blockIdx.z * kVB + tid / kVCols;
     const int xb = blockIdx.x * kVCols;
     const int xc = min(xb + col, p.W - 1);
     const bool term_ok = g < p.n_terms;
-    const float tm = p.tv[g];
+    const float tm = p.tv[min(g, p.n_terms - 1)];
     const int y0 = blockIdx.y * p.band_h;
     const int y1 = min(y0 + p.band_h, p.H);
     const int r = p.r, L = 2 * r + 1;
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(128) lr_horz(const __grid_constant__ LrParams 
     const int W = p.W;
     const size_t plane = blocked_plane(p.H, W);
     const size_t row = blocked_at(W, 0, min(y, p.H - 1));  // column 0 of this lane's row
-    const float *V = p.Vt + ((size_t)slot * 4 + 2 * pr + half) * plane + row;
+    const float *V = p.Vt + ((size_t)(p.h0 + slot) * 4 + 2 * pr + half) * plane + row;
     const float *F = p.ft + row;
     float *A = p.Acc + ((size_t)slot * 2 + pr) * plane + row;
     const int x0 = blockIdx.y * p.band_w;
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(128) lr_horz(const __grid_constant__ LrParams 
     const int r = p.r, L = 2 * r + 1;
     const int p0 = x0 - 3 * r;  // inputs before p0 count as zero
     const int e_end = x1 + 3 * r;
-    const float am = p.av[slot], tm = p.tv[slot];
+    const float am = p.ah[slot], tm = p.th[slot];
     // cos(x) = sin(x + quarter turn): each half evaluates one sine
     const float ph = half ? 0.f : 0.25f;
     const bool store = half == 0 && y < p.H;
@@ -406,12 +413,24 @@ __global__ void lr_final(const float *__restrict__ Acc, int n_slots, float *__re
 
 }  // namespace
 
-size_t large_workspace(int H, int W) {
-    return (size_t)(4 * kVG + 2 * kVG + 1) * blocked_plane(H, W) * sizeof(float) + 256;
+// Terms per lr_vert launch: all of them while their filtered planes stay
+// within 4 GiB, else fewer (at least one lr_horz launch's worth).
+static int vert_terms(const bf_plan *pl, int H, int W) {
+    const size_t term_bytes = 4 * blocked_plane(H, W) * sizeof(float);
+    const size_t budget = (size_t)4 << 30;
+    const int nt = (int)pl->a32.size();
+    const int cap = (int)std::max<size_t>(kHG, std::min<size_t>(kVMax, budget / term_bytes));
+    return std::min(nt, cap);
+}
+
+size_t large_workspace(const bf_plan *pl, int H, int W) {
+    const size_t planes = 4 * (size_t)vert_terms(pl, H, W) + 2 * kHG + 1;
+    return planes * blocked_plane(H, W) * sizeof(float) + 256;
 }
 
 cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cudaStream_t s) {
     const int H = img.H, W = img.W;
+    const int nt = (int)pl->a32.size();
     char *base = reinterpret_cast<char *>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     LrParams p{};
     p.in_stride = img.in_row_stride;
@@ -421,10 +440,11 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     p.W = W;
     p.nyb = (H + kYB - 1) / kYB;
     p.r = pl->r_box;
-    p.Vt = reinterpret_cast<float *>(base);
+    const int gv_max = vert_terms(pl, H, W);
     const size_t plane = blocked_plane(H, W);
-    p.Acc = p.Vt + (size_t)4 * kVG * plane;
-    p.ft = p.Acc + (size_t)2 * kVG * plane;
+    p.Vt = reinterpret_cast<float *>(base);
+    p.Acc = p.Vt + (size_t)4 * gv_max * plane;
+    p.ft = p.Acc + (size_t)2 * kHG * plane;
     const int RS = ring_size(p.r);
     const size_t sm_v = sizeof(float) * (size_t)kVCols * RS;
     if (sm_v > 227 * 1024) return cudaErrorInvalidValue;
@@ -444,9 +464,17 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     int n_sm = 0, per_sm = 0;
     e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv, kVCols * kVG, sm_v);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kv, kVCols * kVB, sm_v);
     if (e != cudaSuccess) return e;
     const int resident_vert = std::max(1, n_sm * per_sm);
+
+    // lr_horz launches: ceil(nt / kHG) of them, sizes as equal as possible
+    // and non-increasing (the first launch, which starts every slot from
+    // zero, is the largest); each lr_vert launch covers whole lr_horz launches.
+    const int n_h = (nt + kHG - 1) / kHG;
+    std::vector<int> h_size(n_h);
+    for (int i = 0; i < n_h; ++i) h_size[i] = nt / n_h + (i < nt % n_h ? 1 : 0);
+
     // Bands.  lr_vert's (multiples of 8 rows): as many as one wave of
     // resident blocks holds (a partial second wave costs a whole band's time).
     // lr_horz's: about 2048 warps in all, which keeps the working set of the
@@ -454,34 +482,49 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     // most half a band).
     const int min_band = 12 * p.r;
     const int ncb = (W + kVCols - 1) / kVCols;
-    const int nbh_max = std::max(1, std::min(resident_vert / ncb, H / min_band));
+    const int zb_max = (gv_max + kVB - 1) / kVB;
+    const int nbh_max = std::max(1, std::min(resident_vert / (ncb * zb_max), H / min_band));
     p.band_h = ((H + nbh_max - 1) / nbh_max + 7) / 8 * 8;
     const int nbh = (H + p.band_h - 1) / p.band_h;
-    const int nt = (int)pl->a32.size();
-    const int g_warps = p.nyb * 2 * std::min(kVG, nt);
+    const int g_warps = p.nyb * 2 * h_size[0];
     const int nbw_max = std::max(1, std::min((2048 + g_warps / 2) / g_warps, W / min_band));
     p.band_w = ((W + nbw_max - 1) / nbw_max + 7) / 8 * 8;
     const int nbw = (W + p.band_w - 1) / p.band_w;
+
     const int esz = img.dtype == 0 ? 4 : 1;
     for (int ch = 0; ch < img.C; ++ch) {
         p.in = reinterpret_cast<const char *>(img.in) + (long long)ch * img.in_z * esz;
         dim3 gt((W + 31) / 32, (H + 31) / 32);
         kt<<<gt, dim3(32, 8), 0, s>>>(p);
-        for (int m0 = 0; m0 < nt; m0 += kVG) {
-            p.n_terms = std::min(kVG, nt - m0);
-            for (int g = 0; g < kVG; ++g) {
-                p.tv[g] = pl->turns32[std::min(m0 + g, nt - 1)];
-                p.av[g] = pl->a32[std::min(m0 + g, nt - 1)];
+        int h = 0, m0 = 0;
+        while (h < n_h) {
+            // lr_horz launches [h, h1) fit one lr_vert launch
+            int h1 = h, nv = 0;
+            while (h1 < n_h && nv + h_size[h1] <= gv_max) nv += h_size[h1++];
+            if (h1 == h) return cudaErrorInvalidValue;  // cannot happen: h_size <= kHG <= gv_max
+            p.n_terms = nv;
+            for (int g = 0; g < kVMax; ++g) p.tv[g] = pl->turns32[m0 + std::min(g, nv - 1)];
+            dim3 gv(ncb, nbh, (nv + kVB - 1) / kVB);
+            kv<<<gv, kVCols * kVB, sm_v, s>>>(p);
+            int off = 0;
+            for (; h < h1; ++h) {
+                p.n_terms = h_size[h];
+                p.h0 = off;
+                for (int g = 0; g < kHG; ++g) {
+                    const int m = m0 + off + std::min(g, h_size[h] - 1);
+                    p.th[g] = pl->turns32[m];
+                    p.ah[g] = pl->a32[m];
+                }
+                p.first = h == 0;
+                dim3 gh((p.nyb + 3) / 4, nbw, 2 * p.n_terms);
+                lr_horz<<<gh, 128, 0, s>>>(p);
+                off += h_size[h];
             }
-            p.first = m0 == 0;
-            dim3 gv((W + kVCols - 1) / kVCols, nbh);
-            kv<<<gv, kVCols * kVG, sm_v, s>>>(p);
-            dim3 gh((p.nyb + 3) / 4, nbw, 2 * p.n_terms);
-            lr_horz<<<gh, 128, 0, s>>>(p);
+            m0 += nv;
         }
         dim3 gf((W + 31) / 32, (H + 31) / 32);
         lr_final<<<gf, dim3(32, 8), 0, s>>>(
-            p.Acc, std::min(kVG, nt), img.out + (long long)ch * img.out_z,
+            p.Acc, h_size[0], img.out + (long long)ch * img.out_z,
             img.q_out ? img.q_out + (long long)ch * img.out_z : nullptr, H, W, img.out_px,
             img.q_scale);
     }
