@@ -104,15 +104,20 @@ constexpr int kVCols = 32;    // lr_vert: columns per block
 constexpr int kChunk = 8;     // lr_vert: steps between barriers / whose loads are issued together
 
 // The four auxiliary planes of one pixel value (cos, sin, f cos, f sin).
+// The products are rounded explicitly (__fmul_rn is never fused into an
+// FMA): a value regenerated from the f ring must equal, bit for bit, the one
+// generated when it entered, or the running sums lose the exact shifted-copy
+// relation between them and their rounding errors integrate (error growing
+// like n^2.5 over an n-row band instead of n^0.5).
 __device__ __forceinline__ void aux4(float tm, float fv, float (&x)[4]) {
-    float r = tm * fv;
+    float r = __fmul_rn(tm, fv);
     r = r - rintf(r);
     float sn, cs;
     __sincosf(kTwoPi * r, &sn, &cs);
     x[0] = cs;
     x[1] = sn;
-    x[2] = fv * cs;
-    x[3] = fv * sn;
+    x[2] = __fmul_rn(fv, cs);
+    x[3] = __fmul_rn(fv, sn);
 }
 
 // grid: (ceil(W / kVCols), bands, ceil(terms / kVB)); block: kVCols x kVB

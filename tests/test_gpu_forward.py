@@ -210,6 +210,54 @@ def test_config2_full_size_sampled(bf, oracle, sigma_s):
     assert err <= TOL
 
 
+def test_box_large_radius_error_does_not_grow_along_the_sweep(bf, oracle):
+    # The vertical sweep runs one band over all 2048 rows here.  Its running
+    # sums stay accurate only if a regenerated plane value equals the one
+    # generated when it entered bit for bit; with a product fused into an FMA
+    # at one of the two places the error grew like n^2.5 down the band (about
+    # 3e-3 on the last row against 2e-4 on the first).
+    img = synth.smooth_field(2048, 2048, noise=5.0, seed=0)
+    plan = bf.Plan(32.0, 20.0, kind="box")
+    out = _run(bf, img, plan)
+    w1 = plan_w1(oracle, plan)
+    cols = np.arange(0, 2048, 8)
+    errs = {}
+    for name, row in [("first row", 0), ("row 1024", 1024), ("last row", 2047)]:
+        idx = row * 2048 + cols
+        ref = oracle.bf_brute_at(img.astype(np.float64), idx, sigma_r=20.0, w1=w1, N=plan.N)
+        errs[name] = float(np.abs(out.ravel()[idx] - ref).max())
+    print("box r=32 2048^2 max abs err by row:", errs)
+    assert max(errs.values()) <= 1e-3
+
+
+@pytest.mark.parametrize("sigma_r", [10.0, 50.0])
+def test_config3_u8_hwc_full_size_sampled(bf, oracle, sigma_r):
+    # 4096 x 4096 x 3 u8 interleaved (rectangles and disks plus noise),
+    # truncated Gaussian sigma_s = 6 (R = 18); sigma_r = 10 gives N = 264 (50
+    # coefficients zero in FP32 and skipped), sigma_r = 50 gives N = 11.
+    # Checked per channel on every border pixel plus seeded interior pixels.
+    img = synth.rect_disk_u8(4096, 4096, 3, seed=0)
+    plan = bf.Plan(6.0, sigma_r, kind="gauss")
+    assert plan.radius == 18 and plan.N == (264 if sigma_r == 10.0 else 11)
+    out = _run(bf, img, plan)
+    assert out.shape == (4096, 4096, 3) and out.dtype == np.float32
+    idx = synth.sample_indices(4096, 4096, 2048, seed=11)
+    w1 = plan_w1(oracle, plan)
+    err = err_g = 0.0
+    for c in range(3):
+        ch = img[..., c].astype(np.float64)
+        got = out[..., c].ravel()[idx]
+        ref = oracle.bf_brute_at(ch, idx, sigma_r=sigma_r, w1=w1, N=plan.N)
+        err = max(err, float(np.abs(got - ref).max()))
+        # distance to the Gaussian range kernel the raised cosine approximates
+        # (Section 2.4): reported, not bounded
+        ref_g = oracle.bf_brute_at(ch, idx, sigma_r=sigma_r, w1=w1, range_mode="gaussian")
+        err_g = max(err_g, float(np.abs(got - ref_g).max()))
+    print("config3 sigma_r=%g N=%d: max abs err %.3e vs raised cosine, %.3e vs Gaussian range "
+          "kernel, %d px x 3 channels" % (sigma_r, plan.N, err, err_g, len(idx)))
+    assert err <= TOL
+
+
 @pytest.mark.parametrize("kind,ss,r", [("box", 2.0, None), ("gauss", 3.0, None), ("box", 8.0, None),
                                        ("box", 12.0, 12)])
 def test_unfused_baseline_matches_oracle(bf, oracle, kind, ss, r):
