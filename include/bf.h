@@ -250,21 +250,26 @@ bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, const float *
 
 /*
  * Batched forward: many f32 single-channel images of uneven sizes, each with
- * its own plan (own sigma_s, sigma_r and hence N), in ONE persistent launch
- * that pulls tiles from a device work queue, largest cost first.  The launch
- * is recorded once into a CUDA graph and replayed by bf_batch_forward.
+ * its own plan (own sigma_s, sigma_r and hence N), replayed from one CUDA
+ * graph.  Images whose box half-width fits a tile (r <= 8) share ONE
+ * persistent launch that pulls tiles from a device work queue, largest cost
+ * first; images with 8 < r <= 64 run the streaming sweeps of bf_forward, one
+ * after the other, in the same graph.
  *
  * bf_batch_create  : plans[count], H[count], W[count] are host arrays; the
  *                    batch copies what it needs (the plans may be destroyed
  *                    afterwards).  Every plan must be the 3-pass box with
- *                    1 <= r <= 16 (BF_EUNSUPPORTED otherwise).  Allocates the
- *                    batch's device tables and queue (freed by
- *                    bf_batch_destroy); builds the graph.
+ *                    1 <= r <= 64 (BF_EUNSUPPORTED otherwise).  Allocates the
+ *                    batch's device tables, queue and, if some r > 8, the
+ *                    scratch of the streaming sweeps (the largest such
+ *                    image's bf_forward scratch); all freed by
+ *                    bf_batch_destroy.
  * bf_batch_bind    : in[count], out[count] are host arrays of device
  *                    pointers (f32, row stride W); copied to the device on
- *                    `stream`.  Call again whenever the buffers change.
- * bf_batch_forward : replays the graph on `stream` (capturable, allocates
- *                    nothing).
+ *                    `stream`, which is synchronised; the graph is captured
+ *                    again (on a private stream of the batch).  Call again
+ *                    whenever the buffers change.
+ * bf_batch_forward : replays the graph on `stream` (allocates nothing).
  * bf_batch_check   : waits for `stream` and reports the device error flag
  *                    (non-zero if a tile-queue bound was hit).
  */
@@ -282,8 +287,8 @@ void bf_batch_destroy(bf_batch *batch);
  * `reps` replays for each candidate -- persistent grid of 1x or 2x the
  * resident blocks, tile queue in largest-cost-first or image order -- keeps
  * the fastest in the batch's graph and reports it (any output may be NULL).
- * Synchronises `stream`.  The tile shapes themselves are fixed per box
- * half-width (32 x 64 for r <= 8, 16 x 64 above).
+ * Synchronises `stream`.  The tile shape itself is fixed (32 x 64); the
+ * streaming images are timed with the rest but not tuned here.
  */
 bf_status bf_batch_tune(bf_batch *batch, cudaStream_t stream, int reps, int *grid,
                         int *order, float *ms);

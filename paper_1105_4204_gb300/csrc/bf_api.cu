@@ -51,8 +51,6 @@ static cudaError_t launch_tile_shape(const bf_plan *p, const BfImage &img, cudaS
     return launch_tile_box(p, img, s, shape);
 }
 
-size_t large_workspace(const bf_plan *pl, int H, int W);
-cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cudaStream_t s);
 
 // Library-owned scratch for the large-radius box path, one buffer per device,
 // grown on demand and reused until bf_release_scratch().

@@ -1,16 +1,22 @@
 // Batched forward: many single-channel f32 images of uneven sizes, each with
-// its own plan, in one persistent launch.
+// its own plan, replayed from one CUDA graph.
 //
-// The host flattens every image into tiles, orders them largest cost first
-// (longest-processing-time order: cost ~ terms x tile area including the
-// halo), and uploads the queue with a per-image descriptor and term table.
-// Each resident block of the persistent kernel claims the next tile with one
-// atomicAdd and runs the fused tile body of that image's box half-width r
-// (1 <= r <= 16, one instantiation per r), so small and large images, cheap
-// and expensive plans share the GPU without a tail of idle SMs per image.
-// The claim loop is bounded by the number of tiles; a block that would exceed
-// it sets the device error flag instead.  The counter reset and the launch are
-// recorded once as a CUDA graph (memset node + kernel node) and replayed.
+// Images whose box half-width r fits a tile (r <= 8): the host flattens them
+// into tiles, orders the tiles largest cost first (longest-processing-time
+// order: cost ~ terms x tile area including the halo), and uploads the queue
+// with a per-image descriptor and term table.  Each resident block of the
+// persistent kernel claims the next tile with one atomicAdd and runs the
+// fused tile body of that image's r (one instantiation per r), so small and
+// large images, cheap and expensive plans share the GPU without a tail of
+// idle SMs per image.  The claim loop is bounded by the number of tiles; a
+// block that would exceed it sets the device error flag instead.
+//
+// Images with 8 < r <= 64: the streaming sweeps of the single-image path,
+// one image after the other through a scratch buffer the batch owns.
+//
+// The counter reset, the persistent launch and the streaming images' launches
+// are captured once into a CUDA graph (again after every bind, which changes
+// the streaming images' pointers) and replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -24,19 +30,20 @@ namespace bf {
 namespace {
 
 constexpr int kBatchNT = 256;
-constexpr int kBatchMaxR = 16;
+constexpr int kBatchTileMaxR = 8;  // larger half-widths take the streaming sweeps
+constexpr int kBatchMaxR = 64;
 
-// tile shapes of the batch bodies; every body uses kBatchNT threads
+// tile shape of the batch bodies; every body uses kBatchNT threads
 template <int R>
 struct BatchShape {
-    static constexpr int TH = R <= 8 ? 32 : 16;
+    static constexpr int TH = 32;
     static constexpr int TW = 64;
-    static constexpr int TWT = R <= 8 ? 16 : 8;
+    static constexpr int TWT = 16;
     using G = TileGeom<1, R, TH, TW, TWT>;
     static_assert(G::NT == kBatchNT, "batch bodies share one block size");
 };
 
-int batch_tile_h(int r) { return r <= 8 ? 32 : 16; }
+constexpr int kBatchTH = 32;
 constexpr int kBatchTW = 64;
 
 struct ImgDesc {
@@ -91,10 +98,10 @@ struct MaxSmem<R, Rs...> {
     static constexpr size_t v =
         BatchShape<R>::G::SMEM > MaxSmem<Rs...>::v ? BatchShape<R>::G::SMEM : MaxSmem<Rs...>::v;
 };
-constexpr size_t kBatchSmem = MaxSmem<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16>::v;
+constexpr size_t kBatchSmem = MaxSmem<1, 2, 3, 4, 5, 6, 7, 8>::v;
 static_assert(kBatchSmem <= 227 * 1024, "batch shared memory");
 
-__global__ void __launch_bounds__(kBatchNT) bf_batch_persist(const __grid_constant__ BatchParams p) {
+__global__ void __launch_bounds__(kBatchNT, 2) bf_batch_persist(const __grid_constant__ BatchParams p) {
     extern __shared__ float4 sm4[];
     float *smem = reinterpret_cast<float *>(sm4);
     __shared__ int s_tile;
@@ -119,14 +126,6 @@ __global__ void __launch_bounds__(kBatchNT) bf_batch_persist(const __grid_consta
             case 6: run_tile<6>(p, d, w.y, w.z, smem); break;
             case 7: run_tile<7>(p, d, w.y, w.z, smem); break;
             case 8: run_tile<8>(p, d, w.y, w.z, smem); break;
-            case 9: run_tile<9>(p, d, w.y, w.z, smem); break;
-            case 10: run_tile<10>(p, d, w.y, w.z, smem); break;
-            case 11: run_tile<11>(p, d, w.y, w.z, smem); break;
-            case 12: run_tile<12>(p, d, w.y, w.z, smem); break;
-            case 13: run_tile<13>(p, d, w.y, w.z, smem); break;
-            case 14: run_tile<14>(p, d, w.y, w.z, smem); break;
-            case 15: run_tile<15>(p, d, w.y, w.z, smem); break;
-            case 16: run_tile<16>(p, d, w.y, w.z, smem); break;
             default:
                 if (threadIdx.x == 0) atomicExch(p.err, 2);
                 break;
@@ -154,6 +153,12 @@ struct bf_batch {
     int grid = 0;
     int order = 0;  // 0: largest cost first, 1: image by image
     bool bound = false;
+    // images with r > kBatchTileMaxR: their index, a copy of their plan, and
+    // the scratch the streaming sweeps run through (one image at a time)
+    std::vector<int> stream_ids;
+    std::vector<bf_plan> stream_plans;
+    void *d_scratch = nullptr;
+    cudaStream_t cap = nullptr;  // private stream the graph is captured on
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -171,11 +176,16 @@ static void batch_free(bf_batch *b) {
     cudaFree(b->d_err);
     cudaFree(b->d_ta);
     cudaFree(b->d_tt);
+    cudaFree(b->d_scratch);
+    if (b->cap) cudaStreamDestroy(b->cap);
     cudaSetDevice(cur);
     delete b;
 }
 
-// (Re)build the graph: counter reset, then the persistent kernel.
+// (Re)build the graph by capturing, on the batch's private stream: the
+// counter reset and the persistent kernel (if any image is tiled), then the
+// streaming sweeps of every image with r > kBatchTileMaxR once the batch is
+// bound (before that their pointers are unknown).
 static cudaError_t batch_build_graph(bf_batch *b) {
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
@@ -185,34 +195,53 @@ static cudaError_t batch_build_graph(bf_batch *b) {
         cudaGraphDestroy(b->graph);
         b->graph = nullptr;
     }
-    cudaError_t e = cudaGraphCreate(&b->graph, 0);
+    cudaError_t e = cudaSuccess;
+    if (!b->cap) {
+        e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    const bool streaming = b->bound && !b->stream_ids.empty();
+    if (b->n_tiles == 0 && !streaming) return cudaSuccess;  // nothing to replay yet
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return e;
-    cudaMemsetParams ms{};
-    ms.dst = b->d_counter;
-    ms.value = 0;
-    ms.elementSize = sizeof(int);
-    ms.width = 1;
-    ms.height = 1;
-    ms.pitch = sizeof(int);
-    cudaGraphNode_t n_memset, n_kernel;
-    e = cudaGraphAddMemsetNode(&n_memset, b->graph, nullptr, 0, &ms);
-    if (e != cudaSuccess) return e;
-    BatchParams prm;
-    prm.imgs = b->d_imgs;
-    prm.queue = b->d_queue;
-    prm.n_tiles = b->n_tiles;
-    prm.counter = b->d_counter;
-    prm.err = b->d_err;
-    prm.ta = b->d_ta;
-    prm.tt = b->d_tt;
-    void *args[] = {&prm};
-    cudaKernelNodeParams kp{};
-    kp.func = (void *)bf_batch_persist;
-    kp.gridDim = dim3(b->grid);
-    kp.blockDim = dim3(kBatchNT);
-    kp.sharedMemBytes = (unsigned)kBatchSmem;
-    kp.kernelParams = args;
-    e = cudaGraphAddKernelNode(&n_kernel, b->graph, &n_memset, 1, &kp);
+    cudaError_t le = cudaSuccess;
+    if (b->n_tiles > 0) {
+        le = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap);
+        BatchParams prm;
+        prm.imgs = b->d_imgs;
+        prm.queue = b->d_queue;
+        prm.n_tiles = b->n_tiles;
+        prm.counter = b->d_counter;
+        prm.err = b->d_err;
+        prm.ta = b->d_ta;
+        prm.tt = b->d_tt;
+        if (le == cudaSuccess) {
+            bf_batch_persist<<<b->grid, kBatchNT, kBatchSmem, b->cap>>>(prm);
+            le = cudaGetLastError();
+        }
+    }
+    if (streaming) {
+        for (size_t k = 0; k < b->stream_ids.size() && le == cudaSuccess; ++k) {
+            const ImgDesc &d = b->h_imgs[b->stream_ids[k]];
+            BfImage img;
+            img.in = d.in;
+            img.out = d.out;
+            img.q_out = nullptr;
+            img.in_row_stride = d.W;
+            img.H = d.H;
+            img.W = d.W;
+            img.C = 1;
+            img.dtype = 0;
+            img.q_scale = d.q_scale;
+            img.in_px = 1;
+            img.out_px = 1;
+            img.in_z = 1;
+            img.out_z = 1;
+            le = launch_large_box(&b->stream_plans[k], img, b->d_scratch, b->cap);
+        }
+    }
+    e = cudaStreamEndCapture(b->cap, &b->graph);
+    if (le != cudaSuccess) return le;
     if (e != cudaSuccess) return e;
     return cudaGraphInstantiate(&b->exec, b->graph, 0);
 }
@@ -236,7 +265,7 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
         if (plans[i]->kind != BF_SPATIAL_BOX_ITER || plans[i]->r_box < 1 ||
             plans[i]->r_box > kBatchMaxR)
             return fail(BF_EUNSUPPORTED,
-                        "bf_batch_create: the batch serves the 3-pass box with 1 <= r <= 16");
+                        "bf_batch_create: the batch serves the 3-pass box with 1 <= r <= 64");
     }
     bf_batch *b = new (std::nothrow) bf_batch();
     if (!b) return fail(BF_ENOMEM, "bf_batch_create: out of host memory");
@@ -252,6 +281,7 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
         int4 w;
     };
     std::vector<Cost> tiles;
+    size_t scratch = 0;
     for (int i = 0; i < count; ++i) {
         const bf_plan *pl = plans[i];
         ImgDesc d{};
@@ -261,7 +291,14 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
         d.n_terms = (int)pl->a32.size();
         d.term_off = (int)ta.size();
         d.q_scale = pl->q_scale;
-        const int th = batch_tile_h(d.r);
+        if (d.r > kBatchTileMaxR) {
+            b->h_imgs.push_back(d);
+            b->stream_ids.push_back(i);
+            b->stream_plans.push_back(*pl);
+            scratch = std::max(scratch, large_workspace(pl, H[i], W[i]));
+            continue;
+        }
+        const int th = kBatchTH;
         d.tiles_x = (W[i] + kBatchTW - 1) / kBatchTW;
         const int tiles_y = (H[i] + th - 1) / th;
         for (int k = 0; k < d.n_terms; ++k) {
@@ -292,20 +329,21 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
                                                           kBatchSmem);
     if (e == cudaSuccess) {
         b->grid = std::max(1, std::min(sms * std::max(per_sm, 1), b->n_tiles));
-        size_t nq = sizeof(int4) * (size_t)b->n_tiles;
+        size_t nq = sizeof(int4) * (size_t)std::max(1, b->n_tiles);
         e = cudaMalloc(&b->d_imgs, sizeof(ImgDesc) * count);
         if (e == cudaSuccess) e = cudaMalloc(&b->d_queue, nq);
         if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&b->d_ta, sizeof(float) * std::max<size_t>(1, ta.size()));
         if (e == cudaSuccess) e = cudaMalloc(&b->d_tt, sizeof(float) * std::max<size_t>(1, tt.size()));
+        if (e == cudaSuccess && scratch > 0) e = cudaMalloc(&b->d_scratch, scratch);
     }
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && b->n_tiles > 0)
         e = cudaMemcpy(b->d_queue, b->h_queue_lpt.data(), sizeof(int4) * b->n_tiles,
                        cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !ta.empty())
         e = cudaMemcpy(b->d_ta, ta.data(), sizeof(float) * ta.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !tt.empty())
         e = cudaMemcpy(b->d_tt, tt.data(), sizeof(float) * tt.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = batch_build_graph(b);
@@ -332,13 +370,22 @@ extern "C" bf_status bf_batch_bind(bf_batch *b, const float *const *in, float *c
                                     cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // h_imgs may change on the next bind
     if (e != cudaSuccess) return cuda_check(e, "bf_batch_bind");
+    const bool was_bound = b->bound;
     b->bound = true;
+    if (!b->stream_ids.empty() || !was_bound) {
+        // the streaming images' pointers live in the graph: capture it again
+        e = batch_build_graph(b);
+        if (e != cudaSuccess) {
+            b->bound = false;
+            return cuda_check(e, "bf_batch_bind");
+        }
+    }
     return BF_OK;
 }
 
 extern "C" bf_status bf_batch_forward(bf_batch *b, cudaStream_t stream) {
     if (!b) return fail(BF_EINVAL, "bf_batch_forward: batch is NULL");
-    if (!b->bound) return fail(BF_EINVAL, "bf_batch_forward: call bf_batch_bind first");
+    if (!b->bound || !b->exec) return fail(BF_EINVAL, "bf_batch_forward: call bf_batch_bind first");
     return cuda_check(cudaGraphLaunch(b->exec, stream), "bf_batch_forward");
 }
 

@@ -1,6 +1,6 @@
-"""GPU parity of the batched persistent launch: every image against the
-single-image fused path (bit-for-bit where both run the same tile body,
-r <= 8) and against the FP64 oracle on sampled pixels."""
+"""GPU parity of the batched launch: every image against the single-image
+path (bit for bit: both run the same tile body for r <= 8 and the same
+streaming sweeps above) and against the FP64 oracle on sampled pixels."""
 import numpy as np
 import pytest
 
@@ -42,13 +42,7 @@ def test_small_batch_against_single_and_oracle(bf, oracle):
         got = outs[i].cpu().numpy()
         single = bf.forward(plans[i], ins[i]).cpu().numpy()
         r = plans[i].radius // 3
-        if r <= 8:
-            np.testing.assert_array_equal(got, single)
-        else:
-            # r > 8: the single-image path runs the streaming sweeps, a different
-            # FP32 summation order; both are held to the oracle below, and to
-            # each other within a fifth of the oracle tolerance
-            assert np.abs(got - single).max() <= TOL / 5
+        np.testing.assert_array_equal(got, single)
         idx = synth.sample_indices(h, w, 300, seed=i)
         w1 = oracle.spatial_w1("box", ss)
         ref = oracle.bf_brute_at(imgs[i].astype(np.float64), idx, sigma_r=sr, w1=w1, N=plans[i].N)
@@ -63,6 +57,8 @@ def test_config4_batch_matches_single_image_path(bf, oracle):
     imgs, plans, ins, outs, b = _setup(bf, specs, seed=0)
     Ns = sorted(p.N for p in plans)
     assert Ns[0] >= 8 and Ns[-1] <= 118
+    rs = [p.radius // 3 for p in plans]
+    assert min(rs) <= 8 < max(rs)  # both the persistent tiles and the streaming sweeps
     b.forward()
     torch.cuda.synchronize()
     assert b.check() == 0
@@ -76,7 +72,7 @@ def test_config4_batch_matches_single_image_path(bf, oracle):
             ref = oracle.bf_brute_at(imgs[i].astype(np.float64), idx, sigma_r=sr,
                                      w1=oracle.spatial_w1("box", ss), N=plans[i].N)
             assert np.abs(got.cpu().numpy().ravel()[idx] - ref).max() <= TOL
-    assert worst <= TOL / 5
+    assert worst == 0.0
 
 
 def test_replay_tune_and_rebind(bf):
@@ -107,5 +103,21 @@ def test_batch_rejects_unsupported_plans(bf):
     from paper_1105_4204_gb300._lib import BfError
     with pytest.raises(BfError):
         bf.Batch([bf.Plan(3.0, 30.0, kind="gauss")], [(32, 32)])
-    with pytest.raises(BfError):
-        bf.Batch([bf.Plan(20.0, 30.0, kind="box")], [(32, 32)])  # r = 20 > 16
+
+
+def test_batch_of_streaming_images_only(bf, oracle):
+    # every image with r > 8: no persistent launch, only streaming sweeps
+    import torch
+    specs = [(70, 150, 12.0, 30.0), (130, 90, 20.0, 25.0), (40, 300, 40.0, 40.0)]
+    imgs, plans, ins, outs, b = _setup(bf, specs, seed=4)
+    assert all(p.radius // 3 > 8 for p in plans)
+    b.forward()
+    b.forward()
+    assert b.check() == 0
+    for i, (h, w, ss, sr) in enumerate(specs):
+        got = outs[i].cpu().numpy()
+        np.testing.assert_array_equal(got, bf.forward(plans[i], ins[i]).cpu().numpy())
+        idx = synth.sample_indices(h, w, 200, seed=i)
+        ref = oracle.bf_brute_at(imgs[i].astype(np.float64), idx, sigma_r=sr,
+                                 w1=oracle.spatial_w1("box", ss), N=plans[i].N)
+        assert np.abs(got.ravel()[idx] - ref).max() <= TOL
