@@ -253,17 +253,18 @@ bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, const float *
  * its own plan (own sigma_s, sigma_r and hence N), replayed from one CUDA
  * graph.  Images whose box half-width fits a tile (r <= 8) share ONE
  * persistent launch that pulls tiles from a device work queue, largest cost
- * first; images with 8 < r <= 64 run the streaming sweeps of bf_forward, one
- * after the other, in the same graph.
+ * first; images with 8 < r <= 64 run the streaming sweeps of bf_forward in
+ * the same graph, in up to four concurrent chains (images spread over the
+ * chains largest cost first), concurrently with the persistent launch.
  *
  * bf_batch_create  : plans[count], H[count], W[count] are host arrays; the
  *                    batch copies what it needs (the plans may be destroyed
  *                    afterwards).  Every plan must be the 3-pass box with
  *                    1 <= r <= 64 (BF_EUNSUPPORTED otherwise).  Allocates the
- *                    batch's device tables, queue and, if some r > 8, the
- *                    scratch of the streaming sweeps (the largest such
- *                    image's bf_forward scratch); all freed by
- *                    bf_batch_destroy.
+ *                    batch's device tables, queue and, if some r > 8, one
+ *                    scratch per chain of streaming images (the largest
+ *                    bf_forward scratch among the chain's images); all freed
+ *                    by bf_batch_destroy.
  * bf_batch_bind    : in[count], out[count] are host arrays of device
  *                    pointers (f32, row stride W); copied to the device on
  *                    `stream`, which is synchronised; the graph is captured

@@ -12,11 +12,13 @@
 // block that would exceed it sets the device error flag instead.
 //
 // Images with 8 < r <= 64: the streaming sweeps of the single-image path,
-// one image after the other through a scratch buffer the batch owns.
+// spread over kBatchLanes chains (largest cost first onto the least loaded);
+// the images of a chain run one after the other through that chain's
+// scratch, the chains and the persistent launch run concurrently.
 //
-// The counter reset, the persistent launch and the streaming images' launches
-// are captured once into a CUDA graph (again after every bind, which changes
-// the streaming images' pointers) and replayed.
+// The counter reset, the persistent launch and the chains are captured into
+// a CUDA graph (again after every bind, which changes the streaming images'
+// pointers) and replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -32,6 +34,7 @@ namespace {
 constexpr int kBatchNT = 256;
 constexpr int kBatchTileMaxR = 8;  // larger half-widths take the streaming sweeps
 constexpr int kBatchMaxR = 64;
+constexpr int kBatchLanes = 4;     // concurrent chains of streaming images
 
 // tile shape of the batch bodies; every body uses kBatchNT threads
 template <int R>
@@ -153,12 +156,18 @@ struct bf_batch {
     int grid = 0;
     int order = 0;  // 0: largest cost first, 1: image by image
     bool bound = false;
-    // images with r > kBatchTileMaxR: their index, a copy of their plan, and
-    // the scratch the streaming sweeps run through (one image at a time)
+    // images with r > kBatchTileMaxR: their index, a copy of their plan, the
+    // chain (lane) each runs in, and one scratch per lane (the images of a
+    // lane run one after the other)
     std::vector<int> stream_ids;
     std::vector<bf_plan> stream_plans;
-    void *d_scratch = nullptr;
+    std::vector<int> stream_lane;
+    int n_lanes = 0;
+    void *d_scratch[kBatchLanes] = {};
     cudaStream_t cap = nullptr;  // private stream the graph is captured on
+    cudaStream_t lane_stream[kBatchLanes] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kBatchLanes] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -176,7 +185,12 @@ static void batch_free(bf_batch *b) {
     cudaFree(b->d_err);
     cudaFree(b->d_ta);
     cudaFree(b->d_tt);
-    cudaFree(b->d_scratch);
+    for (int k = 0; k < kBatchLanes; ++k) {
+        cudaFree(b->d_scratch[k]);
+        if (b->lane_stream[k]) cudaStreamDestroy(b->lane_stream[k]);
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->cap) cudaStreamDestroy(b->cap);
     cudaSetDevice(cur);
     delete b;
@@ -198,6 +212,11 @@ static cudaError_t batch_build_graph(bf_batch *b) {
     cudaError_t e = cudaSuccess;
     if (!b->cap) {
         e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+        for (int k = 0; k < b->n_lanes && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&b->lane_stream[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+        }
         if (e != cudaSuccess) return e;
     }
     const bool streaming = b->bound && !b->stream_ids.empty();
@@ -205,7 +224,13 @@ static cudaError_t batch_build_graph(bf_batch *b) {
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
-    if (b->n_tiles > 0) {
+    if (streaming) {
+        // fork the lanes off the capture stream
+        le = cudaEventRecord(b->ev_fork, b->cap);
+        for (int k = 0; k < b->n_lanes && le == cudaSuccess; ++k)
+            le = cudaStreamWaitEvent(b->lane_stream[k], b->ev_fork, 0);
+    }
+    if (b->n_tiles > 0 && le == cudaSuccess) {
         le = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->cap);
         BatchParams prm;
         prm.imgs = b->d_imgs;
@@ -237,7 +262,14 @@ static cudaError_t batch_build_graph(bf_batch *b) {
             img.out_px = 1;
             img.in_z = 1;
             img.out_z = 1;
-            le = launch_large_box(&b->stream_plans[k], img, b->d_scratch, b->cap);
+            const int lane = b->stream_lane[k];
+            le = launch_large_box(&b->stream_plans[k], img, b->d_scratch[lane],
+                                  b->lane_stream[lane]);
+        }
+        // join every lane back
+        for (int k = 0; k < b->n_lanes && le == cudaSuccess; ++k) {
+            le = cudaEventRecord(b->ev_join[k], b->lane_stream[k]);
+            if (le == cudaSuccess) le = cudaStreamWaitEvent(b->cap, b->ev_join[k], 0);
         }
     }
     e = cudaStreamEndCapture(b->cap, &b->graph);
@@ -281,7 +313,7 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
         int4 w;
     };
     std::vector<Cost> tiles;
-    size_t scratch = 0;
+    std::vector<size_t> stream_ws;  // scratch each streaming image needs
     for (int i = 0; i < count; ++i) {
         const bf_plan *pl = plans[i];
         ImgDesc d{};
@@ -295,7 +327,7 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
             b->h_imgs.push_back(d);
             b->stream_ids.push_back(i);
             b->stream_plans.push_back(*pl);
-            scratch = std::max(scratch, large_workspace(pl, H[i], W[i]));
+            stream_ws.push_back(large_workspace(pl, H[i], W[i]));
             continue;
         }
         const int th = kBatchTH;
@@ -316,6 +348,28 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
     }
     std::stable_sort(tiles.begin(), tiles.end(),
                      [](const Cost &x, const Cost &y) { return x.c > y.c; });
+    // streaming images onto lanes, largest cost first onto the least loaded
+    {
+        const int ns = (int)b->stream_ids.size();
+        b->n_lanes = std::min(kBatchLanes, ns);
+        b->stream_lane.assign(ns, 0);
+        std::vector<int> order(ns);
+        for (int k = 0; k < ns; ++k) order[k] = k;
+        auto cost = [&](int k) {
+            const ImgDesc &d = b->h_imgs[b->stream_ids[k]];
+            return (double)d.n_terms * d.H * d.W;
+        };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+        std::vector<double> load(std::max(1, b->n_lanes), 0.0);
+        for (int k : order) {
+            const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            b->stream_lane[k] = l;
+            load[l] += cost(k);
+        }
+    }
+    size_t lane_ws[kBatchLanes] = {};
+    for (size_t k = 0; k < b->stream_ids.size(); ++k)
+        lane_ws[b->stream_lane[k]] = std::max(lane_ws[b->stream_lane[k]], stream_ws[k]);
     for (auto &c : tiles) b->h_queue_lpt.push_back(c.w);
     b->n_tiles = (int)tiles.size();
 
@@ -336,7 +390,8 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
         if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&b->d_ta, sizeof(float) * std::max<size_t>(1, ta.size()));
         if (e == cudaSuccess) e = cudaMalloc(&b->d_tt, sizeof(float) * std::max<size_t>(1, tt.size()));
-        if (e == cudaSuccess && scratch > 0) e = cudaMalloc(&b->d_scratch, scratch);
+        for (int k = 0; k < b->n_lanes && e == cudaSuccess; ++k)
+            e = cudaMalloc(&b->d_scratch[k], lane_ws[k]);
     }
     if (e == cudaSuccess && b->n_tiles > 0)
         e = cudaMemcpy(b->d_queue, b->h_queue_lpt.data(), sizeof(int4) * b->n_tiles,
