@@ -84,7 +84,7 @@ __device__ __forceinline__ void run_tile(const BatchParams &p, const ImgDesc &d,
     jb.a = p.ta + d.term_off;
     jb.t = p.tt + d.term_off;
     jb.n_terms = d.n_terms;
-    jb.w = nullptr;
+    jb.w2 = nullptr;
     jb.x0 = tx * S::TW;
     jb.y0 = ty * S::TH;
     tile_body<1, R, S::TH, S::TW, S::TWT>(jb, smem);

@@ -42,6 +42,7 @@ struct BfTerms {
 
 struct BfTaps {
     float w[2 * BF_MAX_TAPS_R + 1];
+    float2 w2[2 * BF_MAX_TAPS_R + 1];  // the same taps, each duplicated into a pair
 };
 
 // One launch covers C planes (z): interleaved channels of one image
@@ -67,6 +68,8 @@ bf_status cuda_check(cudaError_t e, const char *what);
 
 void fill_terms(const bf_plan *p, BfTerms *t);
 void fill_taps(const bf_plan *p, BfTaps *t);
+// Copies t->w into the paired taps t->w2.
+void pair_taps(BfTaps *t);
 
 // Launchers (return cudaGetLastError() of the launch).
 // Fused tile kernel for the truncated Gaussian / small-radius box.

@@ -48,6 +48,10 @@ namespace {
 constexpr int kVB = 4;     // lr_vert: terms per block (they share the f ring)
 constexpr int kVMax = 64;  // most terms one lr_vert launch filters
 constexpr int kHG = 8;     // most terms one lr_horz launch filters (accumulator slots)
+#ifndef BF_LR_HWARPS
+#define BF_LR_HWARPS 2048
+#endif
+constexpr int kHWarps = BF_LR_HWARPS;  // lr_horz: target warps per launch (sets the bands)
 
 struct LrParams {
     const void *in;       // first pixel of the plane being filtered
@@ -120,6 +124,16 @@ __device__ __forceinline__ void aux4(float tm, float fv, float (&x)[4]) {
     x[3] = __fmul_rn(fv, sn);
 }
 
+// The same four values as pairs: x[0] = (cos, sin), x[1] = (f cos, f sin).
+__device__ __forceinline__ void aux4p(float tm, float fv, float2 (&x)[2]) {
+    float r = __fmul_rn(tm, fv);
+    r = r - rintf(r);
+    float sn, cs;
+    __sincosf(kTwoPi * r, &sn, &cs);
+    x[0] = make_float2(cs, sn);
+    x[1] = make_float2(__fmul_rn(fv, cs), __fmul_rn(fv, sn));
+}
+
 // grid: (ceil(W / kVCols), bands, ceil(terms / kVB)); block: kVCols x kVB
 // threads, thread (column, term g) computes the four planes of term g for one
 // column.  The kVB terms of a block share one ring of the last ring_size(r)
@@ -151,48 +165,51 @@ __global__ void __launch_bounds__(kVCols * kVB) lr_vert(const __grid_constant__ 
     const bool col_ok = xb + col < p.W && term_ok;
     const size_t plane = blocked_plane(p.H, p.W);
     float *dst = p.Vt + (size_t)g * 4 * plane;
-    float s1[4][3], s2[4][2], s3[4];
+    // running sums of the plane pairs (cos, sin) [index 0] and (f cos, f sin)
+    // [index 1], one f32x2 instruction per pair and update
+    float2 s1[2][3], s2[2][2], s3[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        s1[q][0] = s1[q][1] = s1[q][2] = 0.f;
-        s2[q][0] = s2[q][1] = 0.f;
-        s3[q] = 0.f;
+    for (int q = 0; q < 2; ++q) {
+        s1[q][0] = s1[q][1] = s1[q][2] = make_float2(0.f, 0.f);
+        s2[q][0] = s2[q][1] = make_float2(0.f, 0.f);
+        s3[q] = make_float2(0.f, 0.f);
     }
     float cur[kChunk], nxt[kChunk];
 #pragma unroll
     for (int d = 0; d < kChunk; ++d) cur[d] = load_px<DT>(p, min(max(e_s + d, 0), p.H - 1), xc);
-    float st[4][kChunk];
+    float2 st[2][kChunk];
     // one step; CHECKED covers steps before p0 + 3L (inputs before p0 are
     // zero) and the band's last chunk
     auto step = [&](int e, int d, auto checked) {
         constexpr bool CHECKED = decltype(checked)::value;
         const float fv = cur[d];
         ring[(e & M) * kVCols] = fv;
-        float x0[4], x1[4], x2[4], x3[4];
-        aux4(tm, fv, x0);
+        float2 x0[2], x1[2], x2[2], x3[2];
+        aux4p(tm, fv, x0);
         if (!CHECKED) {
-            aux4(tm, ring[((e - L) & M) * kVCols], x1);
-            aux4(tm, ring[((e - 2 * L) & M) * kVCols], x2);
-            aux4(tm, ring[((e - 3 * L) & M) * kVCols], x3);
+            aux4p(tm, ring[((e - L) & M) * kVCols], x1);
+            aux4p(tm, ring[((e - 2 * L) & M) * kVCols], x2);
+            aux4p(tm, ring[((e - 3 * L) & M) * kVCols], x3);
         } else {
+            const float2 z = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) x1[q] = x2[q] = x3[q] = 0.f;
+            for (int q = 0; q < 2; ++q) x1[q] = x2[q] = x3[q] = z;
             if (e < p0) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) x0[q] = 0.f;
+                for (int q = 0; q < 2; ++q) x0[q] = z;
             }
-            if (e >= p0 + L) aux4(tm, ring[((e - L) & M) * kVCols], x1);
-            if (e >= p0 + 2 * L) aux4(tm, ring[((e - 2 * L) & M) * kVCols], x2);
-            if (e >= p0 + 3 * L) aux4(tm, ring[((e - 3 * L) & M) * kVCols], x3);
+            if (e >= p0 + L) aux4p(tm, ring[((e - L) & M) * kVCols], x1);
+            if (e >= p0 + 2 * L) aux4p(tm, ring[((e - 2 * L) & M) * kVCols], x2);
+            if (e >= p0 + 3 * L) aux4p(tm, ring[((e - 3 * L) & M) * kVCols], x3);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            s1[q][0] += x0[q] - x1[q];
-            s1[q][1] += x1[q] - x2[q];
-            s1[q][2] += x2[q] - x3[q];
-            s2[q][0] += s1[q][0] - s1[q][1];
-            s2[q][1] += s1[q][1] - s1[q][2];
-            s3[q] += s2[q][0] - s2[q][1];
+        for (int q = 0; q < 2; ++q) {
+            s1[q][0] = f2add(s1[q][0], f2sub(x0[q], x1[q]));
+            s1[q][1] = f2add(s1[q][1], f2sub(x1[q], x2[q]));
+            s1[q][2] = f2add(s1[q][2], f2sub(x2[q], x3[q]));
+            s2[q][0] = f2add(s2[q][0], f2sub(s1[q][0], s1[q][1]));
+            s2[q][1] = f2add(s2[q][1], f2sub(s1[q][1], s1[q][2]));
+            s3[q] = f2add(s3[q], f2sub(s2[q][0], s2[q][1]));
             st[q][d] = s3[q];
         }
     };
@@ -216,17 +233,23 @@ __global__ void __launch_bounds__(kVCols * kVB) lr_vert(const __grid_constant__ 
             float *dc = dst + blocked_at(p.W, xb + col, tb);
             if (tb + kChunk <= y1) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float4 *d4 = reinterpret_cast<float4 *>(dc + q * plane);
-                    d4[0] = make_float4(st[q][0], st[q][1], st[q][2], st[q][3]);
-                    d4[1] = make_float4(st[q][4], st[q][5], st[q][6], st[q][7]);
+                for (int q = 0; q < 2; ++q) {
+                    float4 *d4 = reinterpret_cast<float4 *>(dc + 2 * q * plane);
+                    d4[0] = make_float4(st[q][0].x, st[q][1].x, st[q][2].x, st[q][3].x);
+                    d4[1] = make_float4(st[q][4].x, st[q][5].x, st[q][6].x, st[q][7].x);
+                    d4 = reinterpret_cast<float4 *>(dc + (2 * q + 1) * plane);
+                    d4[0] = make_float4(st[q][0].y, st[q][1].y, st[q][2].y, st[q][3].y);
+                    d4[1] = make_float4(st[q][4].y, st[q][5].y, st[q][6].y, st[q][7].y);
                 }
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 2; ++q)
 #pragma unroll
                     for (int d = 0; d < kChunk; ++d)
-                        if (tb + d < y1) dc[q * plane + d] = st[q][d];
+                        if (tb + d < y1) {
+                            dc[2 * q * plane + d] = st[q][d].x;
+                            dc[(2 * q + 1) * plane + d] = st[q][d].y;
+                        }
             }
         }
 #pragma unroll
@@ -492,7 +515,7 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     p.band_h = ((H + nbh_max - 1) / nbh_max + 7) / 8 * 8;
     const int nbh = (H + p.band_h - 1) / p.band_h;
     const int g_warps = p.nyb * 2 * h_size[0];
-    const int nbw_max = std::max(1, std::min((2048 + g_warps / 2) / g_warps, W / min_band));
+    const int nbw_max = std::max(1, std::min((kHWarps + g_warps / 2) / g_warps, W / min_band));
     p.band_w = ((W + nbw_max - 1) / nbw_max + 7) / 8 * 8;
     const int nbw = (W + p.band_w - 1) / p.band_w;
 

@@ -225,6 +225,11 @@ void fill_taps(const bf_plan *p, BfTaps *t) {
     std::memset(t, 0, sizeof(*t));
     int n = (int)p->w1f.size();
     for (int k = 0; k < n && k < 2 * BF_MAX_TAPS_R + 1; ++k) t->w[k] = p->w1f[k];
+    pair_taps(t);
+}
+
+void pair_taps(BfTaps *t) {
+    for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) t->w2[k] = make_float2(t->w[k], t->w[k]);
 }
 
 }  // namespace bf

@@ -7,18 +7,20 @@
 //
 //   phase 1: for each extended column j and each of cos / sin:
 //              x(i) = cos|sin(omega f(i, j))                 (auxiliary image)
-//              filter x vertically        -> V[cos|sin](:, j)
-//              filter f*x vertically      -> V[f cos|f sin](:, j)
+//              filter the pair (x, f*x) vertically -> V[cos|sin](:, j),
+//                                                     V[f cos|f sin](:, j)
 //            and keep a_m cos, a_m sin at the tile's own pixels;
 //   phase 2: each thread owns a TWT-pixel row segment of either the
-//            numerator P or the normaliser Q in registers, filters the two
-//            planes it needs horizontally and accumulates
+//            numerator P or the normaliser Q in registers, filters the pair
+//            of planes it needs (cos part, sin part) horizontally and
+//            accumulates
 //              P += a_m cos(omega f(x)) W[f cos](x) + a_m sin(omega f(x)) W[f sin](x)
 //              Q += a_m cos(omega f(x)) W[cos](x)   + a_m sin(omega f(x)) W[sin](x)
 //
 // and finally writes out = P / Q (Algorithm 1 step 5).  The auxiliary images
 // never leave the SM; HBM sees one read of f and one write of out (and of Q
-// when asked).  All arithmetic is FP32.
+// when asked).  All arithmetic is FP32; the two planes of a pair share every
+// filter instruction as one f32x2 operation (sm_100 and later).
 //
 // Spatial kernels (both separable, per axis):
 //   KIND 0: truncated Gaussian, taps w[0 .. 2 RAD] from the kernel parameters;
@@ -93,6 +95,122 @@ struct Filt {
     }
 };
 
+// ---- paired FP32 arithmetic (sm_100+: one instruction, two lanes of work) --
+//
+// The four auxiliary images of a term are filtered in pairs: (x, f x) in the
+// vertical pass and (cos part, sin part) in the horizontal pass, so that every
+// running-sum step, tap and accumulation of a pair is one f32x2 instruction.
+
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    unsigned long long d;
+    const unsigned long long x = *reinterpret_cast<const unsigned long long *>(&a);
+    const unsigned long long y = *reinterpret_cast<const unsigned long long *>(&b);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+    return *reinterpret_cast<const float2 *>(&d);
+}
+
+// Streamed 1-D filters on pairs.  Input k is produced by gen(k) right before
+// the filter first needs it, and output k is handed to sink(k, y) as soon as
+// it is complete, so only the filter's window is live in registers (all
+// indices are compile-time after unrolling).
+
+// Three cascaded boxes of half-width r (running sums, unnormalised):
+// level l output k: s(k) = s(k - 1) + (in(k + 2r) - in(k - 1)).
+template <int r, int NIN, class Gen, class Sink>
+__device__ __forceinline__ void box3_stream(Gen &&gen, Sink &&sink) {
+    constexpr int D = 2 * r;
+    float2 a[NIN];
+    float2 b[NIN - D];
+    float2 c[NIN - 2 * D];
+    float2 s1 = make_float2(0.f, 0.f), s2 = s1, s3 = s1;
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+        a[i] = gen(i);
+        if (i >= D) {
+            const int k1 = i - D;
+            if (k1 == 0) {
+                s1 = a[0];
+#pragma unroll
+                for (int d = 1; d <= D; ++d) s1 = f2add(s1, a[d]);
+            } else {
+                s1 = f2add(s1, f2sub(a[k1 + D], a[k1 - 1]));
+            }
+            b[k1] = s1;
+            if (k1 >= D) {
+                const int k2 = k1 - D;
+                if (k2 == 0) {
+                    s2 = b[0];
+#pragma unroll
+                    for (int d = 1; d <= D; ++d) s2 = f2add(s2, b[d]);
+                } else {
+                    s2 = f2add(s2, f2sub(b[k2 + D], b[k2 - 1]));
+                }
+                c[k2] = s2;
+                if (k2 >= D) {
+                    const int k3 = k2 - D;
+                    if (k3 == 0) {
+                        s3 = c[0];
+#pragma unroll
+                        for (int d = 1; d <= D; ++d) s3 = f2add(s3, c[d]);
+                    } else {
+                        s3 = f2add(s3, f2sub(c[k3 + D], c[k3 - 1]));
+                    }
+                    sink(k3, s3);
+                }
+            }
+        }
+    }
+}
+
+// Truncated Gaussian taps w2[0 .. 2R] (each tap duplicated into both lanes).
+template <int R, int NIN, class Gen, class Sink>
+__device__ __forceinline__ void gauss_stream(Gen &&gen, Sink &&sink, const float2 *__restrict__ w2) {
+    float2 a[NIN];
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+        a[i] = gen(i);
+        if (i >= 2 * R) {
+            const int k = i - 2 * R;
+            float2 acc = f2mul(w2[0], a[k]);
+#pragma unroll
+            for (int d = 1; d <= 2 * R; ++d) acc = f2fma(w2[d], a[k + d], acc);
+            sink(k, acc);
+        }
+    }
+}
+
+template <int KIND, int RAD, int NIN, class Gen, class Sink>
+__device__ __forceinline__ void filt2_stream(Gen &&gen, Sink &&sink, const float2 *__restrict__ w2) {
+    if constexpr (KIND == 0) {
+        gauss_stream<RAD, NIN>(gen, sink, w2);
+    } else {
+        box3_stream<RAD, NIN>(gen, sink);
+    }
+}
+
+// Generator adaptor: produces the inputs in batches of GA so that their
+// independent latency chains (shared-memory load, sine) overlap; measured
+// faster than generating one input per step (too little to overlap) or all of
+// them up front (too many registers).
+constexpr int kGenAhead = 8;
+template <int GA, int NIN, class Gen>
+struct Ahead {
+    Gen &g;
+    float2 buf[NIN];
+    __device__ __forceinline__ explicit Ahead(Gen &gen) : g(gen) {}
+    __device__ __forceinline__ float2 operator()(int i) {
+        if (i % GA == 0) {
+#pragma unroll
+            for (int d = 0; d < GA; ++d)
+                if (i + d < NIN) buf[i + d] = g(i + d);
+        }
+        return buf[i];
+    }
+};
+
 // ---- geometry --------------------------------------------------------------
 
 template <int KIND, int RAD, int TH, int TW, int TWT>
@@ -106,20 +224,29 @@ struct TileGeom {
     static constexpr int LN4 = (LN + 3) / 4;
     // f tile row stride (floats); rounded to a multiple of 4 for alignment
     static constexpr int SF = (EW + 3) / 4 * 4;
-    // V row stride: covers every float4 a segment reads, and is an odd number
-    // of float4s so that 8 consecutive rows hit 8 different 16-byte bank groups
+    // V row stride in floats (scalar kernels): covers every float4 a segment
+    // reads, an odd number of float4s so that 8 consecutive rows hit 8
+    // different 16-byte bank groups
     static constexpr int SV_MIN4 = (TW - TWT + 4 * LN4 + 3) / 4;
     static constexpr int SV = 4 * (SV_MIN4 % 2 ? SV_MIN4 : SV_MIN4 + 1);
     static constexpr int SC4 = TW / 4;
     static constexpr int SC = 4 * (SC4 % 2 ? SC4 : SC4 + 1);
+    // Paired layout (forward): V2 rows of float2 {cos part, sin part}; the row
+    // stride covers the columns phase 1 writes and the pairs of float2 that a
+    // segment reads, and is 2 mod 4 float2 (an odd number of 16-byte units).
+    static constexpr int LN2 = (LN + 1) / 2 * 2;
+    static constexpr int SV2_MIN = (EW > TW - TWT + LN2 ? EW : TW - TWT + LN2);
+    static constexpr int SV2 = (SV2_MIN + 3) / 4 * 4 + 2;
+    static constexpr int SC2 = (TW + 3) / 4 * 4 + 2;
     static constexpr int F_FLOATS = EH * SF;
-    static constexpr int V_FLOATS = 4 * TH * SV;
-    static constexpr int C_FLOATS = 2 * TH * SC;
+    static constexpr int V_FLOATS = 4 * TH * (SV > SV2 ? SV : SV2);
+    static constexpr int C_FLOATS = 2 * TH * (SC > SC2 ? SC : SC2);
     static constexpr size_t SMEM = sizeof(float) * (size_t)(F_FLOATS + V_FLOATS + C_FLOATS);
     static_assert(TW % TWT == 0, "segments must tile the row");
     static_assert(TWT % 4 == 0 && TW % 4 == 0, "float4 access");
     static_assert(NT <= 1024, "block too large");
     static_assert(TH * SV <= V_FLOATS, "exchange buffer");
+    static_assert(2 * EW <= NT, "one phase-1 item per thread");
 };
 
 struct TileParams {
@@ -141,7 +268,7 @@ struct TileJob {
     const float *a;
     const float *t;
     int n_terms;
-    const float *w;
+    const float2 *w2;  // Gaussian taps, each duplicated into a pair
     int x0, y0;
 };
 
@@ -149,9 +276,13 @@ template <int KIND, int RAD, int TH, int TW, int TWT>
 __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
     using G = TileGeom<KIND, RAD, TH, TW, TWT>;
     constexpr int HALO = G::HALO, EH = G::EH, EW = G::EW;
+    constexpr int SV2 = G::SV2, SC2 = G::SC2;
     float *Fs = smem;
-    float *V = Fs + G::F_FLOATS;
-    float *Cc = V + G::V_FLOATS;
+    // VP: vertically filtered {f cos, f sin}; VQ: {cos, sin} (float2 rows)
+    float *VP = Fs + G::F_FLOATS;
+    float *VQ = VP + 2 * TH * SV2;
+    // CC: {a cos, a sin} at the tile's own pixels
+    float *CC = Fs + G::F_FLOATS + G::V_FLOATS;
 
     const int tid = threadIdx.x;
     const int x0 = jb.x0, y0 = jb.y0;
@@ -172,11 +303,19 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
         Fs[i * G::SF + j] = v;
     }
 
+    // phase-1 identity: item = (extended column j, q = cos | sin); adjacent
+    // lanes take cos and sin of one column, so their stores are contiguous
+    const int j1 = tid >> 1;
+    const int q1 = tid & 1;
+    const bool p1 = tid < 2 * EW;
+    const bool own_col = j1 >= HALO && j1 < HALO + TW;
+    const float ph0 = q1 ? 0.f : 0.25f;  // cos(t) = sin(t + quarter turn)
     // phase-2 identity: 8 consecutive lanes take 8 consecutive rows
     const int pi = tid % TH;
     const int rest = tid / TH;
     const int pa = rest & 1;   // 0: numerator P, 1: normaliser Q
     const int ps = rest >> 1;  // segment
+    // P or Q of the segment's pixels (scalar: registers are the occupancy limit)
     float acc[TWT];
 #pragma unroll
     for (int k = 0; k < TWT; ++k) acc[k] = 0.f;
@@ -186,68 +325,51 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
         __syncthreads();
         const float am = jb.a[m];
         const float tm = jb.t[m];
-        // ---- phase 1: vertical filtering of the four auxiliary images
-        for (int item = tid; item < 2 * EW; item += G::NT) {
-            const int q = item >= EW ? 1 : 0;  // 0: cos, 1: sin
-            const int j = item - q * EW;
-            const float ph0 = q ? 0.f : 0.25f;  // cos(t) = sin(t + quarter turn)
-            float x[EH];
-#pragma unroll
-            for (int i = 0; i < EH; ++i) x[i] = sin_turns(fmaf(tm, Fs[i * G::SF + j], ph0));
-            if (j >= HALO && j < HALO + TW) {
-                float *cdst = Cc + q * TH * G::SC + (j - HALO);
-#pragma unroll
-                for (int i = 0; i < TH; ++i) cdst[i * G::SC] = am * x[i + HALO];
-            }
-            float y[TH];
-            Filt<KIND, RAD, EH>::run(x, y, jb.w);
-            float *vdst = V + q * TH * G::SV + j;
-#pragma unroll
-            for (int i = 0; i < TH; ++i) vdst[i * G::SV] = y[i];
-#pragma unroll
-            for (int i = 0; i < EH; ++i) x[i] *= Fs[i * G::SF + j];
-            Filt<KIND, RAD, EH>::run(x, y, jb.w);
-            vdst += 2 * TH * G::SV;
-#pragma unroll
-            for (int i = 0; i < TH; ++i) vdst[i * G::SV] = y[i];
+        // ---- phase 1: vertical filtering of (x, f x), x = cos | sin (omega f)
+        if (p1) {
+            const float *fcol = Fs + j1;
+            float *ccol = CC + 2 * (j1 - HALO) + q1;
+            float *vpcol = VP + 2 * j1 + q1;
+            float *vqcol = VQ + 2 * j1 + q1;
+            auto gen = [&](int i) {
+                const float fv = fcol[i * G::SF];
+                const float x = sin_turns(fmaf(tm, fv, ph0));
+                if (i >= HALO && i < HALO + TH && own_col) ccol[(i - HALO) * 2 * SC2] = am * x;
+                return make_float2(x, x * fv);
+            };
+            auto sink = [&](int k, float2 y) {
+                vqcol[k * 2 * SV2] = y.x;
+                vpcol[k * 2 * SV2] = y.y;
+            };
+            Ahead<kGenAhead, EH, decltype(gen)> ahead(gen);
+            filt2_stream<KIND, RAD, EH>(ahead, sink, jb.w2);
         }
         __syncthreads();
-        // ---- phase 2: horizontal filtering + per-pixel combine
-#pragma unroll
-        for (int qq = 0; qq < 2; ++qq) {
-            const int plane = (pa == 0 ? 2 : 0) + qq;
-            const float4 *src =
-                reinterpret_cast<const float4 *>(V + plane * TH * G::SV + pi * G::SV + ps * TWT);
-            float yv[4 * G::LN4];
-#pragma unroll
-            for (int k = 0; k < G::LN4; ++k) {
-                const float4 v4 = src[k];
-                yv[4 * k] = v4.x;
-                yv[4 * k + 1] = v4.y;
-                yv[4 * k + 2] = v4.z;
-                yv[4 * k + 3] = v4.w;
-            }
-            float yin[G::LN];
-#pragma unroll
-            for (int k = 0; k < G::LN; ++k) yin[k] = yv[k];
-            float z[TWT];
-            Filt<KIND, RAD, G::LN>::run(yin, z, jb.w);
-            const float4 *cs =
-                reinterpret_cast<const float4 *>(Cc + qq * TH * G::SC + pi * G::SC + ps * TWT);
-#pragma unroll
-            for (int k = 0; k < TWT / 4; ++k) {
-                const float4 c4 = cs[k];
-                acc[4 * k] = fmaf(c4.x, z[4 * k], acc[4 * k]);
-                acc[4 * k + 1] = fmaf(c4.y, z[4 * k + 1], acc[4 * k + 1]);
-                acc[4 * k + 2] = fmaf(c4.z, z[4 * k + 2], acc[4 * k + 2]);
-                acc[4 * k + 3] = fmaf(c4.w, z[4 * k + 3], acc[4 * k + 3]);
-            }
+        // ---- phase 2: horizontal filtering of (cos part, sin part) + combine
+        {
+            const float *vrow = (pa == 0 ? VP : VQ) + 2 * (pi * SV2 + ps * TWT);
+            const float4 *src4 = reinterpret_cast<const float4 *>(vrow);
+            const float4 *cc4 = reinterpret_cast<const float4 *>(CC + 2 * (pi * SC2 + ps * TWT));
+            float4 ld[(G::LN + 1) / 2];
+            float4 cl[TWT / 2];
+            auto gen = [&](int i) {
+                if ((i & 1) == 0) ld[i >> 1] = src4[i >> 1];
+                const float4 v = ld[i >> 1];
+                return (i & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+            };
+            auto sink = [&](int k, float2 z) {
+                if ((k & 1) == 0) cl[k >> 1] = cc4[k >> 1];
+                const float4 c = cl[k >> 1];
+                const float2 c2 = (k & 1) ? make_float2(c.z, c.w) : make_float2(c.x, c.y);
+                acc[k] = fmaf(c2.x, z.x, fmaf(c2.y, z.y, acc[k]));
+            };
+            filt2_stream<KIND, RAD, G::LN>(gen, sink, jb.w2);
         }
     }
 
     // ---- out = P / Q
     __syncthreads();
-    float *Xq = V;
+    float *Xq = VP;
     if (pa == 1) {
 #pragma unroll
         for (int k = 0; k < TWT; ++k) Xq[pi * G::SV + ps * TWT + k] = acc[k];
@@ -270,8 +392,17 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
     }
 }
 
+// Resident blocks per SM the register allocation is sized for: three for the
+// narrow tiles of the smallest boxes (whose shared memory allows three and
+// whose registers fit 80 without spilling), two otherwise.
+template <int KIND, int RAD, int TW>
+struct TileMinBlocks {
+    static constexpr int value = (KIND == 1 && RAD <= 2 && TW == 64) ? 3 : 2;
+};
+
 template <int KIND, int RAD, int TH, int TW, int TWT>
-__global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT, 2)
+__global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT,
+                                  TileMinBlocks<KIND, RAD, TW>::value)
     bf_tile_fwd(const __grid_constant__ TileParams p) {
     extern __shared__ float4 smem4[];
     TileJob jb;
@@ -290,7 +421,7 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT, 2)
     jb.a = p.terms.a;
     jb.t = p.terms.t;
     jb.n_terms = p.terms.n_terms;
-    jb.w = p.taps.w;
+    jb.w2 = p.taps.w2;
     jb.x0 = blockIdx.x * TW;
     jb.y0 = blockIdx.y * TH;
     tile_body<KIND, RAD, TH, TW, TWT>(jb, reinterpret_cast<float *>(smem4));

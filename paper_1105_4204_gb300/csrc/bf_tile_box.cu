@@ -14,6 +14,7 @@ cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t
     prm.img = img0;
     fill_terms(pl, &prm.terms);
     for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) prm.taps.w[k] = 0.f;
+    pair_taps(&prm.taps);
     if (shape == 1) {
         switch (pl->r_box) {
             case 1: return launch_tile<1, 1, 32, 96, 24>(prm, s);

@@ -29,6 +29,7 @@ cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_
     fill_terms(pl, &prm.terms);
     for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) prm.taps.w[k] = 0.f;
     for (int k = 0; k < 2 * pl->R + 1; ++k) prm.taps.w[k + Ri - pl->R] = pl->w1f[k];
+    pair_taps(&prm.taps);
     if (shape == 1) {
         switch (Ri) {
             case 2: return launch_tile<0, 2, 32, 96, 24>(prm, s);
