@@ -9,15 +9,17 @@
 //             fit 4 GiB), walking down a band of rows (f loaded a few rows
 //             ahead).  The four auxiliary images of the term (cos, sin,
 //             f cos, f sin of omega f, Section 2.3) are generated on the fly
-//             and filtered by the three cascaded boxes with running sums;
-//             written in a blocked column layout (rows in blocks of 16, a
+//             and filtered by the three cascaded boxes with running sums, as
+//             two pairs (cos, sin) and (f cos, f sin); written pair-
+//             interleaved in a blocked column layout (rows in blocks of 16, a
 //             column's 16 rows contiguous) so that the second sweep reads
 //             coalesced.
-//   lr_horz : one thread per image row, plane and term of a launch of at most
-//             eight terms, walking along a band of columns of the blocked
-//             planes: the same three cascaded boxes horizontally, then the
-//             per-pixel combine of eq. (final-form) into the term's own Q or P
-//             accumulator slot.
+//   lr_horz : one warp per term, pair and two row blocks (a lane per row,
+//             the pair as a float2), the warps of four terms in one block
+//             walking along a band of columns in step: the same three
+//             cascaded boxes horizontally, the per-pixel combine of
+//             eq. (final-form), and the block's four terms summed on chip into
+//             one Q and one P slot per group, written once.
 //   lr_final: out = P / Q with P and Q summed over the slots, back to
 //             row-major.
 //
@@ -46,8 +48,8 @@ namespace {
 
 
 constexpr int kVB = 4;     // lr_vert: terms per block (they share the f ring)
+constexpr int kHT = 4;     // lr_horz: terms per block (summed on chip into one slot)
 constexpr int kVMax = 64;  // most terms one lr_vert launch filters
-constexpr int kHG = 8;     // most terms one lr_horz launch filters (accumulator slots)
 #ifndef BF_LR_HWARPS
 #define BF_LR_HWARPS 2048
 #endif
@@ -59,19 +61,19 @@ struct LrParams {
     int dtype, in_px;     // element type; elements between adjacent pixels
     int H, W, r;
     int band_h, band_w;
-    int n_terms;          // terms of this launch (lr_vert <= kVMax, lr_horz <= kHG)
+    int n_terms;          // terms of this launch (<= kVMax; lr_horz takes lr_vert's)
     float tv[kVMax];      // lr_vert: turns per gray level of its terms
-    float th[kHG], ah[kHG];  // lr_horz: turns and weights of its terms
+    float th[kVMax], ah[kVMax];  // lr_horz: turns and weights of its terms
     int h0;               // lr_horz: Vt slot of its first term
     int nyb;              // row blocks of the blocked column layout: ceil(H / kYB)
     float *Vt;            // [lr_vert's terms][4 planes] blocked planes: vertically filtered
-    float *Acc;           // [kHG slots][2] blocked planes: Q and P per term slot
+    float *Acc;           // [slots][2] blocked planes: Q and P per group of kHT terms
     float *ft;            // blocked plane: the channel's f
     int first;            // lr_horz: first launch of the channel (the slots start from zero)
 };
 
-// Power-of-two size of lr_vert's shared f ring: the 3L + 1 values a stream
-// needs, plus slack for the warps sharing it to be up to two chunks apart
+// Power-of-two size of lr_vert's shared f ring (which has kChunk more slots
+// mirroring its first kChunk): the 3L + 1 values a stream needs, plus slack for the warps sharing it to be up to two chunks apart
 // (they meet at a barrier every chunk) without overwriting a value another
 // warp still has to read.
 __host__ __device__ __forceinline__ int ring_size(int r) {
@@ -113,18 +115,7 @@ constexpr int kChunk = 8;     // lr_vert: steps between barriers / whose loads a
 // generated when it entered, or the running sums lose the exact shifted-copy
 // relation between them and their rounding errors integrate (error growing
 // like n^2.5 over an n-row band instead of n^0.5).
-__device__ __forceinline__ void aux4(float tm, float fv, float (&x)[4]) {
-    float r = __fmul_rn(tm, fv);
-    r = r - rintf(r);
-    float sn, cs;
-    __sincosf(kTwoPi * r, &sn, &cs);
-    x[0] = cs;
-    x[1] = sn;
-    x[2] = __fmul_rn(fv, cs);
-    x[3] = __fmul_rn(fv, sn);
-}
-
-// The same four values as pairs: x[0] = (cos, sin), x[1] = (f cos, f sin).
+// As pairs: x[0] = (cos, sin), x[1] = (f cos, f sin).
 __device__ __forceinline__ void aux4p(float tm, float fv, float2 (&x)[2]) {
     float r = __fmul_rn(tm, fv);
     r = r - rintf(r);
@@ -164,7 +155,8 @@ __global__ void __launch_bounds__(kVCols * kVB) lr_vert(const __grid_constant__ 
     float *ring = lv_sm + col;  // slot k at ring[k * kVCols]
     const bool col_ok = xb + col < p.W && term_ok;
     const size_t plane = blocked_plane(p.H, p.W);
-    float *dst = p.Vt + (size_t)g * 4 * plane;
+    // pair q of term g: float2 blocked plane at Vt + (2 g + q) * 2 * plane
+    float2 *dst = reinterpret_cast<float2 *>(p.Vt) + (size_t)g * 2 * plane;
     // running sums of the plane pairs (cos, sin) [index 0] and (f cos, f sin)
     // [index 1], one f32x2 instruction per pair and update
     float2 s1[2][3], s2[2][2], s3[2];
@@ -180,16 +172,22 @@ __global__ void __launch_bounds__(kVCols * kVB) lr_vert(const __grid_constant__ 
     float2 st[2][kChunk];
     // one step; CHECKED covers steps before p0 + 3L (inputs before p0 are
     // zero) and the band's last chunk
+    // r1, r2, r3: ring slots of e0 - L, e0 - 2L, e0 - 3L for the chunk at e0;
+    // a chunk's window never wraps (the first kChunk slots are mirrored past
+    // the end of the ring), so step d reads at a fixed offset d * kVCols.
+    const float *r1 = ring, *r2 = ring, *r3 = ring;
     auto step = [&](int e, int d, auto checked) {
         constexpr bool CHECKED = decltype(checked)::value;
         const float fv = cur[d];
-        ring[(e & M) * kVCols] = fv;
+        const int slot = e & M;
+        ring[slot * kVCols] = fv;
+        if (slot < kChunk) ring[(slot + RS) * kVCols] = fv;
         float2 x0[2], x1[2], x2[2], x3[2];
         aux4p(tm, fv, x0);
         if (!CHECKED) {
-            aux4p(tm, ring[((e - L) & M) * kVCols], x1);
-            aux4p(tm, ring[((e - 2 * L) & M) * kVCols], x2);
-            aux4p(tm, ring[((e - 3 * L) & M) * kVCols], x3);
+            aux4p(tm, r1[d * kVCols], x1);
+            aux4p(tm, r2[d * kVCols], x2);
+            aux4p(tm, r3[d * kVCols], x3);
         } else {
             const float2 z = make_float2(0.f, 0.f);
 #pragma unroll
@@ -221,6 +219,9 @@ __global__ void __launch_bounds__(kVCols * kVB) lr_vert(const __grid_constant__ 
         const int tb = e0 - 3 * r;  // output row of step d = 0 (tb - y0 is a multiple of 8)
         const bool fast = e0 >= p0 + 3 * L && e0 + kChunk <= e_end;  // uniform
         if (fast) {
+            r1 = ring + ((e0 - L) & M) * kVCols;
+            r2 = ring + ((e0 - 2 * L) & M) * kVCols;
+            r3 = ring + ((e0 - 3 * L) & M) * kVCols;
 #pragma unroll
             for (int d = 0; d < kChunk; ++d) step(e0 + d, d, std::false_type{});
         } else {
@@ -230,26 +231,22 @@ __global__ void __launch_bounds__(kVCols * kVB) lr_vert(const __grid_constant__ 
         }
         if (col_ok && tb >= y0) {
             // tb is a multiple of 8: the chunk's rows lie in one row block
-            float *dc = dst + blocked_at(p.W, xb + col, tb);
+            float2 *dc = dst + blocked_at(p.W, xb + col, tb);
             if (tb + kChunk <= y1) {
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    float4 *d4 = reinterpret_cast<float4 *>(dc + 2 * q * plane);
-                    d4[0] = make_float4(st[q][0].x, st[q][1].x, st[q][2].x, st[q][3].x);
-                    d4[1] = make_float4(st[q][4].x, st[q][5].x, st[q][6].x, st[q][7].x);
-                    d4 = reinterpret_cast<float4 *>(dc + (2 * q + 1) * plane);
-                    d4[0] = make_float4(st[q][0].y, st[q][1].y, st[q][2].y, st[q][3].y);
-                    d4[1] = make_float4(st[q][4].y, st[q][5].y, st[q][6].y, st[q][7].y);
+                    float4 *d4 = reinterpret_cast<float4 *>(dc + q * plane);
+#pragma unroll
+                    for (int k = 0; k < kChunk / 2; ++k)
+                        d4[k] = make_float4(st[q][2 * k].x, st[q][2 * k].y, st[q][2 * k + 1].x,
+                                            st[q][2 * k + 1].y);
                 }
             } else {
 #pragma unroll
                 for (int q = 0; q < 2; ++q)
 #pragma unroll
                     for (int d = 0; d < kChunk; ++d)
-                        if (tb + d < y1) {
-                            dc[2 * q * plane + d] = st[q][d].x;
-                            dc[(2 * q + 1) * plane + d] = st[q][d].y;
-                        }
+                        if (tb + d < y1) dc[q * plane + d] = st[q][d];
             }
         }
 #pragma unroll
@@ -274,133 +271,147 @@ __global__ void lr_transpose(const __grid_constant__ LrParams p) {
     }
 }
 
-// grid: (ceil(nyb / 4), bands along x, 2 * terms of the group); block: 128
-// threads = four warps, one row block (kYB = 16 rows) each.  blockIdx.z =
-// 2 * slot + pair: pair 0 filters the (cos, sin) planes of the group's term
-// `slot` into Q, pair 1 the (f cos, f sin) planes into P.  In a warp, lanes
-// 0-15 carry the first plane of the pair and lanes 16-31 the second, for the
-// same 16 rows; at an output the two halves meet through one shuffle.  Each
-// term of the group accumulates into its own slot of Acc (summed by
-// lr_final), so the group's terms run concurrently without sharing an
-// accumulator.  The inputs at e - L, e - 2L, e - 3L are read again from the
-// blocked planes (L2) rather than kept, so no shared memory limits the
-// number of resident warps.
-constexpr int kChunkG = 8;
-__global__ void __launch_bounds__(128) lr_horz(const __grid_constant__ LrParams p) {
+// grid: (ceil(nyb / 2), bands along x, groups of kHT terms); block: 2 kHT
+// warps.  Warp w takes term w / 2 of the block's group and pair w % 2 (0: the
+// (cos, sin) planes, whose combine goes to Q; 1: (f cos, f sin), to P) for
+// two row blocks: lane l carries row l % 16 of row block 2 blockIdx.x + l / 16,
+// both planes of the pair in one float2.  All warps of a block walk the same
+// columns in step, kChunkH at a time.  Per chunk every warp turns its
+// filtered pair into the term's contribution a_m (cos(w f) W[.cos] +
+// sin(w f) W[.sin]) at the chunk's outputs, the block sums the contributions
+// of its terms in term order through shared memory and writes the group's
+// Q and P slot once (adding to it when the terms of the image did not fit one
+// lr_vert launch).  The slots are summed in slot order by lr_final.  The
+// inputs at e - L, e - 2L, e - 3L are read again from the blocked planes
+// (L2).
+constexpr int kChunkH = 8;
+__global__ void __launch_bounds__(64 * kHT, 2) lr_horz(const __grid_constant__ LrParams p) {
+    __shared__ float hs_sm[2][2 * kHT][kChunkH][32];
     const int lane = threadIdx.x & 31;
-    const int half = lane >> 4;  // 0: cos-like plane, 1: sin-like plane
-    const int pr = blockIdx.z & 1;
-    const int slot = blockIdx.z >> 1;
-    const int yb = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (yb >= p.nyb) return;  // whole warp
-    const int y = yb * kYB + (lane & (kYB - 1));
+    const int warp = threadIdx.x >> 5;
+    const int q = warp & 1;
+    const int tl = warp >> 1;
+    const int term = blockIdx.z * kHT + tl;
+    const bool term_ok = term < p.n_terms;  // uniform per warp
+    const int tc = min(term, p.n_terms - 1);
     const int W = p.W;
     const size_t plane = blocked_plane(p.H, W);
-    const size_t row = blocked_at(W, 0, min(y, p.H - 1));  // column 0 of this lane's row
-    const float *V = p.Vt + ((size_t)(p.h0 + slot) * 4 + 2 * pr + half) * plane + row;
+    const int rb = min(blockIdx.x * 2 + (lane >> 4), p.nyb - 1);
+    const int y_lane = rb * kYB + (lane & (kYB - 1));
+    const size_t row = blocked_at(W, 0, min(y_lane, p.H - 1));  // column 0 of this lane's row
+    const float2 *V = reinterpret_cast<const float2 *>(p.Vt) + ((size_t)(p.h0 + tc) * 2 + q) * plane + row;
     const float *F = p.ft + row;
-    float *A = p.Acc + ((size_t)slot * 2 + pr) * plane + row;
     const int x0 = blockIdx.y * p.band_w;
     const int x1 = min(x0 + p.band_w, W);
     const int r = p.r, L = 2 * r + 1;
     const int p0 = x0 - 3 * r;  // inputs before p0 count as zero
     const int e_end = x1 + 3 * r;
-    const float am = p.ah[slot], tm = p.th[slot];
-    // cos(x) = sin(x + quarter turn): each half evaluates one sine
-    const float ph = half ? 0.f : 0.25f;
-    const bool store = half == 0 && y < p.H;
-    const bool first = p.first;
-    float s1a = 0.f, s1b = 0.f, s1c = 0.f, s2a = 0.f, s2b = 0.f, s3 = 0.f;
-    for (int e0 = p0; e0 < e_end; e0 += kChunkG) {
-        // the plane at e, e - L, e - 2L, e - 3L for the chunk's steps (0 before p0)
-        float cv[kChunkG][4];
-        const bool edge = max(e0 - 3 * L, p0) < 0 || e0 + kChunkG > W;  // uniform
+    const float am = term_ok ? p.ah[tc] : 0.f, tm = p.th[tc];
+    const float2 z2 = make_float2(0.f, 0.f);
+    float2 s1a = z2, s1b = z2, s1c = z2, s2a = z2, s2b = z2, s3 = z2;
+    // reduction role: thread -> (pair rq, step rd, lane rl) outputs of a chunk
+    constexpr int NOUT = 2 * kChunkH * 32;
+    constexpr int PER = NOUT / (64 * kHT);
+    static_assert(NOUT % (64 * kHT) == 0, "reduction split");
+    int buf = 0;
+    for (int e0 = p0; e0 < e_end; e0 += kChunkH) {
+        // the pair at e, e - L, e - 2L, e - 3L for the chunk's steps (0 before p0)
+        float2 cv[kChunkH][4];
+        const bool edge = max(e0 - 3 * L, p0) < 0 || e0 + kChunkH > W;  // uniform
         if (!edge) {
-            const float *v0 = V + (ptrdiff_t)e0 * kYB;
+            const float2 *v0 = V + (ptrdiff_t)e0 * kYB;
 #pragma unroll
-            for (int d = 0; d < kChunkG; ++d) cv[d][0] = __ldg(v0 + d * kYB);
+            for (int d = 0; d < kChunkH; ++d) cv[d][0] = __ldg(v0 + d * kYB);
 #pragma unroll
             for (int k = 1; k < 4; ++k) {
                 const int rel = e0 - k * L - p0;  // step d valid iff rel + d >= 0
-                const float *vk = v0 - (ptrdiff_t)k * L * kYB;
+                const float2 *vk = v0 - (ptrdiff_t)k * L * kYB;
                 if (rel >= 0) {
 #pragma unroll
-                    for (int d = 0; d < kChunkG; ++d) cv[d][k] = __ldg(vk + d * kYB);
-                } else if (rel > -kChunkG) {
+                    for (int d = 0; d < kChunkH; ++d) cv[d][k] = __ldg(vk + d * kYB);
+                } else if (rel > -kChunkH) {
 #pragma unroll
-                    for (int d = 0; d < kChunkG; ++d) {
-                        const float v = __ldg(vk + max(d, -rel) * kYB);
-                        cv[d][k] = rel + d >= 0 ? v : 0.f;
+                    for (int d = 0; d < kChunkH; ++d) {
+                        const float2 v = __ldg(vk + max(d, -rel) * kYB);
+                        cv[d][k] = rel + d >= 0 ? v : z2;
                     }
                 } else {
 #pragma unroll
-                    for (int d = 0; d < kChunkG; ++d) cv[d][k] = 0.f;
+                    for (int d = 0; d < kChunkH; ++d) cv[d][k] = z2;
                 }
             }
         } else {
 #pragma unroll
-            for (int d = 0; d < kChunkG; ++d) {
+            for (int d = 0; d < kChunkH; ++d) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int pos = e0 + d - k * L;
-                    const float v = __ldg(V + (ptrdiff_t)min(max(pos, 0), W - 1) * kYB);
-                    cv[d][k] = pos >= p0 ? v : 0.f;
+                    const float2 v = __ldg(V + (ptrdiff_t)min(max(pos, 0), W - 1) * kYB);
+                    cv[d][k] = pos >= p0 ? v : z2;
                 }
             }
         }
         const int t0 = e0 - 3 * r;  // output column of step 0
-        if (t0 + kChunkG <= x0) {
-            // warm-up chunk: no outputs
+        if (t0 + kChunkH <= x0) {
+            // warm-up chunk: no outputs (uniform over the block)
 #pragma unroll
-            for (int d = 0; d < kChunkG; ++d) {
-                s1a += cv[d][0] - cv[d][1];
-                s1b += cv[d][1] - cv[d][2];
-                s1c += cv[d][2] - cv[d][3];
-                s2a += s1a - s1b;
-                s2b += s1b - s1c;
-                s3 += s2a - s2b;
+            for (int d = 0; d < kChunkH; ++d) {
+                s1a = f2add(s1a, f2sub(cv[d][0], cv[d][1]));
+                s1b = f2add(s1b, f2sub(cv[d][1], cv[d][2]));
+                s1c = f2add(s1c, f2sub(cv[d][2], cv[d][3]));
+                s2a = f2add(s2a, f2sub(s1a, s1b));
+                s2b = f2add(s2b, f2sub(s1b, s1c));
+                s3 = f2add(s3, f2sub(s2a, s2b));
             }
             continue;
         }
-        // the pixel value and the slot's accumulator at the chunk's outputs
-        float cf[kChunkG], ca[kChunkG];
-        if (t0 >= x0 && t0 + kChunkG <= x1) {  // uniform
+        // the pixel value at the chunk's outputs
+        float cf[kChunkH];
+        if (t0 >= x0 && t0 + kChunkH <= x1) {  // uniform
             const float *f0 = F + (ptrdiff_t)t0 * kYB;
-            const float *a0 = A + (ptrdiff_t)t0 * kYB;
 #pragma unroll
-            for (int d = 0; d < kChunkG; ++d) {
-                cf[d] = __ldg(f0 + d * kYB);
-                ca[d] = first ? 0.f : a0[d * kYB];
-            }
+            for (int d = 0; d < kChunkH; ++d) cf[d] = __ldg(f0 + d * kYB);
         } else {
 #pragma unroll
-            for (int d = 0; d < kChunkG; ++d) {
-                const ptrdiff_t o = (ptrdiff_t)min(max(t0 + d, 0), W - 1) * kYB;
-                cf[d] = __ldg(F + o);
-                ca[d] = first ? 0.f : A[o];
-            }
+            for (int d = 0; d < kChunkH; ++d)
+                cf[d] = __ldg(F + (ptrdiff_t)min(max(t0 + d, 0), W - 1) * kYB);
         }
         // steps past e_end (last chunk) run on clamped inputs and store nothing
-        float o3[kChunkG];
 #pragma unroll
-        for (int d = 0; d < kChunkG; ++d) {
-            s1a += cv[d][0] - cv[d][1];
-            s1b += cv[d][1] - cv[d][2];
-            s1c += cv[d][2] - cv[d][3];
-            s2a += s1a - s1b;
-            s2b += s1b - s1c;
-            s3 += s2a - s2b;
-            o3[d] = s3;
-        }
-#pragma unroll
-        for (int d = 0; d < kChunkG; ++d) {
-            float rr = fmaf(tm, cf[d], ph);
+        for (int d = 0; d < kChunkH; ++d) {
+            s1a = f2add(s1a, f2sub(cv[d][0], cv[d][1]));
+            s1b = f2add(s1b, f2sub(cv[d][1], cv[d][2]));
+            s1c = f2add(s1c, f2sub(cv[d][2], cv[d][3]));
+            s2a = f2add(s2a, f2sub(s1a, s1b));
+            s2b = f2add(s2b, f2sub(s1b, s1c));
+            s3 = f2add(s3, f2sub(s2a, s2b));
+            float rr = tm * cf[d];
             rr = rr - rintf(rr);
-            const float mine = am * __sinf(kTwoPi * rr) * o3[d];
-            const float other = __shfl_down_sync(0xffffffffu, mine, 16);
-            const int t = t0 + d;
-            if (store && t >= x0 && t < x1) A[(ptrdiff_t)t * kYB] = ca[d] + (mine + other);
+            float sn, cs;
+            __sincosf(kTwoPi * rr, &sn, &cs);
+            hs_sm[buf][warp][d][lane] = am * fmaf(cs, s3.x, sn * s3.y);
         }
+        __syncthreads();
+        // sum the group's terms in term order and write the slot
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int o = k * 64 * kHT + threadIdx.x;
+            const int rq = o / (kChunkH * 32);
+            const int rd = (o / 32) % kChunkH;
+            const int rl = o % 32;
+            float v = hs_sm[buf][rq][rd][rl];
+#pragma unroll
+            for (int t = 1; t < kHT; ++t) v += hs_sm[buf][2 * t + rq][rd][rl];
+            const int tcol = t0 + rd;
+            const int orb = blockIdx.x * 2 + (rl >> 4);
+            const int oy = orb * kYB + (rl & (kYB - 1));
+            if (tcol >= x0 && tcol < x1 && orb < p.nyb && oy < p.H) {
+                float *A = p.Acc + ((size_t)blockIdx.z * 2 + rq) * plane +
+                           blocked_at(W, tcol, oy);
+                *A = p.first ? v : *A + v;
+            }
+        }
+        buf ^= 1;
     }
 }
 
@@ -442,17 +453,22 @@ __global__ void lr_final(const float *__restrict__ Acc, int n_slots, float *__re
 }  // namespace
 
 // Terms per lr_vert launch: all of them while their filtered planes stay
-// within 4 GiB, else fewer (at least one lr_horz launch's worth).
+// within 4 GiB, else fewer (at least one lr_horz block's worth).
 static int vert_terms(const bf_plan *pl, int H, int W) {
     const size_t term_bytes = 4 * blocked_plane(H, W) * sizeof(float);
     const size_t budget = (size_t)4 << 30;
     const int nt = (int)pl->a32.size();
-    const int cap = (int)std::max<size_t>(kHG, std::min<size_t>(kVMax, budget / term_bytes));
+    const int cap = (int)std::max<size_t>(kHT, std::min<size_t>(kVMax, budget / term_bytes));
     return std::min(nt, cap);
 }
 
+// Q/P slot pairs: one per lr_horz term group of the largest lr_vert launch.
+static int horz_slots(const bf_plan *pl, int H, int W) {
+    return (vert_terms(pl, H, W) + kHT - 1) / kHT;
+}
+
 size_t large_workspace(const bf_plan *pl, int H, int W) {
-    const size_t planes = 4 * (size_t)vert_terms(pl, H, W) + 2 * kHG + 1;
+    const size_t planes = 4 * (size_t)vert_terms(pl, H, W) + 2 * (size_t)horz_slots(pl, H, W) + 1;
     return planes * blocked_plane(H, W) * sizeof(float) + 256;
 }
 
@@ -469,12 +485,13 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     p.nyb = (H + kYB - 1) / kYB;
     p.r = pl->r_box;
     const int gv_max = vert_terms(pl, H, W);
+    const int n_slots = horz_slots(pl, H, W);
     const size_t plane = blocked_plane(H, W);
     p.Vt = reinterpret_cast<float *>(base);
     p.Acc = p.Vt + (size_t)4 * gv_max * plane;
-    p.ft = p.Acc + (size_t)2 * kHG * plane;
+    p.ft = p.Acc + (size_t)2 * n_slots * plane;
     const int RS = ring_size(p.r);
-    const size_t sm_v = sizeof(float) * (size_t)kVCols * RS;
+    const size_t sm_v = sizeof(float) * (size_t)kVCols * (RS + kChunk);
     if (sm_v > 227 * 1024) return cudaErrorInvalidValue;
     auto kv = img.dtype == 0 ? lr_vert<0> : lr_vert<1>;
     auto kt = img.dtype == 0 ? lr_transpose<0> : lr_transpose<1>;
@@ -496,25 +513,18 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     if (e != cudaSuccess) return e;
     const int resident_vert = std::max(1, n_sm * per_sm);
 
-    // lr_horz launches: ceil(nt / kHG) of them, sizes as equal as possible
-    // and non-increasing (the first launch, which starts every slot from
-    // zero, is the largest); each lr_vert launch covers whole lr_horz launches.
-    const int n_h = (nt + kHG - 1) / kHG;
-    std::vector<int> h_size(n_h);
-    for (int i = 0; i < n_h; ++i) h_size[i] = nt / n_h + (i < nt % n_h ? 1 : 0);
-
     // Bands.  lr_vert's (multiples of 8 rows): as many as one wave of
     // resident blocks holds (a partial second wave costs a whole band's time).
-    // lr_horz's: about 2048 warps in all, which keeps the working set of the
-    // trailing reads in L2.  Both stay at least 12r long (the 6r warm-up at
-    // most half a band).
+    // lr_horz's: enough for about kHWarps warps in all.  Both stay at least
+    // 12r long (the 6r warm-up at most half a band).
     const int min_band = 12 * p.r;
     const int ncb = (W + kVCols - 1) / kVCols;
     const int zb_max = (gv_max + kVB - 1) / kVB;
     const int nbh_max = std::max(1, std::min(resident_vert / (ncb * zb_max), H / min_band));
     p.band_h = ((H + nbh_max - 1) / nbh_max + 7) / 8 * 8;
     const int nbh = (H + p.band_h - 1) / p.band_h;
-    const int g_warps = p.nyb * 2 * h_size[0];
+    const int nyb2 = (p.nyb + 1) / 2;
+    const int g_warps = nyb2 * n_slots * 2 * kHT;
     const int nbw_max = std::max(1, std::min((kHWarps + g_warps / 2) / g_warps, W / min_band));
     p.band_w = ((W + nbw_max - 1) / nbw_max + 7) / 8 * 8;
     const int nbw = (W + p.band_w - 1) / p.band_w;
@@ -524,35 +534,26 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
         p.in = reinterpret_cast<const char *>(img.in) + (long long)ch * img.in_z * esz;
         dim3 gt((W + 31) / 32, (H + 31) / 32);
         kt<<<gt, dim3(32, 8), 0, s>>>(p);
-        int h = 0, m0 = 0;
-        while (h < n_h) {
-            // lr_horz launches [h, h1) fit one lr_vert launch
-            int h1 = h, nv = 0;
-            while (h1 < n_h && nv + h_size[h1] <= gv_max) nv += h_size[h1++];
-            if (h1 == h) return cudaErrorInvalidValue;  // cannot happen: h_size <= kHG <= gv_max
+        for (int m0 = 0; m0 < nt; m0 += gv_max) {
+            // terms [m0, m0 + nv): one lr_vert launch, then one lr_horz launch
+            const int nv = std::min(gv_max, nt - m0);
             p.n_terms = nv;
-            for (int g = 0; g < kVMax; ++g) p.tv[g] = pl->turns32[m0 + std::min(g, nv - 1)];
+            for (int g = 0; g < kVMax; ++g) {
+                const int m = m0 + std::min(g, nv - 1);
+                p.tv[g] = pl->turns32[m];
+                p.th[g] = pl->turns32[m];
+                p.ah[g] = pl->a32[m];
+            }
+            p.h0 = 0;
+            p.first = m0 == 0;
             dim3 gv(ncb, nbh, (nv + kVB - 1) / kVB);
             kv<<<gv, kVCols * kVB, sm_v, s>>>(p);
-            int off = 0;
-            for (; h < h1; ++h) {
-                p.n_terms = h_size[h];
-                p.h0 = off;
-                for (int g = 0; g < kHG; ++g) {
-                    const int m = m0 + off + std::min(g, h_size[h] - 1);
-                    p.th[g] = pl->turns32[m];
-                    p.ah[g] = pl->a32[m];
-                }
-                p.first = h == 0;
-                dim3 gh((p.nyb + 3) / 4, nbw, 2 * p.n_terms);
-                lr_horz<<<gh, 128, 0, s>>>(p);
-                off += h_size[h];
-            }
-            m0 += nv;
+            dim3 gh(nyb2, nbw, (nv + kHT - 1) / kHT);
+            lr_horz<<<gh, 64 * kHT, 0, s>>>(p);
         }
         dim3 gf((W + 31) / 32, (H + 31) / 32);
         lr_final<<<gf, dim3(32, 8), 0, s>>>(
-            p.Acc, h_size[0], img.out + (long long)ch * img.out_z,
+            p.Acc, n_slots, img.out + (long long)ch * img.out_z,
             img.q_out ? img.q_out + (long long)ch * img.out_z : nullptr, H, W, img.out_px,
             img.q_scale);
     }

@@ -172,12 +172,26 @@ def test_box_large_radius(bf, oracle, r, H, W):
 
 @pytest.mark.parametrize("N", [1, 2, 11, 17, 18])
 def test_box_large_radius_term_groups(bf, oracle, N):
-    # the streaming sweeps take the terms in groups of eight, one accumulator
-    # slot per term of a group: 1, 2, 6, 9 and 10 terms leave slots unused or
-    # a partial last group
+    # the horizontal streaming sweep sums the terms on chip in groups of four,
+    # one accumulator slot per group: 1, 2, 6, 9 and 10 terms leave a partial
+    # group
     sigma_r = 1.001 * 2 * 255.0 / (np.pi * np.sqrt(N))
     img = synth.rectangles(45, 83, n_rect=6, noise=8.0, seed=N)
     plan = bf.Plan(12.0, sigma_r, kind="box", radius=12, N=N)
+    out = _run(bf, img, plan)
+    ref = _oracle_full(oracle, img, plan)
+    assert np.abs(out - ref).max() <= TOL
+
+
+def test_box_large_radius_more_terms_than_one_vertical_launch(bf, oracle):
+    # N = 200 has more terms than one vertical sweep takes (64), so the
+    # filtered planes pass through the scratch in two rounds and the second
+    # round adds to the accumulator slots the first one wrote
+    N = 200
+    sigma_r = 1.001 * 2 * 255.0 / (np.pi * np.sqrt(N))
+    img = synth.rectangles(40, 70, n_rect=6, noise=8.0, seed=3)
+    plan = bf.Plan(12.0, sigma_r, kind="box", radius=12, N=N)
+    assert plan.n_terms > 64
     out = _run(bf, img, plan)
     ref = _oracle_full(oracle, img, plan)
     assert np.abs(out - ref).max() <= TOL
