@@ -50,10 +50,17 @@ namespace {
 constexpr int kVB = 4;     // lr_vert: terms per block (they share the f ring)
 constexpr int kHT = 4;     // lr_horz: terms per block (summed on chip into one slot)
 constexpr int kVMax = 64;  // most terms one lr_vert launch filters
-#ifndef BF_LR_HWARPS
-#define BF_LR_HWARPS 2048
+#ifndef BF_LR_HORZ_L2_MB
+#define BF_LR_HORZ_L2_MB 56
 #endif
-constexpr int kHWarps = BF_LR_HWARPS;  // lr_horz: target warps per launch (sets the bands)
+// lr_horz: L2 bytes the lagged reads of all resident blocks may occupy
+constexpr size_t kHorzL2Bytes = (size_t)BF_LR_HORZ_L2_MB << 20;
+constexpr int kHorzPrefetchR = 24;  // lr_horz prefetches the next chunk from this r on
+#ifndef BF_LR_VBANDS_MIN
+#define BF_LR_VBANDS_MIN 1
+#endif
+constexpr int kVBandsMin = BF_LR_VBANDS_MIN;  // lr_vert: fewest bands of rows
+__host__ __device__ __forceinline__ int L_of(int r) { return 2 * r + 1; }
 
 struct LrParams {
     const void *in;       // first pixel of the plane being filtered
@@ -271,147 +278,184 @@ __global__ void lr_transpose(const __grid_constant__ LrParams p) {
     }
 }
 
-// grid: (ceil(nyb / 2), bands along x, groups of kHT terms); block: 2 kHT
-// warps.  Warp w takes term w / 2 of the block's group and pair w % 2 (0: the
-// (cos, sin) planes, whose combine goes to Q; 1: (f cos, f sin), to P) for
-// two row blocks: lane l carries row l % 16 of row block 2 blockIdx.x + l / 16,
-// both planes of the pair in one float2.  All warps of a block walk the same
-// columns in step, kChunkH at a time.  Per chunk every warp turns its
-// filtered pair into the term's contribution a_m (cos(w f) W[.cos] +
-// sin(w f) W[.sin]) at the chunk's outputs, the block sums the contributions
-// of its terms in term order through shared memory and writes the group's
-// Q and P slot once (adding to it when the terms of the image did not fit one
-// lr_vert launch).  The slots are summed in slot order by lr_final.  The
-// inputs at e - L, e - 2L, e - 3L are read again from the blocked planes
-// (L2).
+// Persistent: block b takes work items b, b + gridDim.x, ... where an item is
+// (two row blocks, a band of columns, a group of kHT terms); the grid is
+// sized so that the lagged reads of all resident blocks stay in L2 (each
+// lane reads back the 3L columns behind it).  Block: 2 kHT warps.  Warp w
+// takes term w / 2 of the item's group and pair w % 2 (0: the (cos, sin)
+// planes, whose combine goes to Q; 1: (f cos, f sin), to P); lane l carries
+// row l % 16 of the item's row block l / 16, both planes of the pair in one
+// float2.  All warps of a block walk the same columns in step, kChunkH at a
+// time, the loads of the next chunk issued before the current one is
+// filtered.  Per chunk every warp turns its filtered pair into the term's
+// contribution a_m (cos(w f) W[.cos] + sin(w f) W[.sin]) at the chunk's
+// outputs; the block sums the contributions of its terms in term order
+// through shared memory and writes the group's Q and P slot once (adding to
+// it when the terms of the image did not fit one lr_vert launch).  lr_final
+// sums the slots in slot order.
+//
+// PF (large r): the next chunk's loads are issued before the current chunk is
+// filtered (two register buffers, one block per SM).  Without PF (smaller r,
+// whose lagged reads are closer and more likely in L2) a chunk's loads are
+// issued when it starts, and two blocks fit an SM.
 constexpr int kChunkH = 8;
-__global__ void __launch_bounds__(64 * kHT, 2) lr_horz(const __grid_constant__ LrParams p) {
+template <bool PF>
+__global__ void __launch_bounds__(64 * kHT, PF ? 1 : 2) lr_horz(const __grid_constant__ LrParams p) {
     __shared__ float hs_sm[2][2 * kHT][kChunkH][32];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int q = warp & 1;
     const int tl = warp >> 1;
-    const int term = blockIdx.z * kHT + tl;
-    const bool term_ok = term < p.n_terms;  // uniform per warp
-    const int tc = min(term, p.n_terms - 1);
     const int W = p.W;
     const size_t plane = blocked_plane(p.H, W);
-    const int rb = min(blockIdx.x * 2 + (lane >> 4), p.nyb - 1);
-    const int y_lane = rb * kYB + (lane & (kYB - 1));
-    const size_t row = blocked_at(W, 0, min(y_lane, p.H - 1));  // column 0 of this lane's row
-    const float2 *V = reinterpret_cast<const float2 *>(p.Vt) + ((size_t)(p.h0 + tc) * 2 + q) * plane + row;
-    const float *F = p.ft + row;
-    const int x0 = blockIdx.y * p.band_w;
-    const int x1 = min(x0 + p.band_w, W);
     const int r = p.r, L = 2 * r + 1;
-    const int p0 = x0 - 3 * r;  // inputs before p0 count as zero
-    const int e_end = x1 + 3 * r;
-    const float am = term_ok ? p.ah[tc] : 0.f, tm = p.th[tc];
     const float2 z2 = make_float2(0.f, 0.f);
-    float2 s1a = z2, s1b = z2, s1c = z2, s2a = z2, s2b = z2, s3 = z2;
     // reduction role: thread -> (pair rq, step rd, lane rl) outputs of a chunk
     constexpr int NOUT = 2 * kChunkH * 32;
     constexpr int PER = NOUT / (64 * kHT);
     static_assert(NOUT % (64 * kHT) == 0, "reduction split");
+    const int nyb2 = (p.nyb + 1) / 2;
+    const int nbw = (W + p.band_w - 1) / p.band_w;
+    const int n_groups = (p.n_terms + kHT - 1) / kHT;
+    const int n_items = nyb2 * nbw * n_groups;
     int buf = 0;
-    for (int e0 = p0; e0 < e_end; e0 += kChunkH) {
-        // the pair at e, e - L, e - 2L, e - 3L for the chunk's steps (0 before p0)
-        float2 cv[kChunkH][4];
-        const bool edge = max(e0 - 3 * L, p0) < 0 || e0 + kChunkH > W;  // uniform
-        if (!edge) {
-            const float2 *v0 = V + (ptrdiff_t)e0 * kYB;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int iy = item % nyb2;
+        const int ix = (item / nyb2) % nbw;
+        const int gz = item / (nyb2 * nbw);
+        const int term = gz * kHT + tl;
+        const bool term_ok = term < p.n_terms;  // uniform per warp
+        const int tc = min(term, p.n_terms - 1);
+        const int rb = min(iy * 2 + (lane >> 4), p.nyb - 1);
+        const int y_lane = rb * kYB + (lane & (kYB - 1));
+        const size_t row = blocked_at(W, 0, min(y_lane, p.H - 1));  // column 0 of this row
+        const float2 *V =
+            reinterpret_cast<const float2 *>(p.Vt) + ((size_t)(p.h0 + tc) * 2 + q) * plane + row;
+        const float *F = p.ft + row;
+        const int x0 = ix * p.band_w;
+        const int x1 = min(x0 + p.band_w, W);
+        const int p0 = x0 - 3 * r;  // inputs before p0 count as zero
+        const int e_end = x1 + 3 * r;
+        const float am = term_ok ? p.ah[tc] : 0.f, tm = p.th[tc];
+        float2 s1a = z2, s1b = z2, s1c = z2, s2a = z2, s2b = z2, s3 = z2;
+        // the pair at e, e - L, e - 2L, e - 3L for the steps of the chunk at e0
+        // (0 before p0), and the pixel value at its outputs
+        auto load = [&](int e0, float2 (&cv)[kChunkH][4], float (&cf)[kChunkH]) {
+            const bool edge = max(e0 - 3 * L, p0) < 0 || e0 + kChunkH > W;  // uniform
+            if (!edge) {
+                const float2 *v0 = V + (ptrdiff_t)e0 * kYB;
 #pragma unroll
-            for (int d = 0; d < kChunkH; ++d) cv[d][0] = __ldg(v0 + d * kYB);
+                for (int d = 0; d < kChunkH; ++d) cv[d][0] = __ldg(v0 + d * kYB);
 #pragma unroll
-            for (int k = 1; k < 4; ++k) {
-                const int rel = e0 - k * L - p0;  // step d valid iff rel + d >= 0
-                const float2 *vk = v0 - (ptrdiff_t)k * L * kYB;
-                if (rel >= 0) {
+                for (int k = 1; k < 4; ++k) {
+                    const int rel = e0 - k * L - p0;  // step d valid iff rel + d >= 0
+                    const float2 *vk = v0 - (ptrdiff_t)k * L * kYB;
+                    if (rel >= 0) {
 #pragma unroll
-                    for (int d = 0; d < kChunkH; ++d) cv[d][k] = __ldg(vk + d * kYB);
-                } else if (rel > -kChunkH) {
+                        for (int d = 0; d < kChunkH; ++d) cv[d][k] = __ldg(vk + d * kYB);
+                    } else if (rel > -kChunkH) {
 #pragma unroll
-                    for (int d = 0; d < kChunkH; ++d) {
-                        const float2 v = __ldg(vk + max(d, -rel) * kYB);
-                        cv[d][k] = rel + d >= 0 ? v : z2;
+                        for (int d = 0; d < kChunkH; ++d) {
+                            const float2 v = __ldg(vk + max(d, -rel) * kYB);
+                            cv[d][k] = rel + d >= 0 ? v : z2;
+                        }
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < kChunkH; ++d) cv[d][k] = z2;
                     }
-                } else {
+                }
+            } else {
 #pragma unroll
-                    for (int d = 0; d < kChunkH; ++d) cv[d][k] = z2;
+                for (int d = 0; d < kChunkH; ++d) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int pos = e0 + d - k * L;
+                        const float2 v = __ldg(V + (ptrdiff_t)min(max(pos, 0), W - 1) * kYB);
+                        cv[d][k] = pos >= p0 ? v : z2;
+                    }
                 }
             }
-        } else {
+            const int t0 = e0 - 3 * r;
+            if (t0 >= x0 && t0 + kChunkH <= x1) {  // uniform
+                const float *f0 = F + (ptrdiff_t)t0 * kYB;
 #pragma unroll
-            for (int d = 0; d < kChunkH; ++d) {
+                for (int d = 0; d < kChunkH; ++d) cf[d] = __ldg(f0 + d * kYB);
+            } else {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int pos = e0 + d - k * L;
-                    const float2 v = __ldg(V + (ptrdiff_t)min(max(pos, 0), W - 1) * kYB);
-                    cv[d][k] = pos >= p0 ? v : z2;
-                }
+                for (int d = 0; d < kChunkH; ++d)
+                    cf[d] = __ldg(F + (ptrdiff_t)min(max(t0 + d, 0), W - 1) * kYB);
             }
-        }
-        const int t0 = e0 - 3 * r;  // output column of step 0
-        if (t0 + kChunkH <= x0) {
-            // warm-up chunk: no outputs (uniform over the block)
+        };
+        // one chunk: prefetch the next one into (nxt, nxtf), filter (cur, curf)
+        auto body = [&](int e0, float2 (&cur)[kChunkH][4], float (&curf)[kChunkH],
+                        float2 (&nxt)[kChunkH][4], float (&nxtf)[kChunkH]) {
+            if constexpr (PF) {
+                if (e0 + kChunkH < e_end) load(e0 + kChunkH, nxt, nxtf);
+            } else {
+                load(e0, cur, curf);
+            }
+            const int t0 = e0 - 3 * r;  // output column of step 0
+            if (t0 + kChunkH <= x0) {
+                // warm-up chunk: no outputs (uniform over the block)
+#pragma unroll
+                for (int d = 0; d < kChunkH; ++d) {
+                    s1a = f2add(s1a, f2sub(cur[d][0], cur[d][1]));
+                    s1b = f2add(s1b, f2sub(cur[d][1], cur[d][2]));
+                    s1c = f2add(s1c, f2sub(cur[d][2], cur[d][3]));
+                    s2a = f2add(s2a, f2sub(s1a, s1b));
+                    s2b = f2add(s2b, f2sub(s1b, s1c));
+                    s3 = f2add(s3, f2sub(s2a, s2b));
+                }
+                return;
+            }
+            // steps past e_end (last chunk) run on clamped inputs and store nothing
 #pragma unroll
             for (int d = 0; d < kChunkH; ++d) {
-                s1a = f2add(s1a, f2sub(cv[d][0], cv[d][1]));
-                s1b = f2add(s1b, f2sub(cv[d][1], cv[d][2]));
-                s1c = f2add(s1c, f2sub(cv[d][2], cv[d][3]));
+                s1a = f2add(s1a, f2sub(cur[d][0], cur[d][1]));
+                s1b = f2add(s1b, f2sub(cur[d][1], cur[d][2]));
+                s1c = f2add(s1c, f2sub(cur[d][2], cur[d][3]));
                 s2a = f2add(s2a, f2sub(s1a, s1b));
                 s2b = f2add(s2b, f2sub(s1b, s1c));
                 s3 = f2add(s3, f2sub(s2a, s2b));
+                float rr = tm * curf[d];
+                rr = rr - rintf(rr);
+                float sn, cs;
+                __sincosf(kTwoPi * rr, &sn, &cs);
+                hs_sm[buf][warp][d][lane] = am * fmaf(cs, s3.x, sn * s3.y);
             }
-            continue;
-        }
-        // the pixel value at the chunk's outputs
-        float cf[kChunkH];
-        if (t0 >= x0 && t0 + kChunkH <= x1) {  // uniform
-            const float *f0 = F + (ptrdiff_t)t0 * kYB;
+            __syncthreads();
+            // sum the group's terms in term order and write the slot
 #pragma unroll
-            for (int d = 0; d < kChunkH; ++d) cf[d] = __ldg(f0 + d * kYB);
+            for (int k = 0; k < PER; ++k) {
+                const int o = k * 64 * kHT + threadIdx.x;
+                const int rq = o / (kChunkH * 32);
+                const int rd = (o / 32) % kChunkH;
+                const int rl = o % 32;
+                float v = hs_sm[buf][rq][rd][rl];
+#pragma unroll
+                for (int t = 1; t < kHT; ++t) v += hs_sm[buf][2 * t + rq][rd][rl];
+                const int tcol = t0 + rd;
+                const int orb = iy * 2 + (rl >> 4);
+                const int oy = orb * kYB + (rl & (kYB - 1));
+                if (tcol >= x0 && tcol < x1 && orb < p.nyb && oy < p.H) {
+                    float *A = p.Acc + ((size_t)gz * 2 + rq) * plane + blocked_at(W, tcol, oy);
+                    *A = p.first ? v : *A + v;
+                }
+            }
+            buf ^= 1;
+        };
+        float2 ca[kChunkH][4], cb[kChunkH][4];
+        float fa[kChunkH], fb[kChunkH];
+        if constexpr (PF) {
+            load(p0, ca, fa);
+            // two chunks per iteration so that the buffers swap roles without copies
+            for (int e0 = p0; e0 < e_end; e0 += 2 * kChunkH) {
+                body(e0, ca, fa, cb, fb);
+                if (e0 + kChunkH < e_end) body(e0 + kChunkH, cb, fb, ca, fa);
+            }
         } else {
-#pragma unroll
-            for (int d = 0; d < kChunkH; ++d)
-                cf[d] = __ldg(F + (ptrdiff_t)min(max(t0 + d, 0), W - 1) * kYB);
+            for (int e0 = p0; e0 < e_end; e0 += kChunkH) body(e0, ca, fa, cb, fb);
         }
-        // steps past e_end (last chunk) run on clamped inputs and store nothing
-#pragma unroll
-        for (int d = 0; d < kChunkH; ++d) {
-            s1a = f2add(s1a, f2sub(cv[d][0], cv[d][1]));
-            s1b = f2add(s1b, f2sub(cv[d][1], cv[d][2]));
-            s1c = f2add(s1c, f2sub(cv[d][2], cv[d][3]));
-            s2a = f2add(s2a, f2sub(s1a, s1b));
-            s2b = f2add(s2b, f2sub(s1b, s1c));
-            s3 = f2add(s3, f2sub(s2a, s2b));
-            float rr = tm * cf[d];
-            rr = rr - rintf(rr);
-            float sn, cs;
-            __sincosf(kTwoPi * rr, &sn, &cs);
-            hs_sm[buf][warp][d][lane] = am * fmaf(cs, s3.x, sn * s3.y);
-        }
-        __syncthreads();
-        // sum the group's terms in term order and write the slot
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int o = k * 64 * kHT + threadIdx.x;
-            const int rq = o / (kChunkH * 32);
-            const int rd = (o / 32) % kChunkH;
-            const int rl = o % 32;
-            float v = hs_sm[buf][rq][rd][rl];
-#pragma unroll
-            for (int t = 1; t < kHT; ++t) v += hs_sm[buf][2 * t + rq][rd][rl];
-            const int tcol = t0 + rd;
-            const int orb = blockIdx.x * 2 + (rl >> 4);
-            const int oy = orb * kYB + (rl & (kYB - 1));
-            if (tcol >= x0 && tcol < x1 && orb < p.nyb && oy < p.H) {
-                float *A = p.Acc + ((size_t)blockIdx.z * 2 + rq) * plane +
-                           blocked_at(W, tcol, oy);
-                *A = p.first ? v : *A + v;
-            }
-        }
-        buf ^= 1;
     }
 }
 
@@ -513,19 +557,40 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     if (e != cudaSuccess) return e;
     const int resident_vert = std::max(1, n_sm * per_sm);
 
-    // Bands.  lr_vert's (multiples of 8 rows): as many as one wave of
-    // resident blocks holds (a partial second wave costs a whole band's time).
-    // lr_horz's: enough for about kHWarps warps in all.  Both stay at least
-    // 12r long (the 6r warm-up at most half a band).
+    // lr_vert's bands (multiples of 8 rows): as many as one wave of resident
+    // blocks holds (a partial second wave costs a whole band's time), at
+    // least 12r long (the 6r warm-up at most half a band).
     const int min_band = 12 * p.r;
     const int ncb = (W + kVCols - 1) / kVCols;
     const int zb_max = (gv_max + kVB - 1) / kVB;
-    const int nbh_max = std::max(1, std::min(resident_vert / (ncb * zb_max), H / min_band));
+    const int nbh_max = std::max(
+        1, std::min(std::max(kVBandsMin, resident_vert / (ncb * zb_max)), H / min_band));
     p.band_h = ((H + nbh_max - 1) / nbh_max + 7) / 8 * 8;
     const int nbh = (H + p.band_h - 1) / p.band_h;
     const int nyb2 = (p.nyb + 1) / 2;
-    const int g_warps = nyb2 * n_slots * 2 * kHT;
-    const int nbw_max = std::max(1, std::min((kHWarps + g_warps / 2) / g_warps, W / min_band));
+    // lr_horz: resident blocks as many as fit the SMs -- for large r (the
+    // prefetching variant) only as many as keep the columns each lane reads
+    // back (3L of them, 8 bytes each) within kHorzL2Bytes of L2.  Bands of
+    // columns only add warm-up, so there are just enough of them for every
+    // resident block to have an item when the terms are few.
+    // The prefetching variant needs enough items to fill its grid; with few
+    // terms the other one, two blocks per SM over more bands, does better.
+    const size_t lag_bytes = (size_t)64 * kHT * 8 * 3 * (size_t)L_of(p.r);
+    const int items0 = nyb2 * ((std::min(nt, gv_max) + kHT - 1) / kHT);
+    int per_sm_h = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_h, lr_horz<true>, 64 * kHT, 0);
+    if (e != cudaSuccess) return e;
+    const size_t pf_grid =
+        std::min((size_t)n_sm * std::max(1, per_sm_h), kHorzL2Bytes / lag_bytes);
+    const bool pf = p.r >= kHorzPrefetchR && (size_t)items0 >= pf_grid;
+    auto kh = pf ? lr_horz<true> : lr_horz<false>;
+    if (!pf) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_h, kh, 64 * kHT, 0);
+        if (e != cudaSuccess) return e;
+    }
+    const int horz_grid = (int)std::max<size_t>(
+        1, pf ? pf_grid : (size_t)n_sm * std::max(1, per_sm_h));
+    const int nbw_max = std::max(1, std::min(horz_grid / items0, W / min_band));
     p.band_w = ((W + nbw_max - 1) / nbw_max + 7) / 8 * 8;
     const int nbw = (W + p.band_w - 1) / p.band_w;
 
@@ -548,8 +613,8 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
             p.first = m0 == 0;
             dim3 gv(ncb, nbh, (nv + kVB - 1) / kVB);
             kv<<<gv, kVCols * kVB, sm_v, s>>>(p);
-            dim3 gh(nyb2, nbw, (nv + kHT - 1) / kHT);
-            lr_horz<<<gh, 64 * kHT, 0, s>>>(p);
+            const int items = nyb2 * nbw * ((nv + kHT - 1) / kHT);
+            kh<<<std::min(items, horz_grid), 64 * kHT, 0, s>>>(p);
         }
         dim3 gf((W + 31) / 32, (H + 31) / 32);
         lr_final<<<gf, dim3(32, 8), 0, s>>>(
