@@ -90,6 +90,7 @@ cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, c
         prm.total = (float)norm;
     }
     (void)halo;
+    pair_taps(&prm.taps);
     cudaError_t e;
     if (pl->kind == BF_SPATIAL_GAUSS_TRUNC) {
         switch (gauss_bwd_radius(pl->R)) {

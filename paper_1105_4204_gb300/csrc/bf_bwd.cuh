@@ -53,20 +53,23 @@ struct BwdGeom {
     static constexpr int NSEG = TW / TWT;
     static constexpr int NT = TH * NSEG;
     static constexpr int LN = TWT + 2 * HALO;
-    static constexpr int LN4 = (LN + 3) / 4;
     static constexpr int SF = (EW + 3) / 4 * 4;
-    static constexpr int SV_MIN4 = (TW - TWT + 4 * LN4 + 3) / 4;
-    static constexpr int SV = 4 * (SV_MIN4 % 2 ? SV_MIN4 : SV_MIN4 + 1);
-    static constexpr int SC4 = TW / 4;
-    static constexpr int SC = 4 * (SC4 % 2 ? SC4 : SC4 + 1);
-    static constexpr int NPL = 6;  // planes held at once
+    // filtered planes as rows of float2 {cos part, sin part}; the row stride
+    // covers the columns phase 1 writes and the float4s a segment reads, and
+    // is 2 mod 4 float2 (an odd number of 16-byte units)
+    static constexpr int LN2 = (LN + 1) / 2 * 2;
+    static constexpr int SV2_MIN = (EW > TW - TWT + LN2 ? EW : TW - TWT + LN2);
+    static constexpr int SV2 = (SV2_MIN + 3) / 4 * 4 + 2;
+    static constexpr int SC2 = (TW + 3) / 4 * 4 + 2;
+    static constexpr int NPL = 3;  // pair planes held at once
     static constexpr int T_FLOATS = EH * SF;  // one extended tile
-    static constexpr int V_FLOATS = NPL * TH * SV;
-    static constexpr int C_FLOATS = 2 * TH * SC;
+    static constexpr int V_FLOATS = NPL * 2 * TH * SV2;
+    static constexpr int C_FLOATS = 2 * TH * SC2;
     static constexpr size_t SMEM =
         sizeof(float) * (size_t)(3 * T_FLOATS + V_FLOATS + C_FLOATS) + sizeof(double) * NT;
     static_assert(TW % TWT == 0 && TWT % 4 == 0, "segments");
     static_assert(NT <= 1024, "block");
+    static_assert(2 * EW <= NT, "one phase-1 item per thread");
 };
 
 template <int KIND, int RAD, int TH, int TW, int TWT>
@@ -74,13 +77,17 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
     bf_tile_bwd(const __grid_constant__ BwdParams p) {
     using G = BwdGeom<KIND, RAD, TH, TW, TWT>;
     constexpr int HALO = G::HALO, EH = G::EH, EW = G::EW;
+    constexpr int SV2 = G::SV2, SC2 = G::SC2;
+    // round A's three planes in one sweep while the two pairs' filter window
+    // fits in registers
+    constexpr bool kOneSweep = KIND == 0 ? RAD <= 12 : RAD <= 4;
     extern __shared__ float4 smem4[];
     float *Fs = reinterpret_cast<float *>(smem4);  // f, clamp-extended
     float *As = Fs + G::T_FLOATS;                   // alpha, zero outside the image
     float *Os = As + G::T_FLOATS;                   // o, clamp-extended
-    float *V = Os + G::T_FLOATS;                    // filtered planes
-    float *Cc = V + G::V_FLOATS;                    // cos, sin at the tile's pixels
-    double *red = reinterpret_cast<double *>(Cc + G::C_FLOATS);
+    float *V = Os + G::T_FLOATS;                    // filtered pair planes (3 x TH x SV2 float2)
+    float *CC = V + G::V_FLOATS;                    // {cos, sin} at the tile's pixels
+    double *red = reinterpret_cast<double *>(CC + G::C_FLOATS);
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TW;
@@ -116,36 +123,84 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
     const int lef = (x0 == 0) ? 0 : -1;
     const int rig = (W - 1 >= x0 && W - 1 < x0 + TW) ? W - 1 - x0 : -1;
 
+    // phase-1 identity: (extended column j1, q1 = cos | sin); adjacent lanes
+    // take cos and sin of one column, so their stores are contiguous
+    const int j1 = tid >> 1;
+    const int q1 = tid & 1;
+    const bool p1 = tid < 2 * EW;
+    const bool own_col = j1 >= HALO && j1 < HALO + TW;
+    const float ph0 = q1 ? 0.f : 0.25f;  // cos(t) = sin(t + quarter turn)
+
+    // one phase-2 pass: filter row pi of pair plane `pl` horizontally from
+    // column cx0 and hand output k to use(k, z)
+    auto hpass = [&](int pl, auto &&use) {
+        const float4 *src4 =
+            reinterpret_cast<const float4 *>(V + 2 * ((size_t)pl * TH * SV2 + pi * SV2 + cx0));
+        float4 ld[(G::LN + 1) / 2];
+        auto gen = [&](int i) {
+            if ((i & 1) == 0) ld[i >> 1] = src4[i >> 1];
+            const float4 v = ld[i >> 1];
+            return (i & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+        };
+        filt2_stream<KIND, RAD, G::LN>(gen, use, p.taps.w2);
+    };
+
     const int n_terms = p.terms.n_terms;
     for (int m = 0; m < n_terms; ++m) {
         const float am = p.terms.a[m];
         const float tm = p.terms.t[m];
         const float wm = p.omega[m];
-        // ================= round A: W of c, s, f c, f s, f^2 c, f^2 s
+        // ================= round A: W of (c, s), (f c, f s), (f^2 c, f^2 s)
         __syncthreads();
-        for (int item = tid; item < 2 * EW; item += G::NT) {
-            const int qq = item >= EW ? 1 : 0;
-            const int j = item - qq * EW;
-            const float ph0 = qq ? 0.f : 0.25f;
-            float x[EH];
-#pragma unroll
-            for (int i = 0; i < EH; ++i) x[i] = sin_turns(fmaf(tm, Fs[i * G::SF + j], ph0));
-            if (j >= HALO && j < HALO + TW) {
-                float *cd = Cc + qq * TH * G::SC + (j - HALO);
-#pragma unroll
-                for (int i = 0; i < TH; ++i) cd[i * G::SC] = x[i + HALO];
-            }
-            float y[TH];
-#pragma unroll 1
-            for (int pw = 0; pw < 3; ++pw) {
-                if (pw > 0) {
-#pragma unroll
-                    for (int i = 0; i < EH; ++i) x[i] *= Fs[i * G::SF + j];
-                }
-                Filt<KIND, RAD, EH>::run(x, y, p.taps.w);
-                float *vd = V + (2 * pw + qq) * TH * G::SV + j;
-#pragma unroll
-                for (int i = 0; i < TH; ++i) vd[i * G::SV] = y[i];
+        if (p1) {
+            const float *fcol = Fs + j1;
+            float *ccol = CC + 2 * (j1 - HALO) + q1;
+            float *v0 = V + 2 * j1 + q1;
+            auto gen_x = [&](int i, float &fv) {
+                fv = fcol[i * G::SF];
+                return sin_turns(fmaf(tm, fv, ph0));
+            };
+            if constexpr (kOneSweep) {
+                // (x, f x) and (f^2 x, 0) of one generated x in one sweep
+                auto gen = [&](int i) {
+                    float fv;
+                    const float x = gen_x(i, fv);
+                    if (i >= HALO && i < HALO + TH && own_col) ccol[(i - HALO) * 2 * SC2] = x;
+                    Pairs<2> o;
+                    const float fx = x * fv;
+                    o.v[0] = make_float2(x, fx);
+                    o.v[1] = make_float2(fx * fv, 0.f);
+                    return o;
+                };
+                auto sink = [&](int k, const Pairs<2> &y) {
+                    v0[k * 2 * SV2] = y.v[0].x;
+                    v0[(TH + k) * 2 * SV2] = y.v[0].y;
+                    v0[(2 * TH + k) * 2 * SV2] = y.v[1].x;
+                };
+                AheadN<kGenAhead, EH, 2, decltype(gen)> ahead(gen);
+                filt2n_stream<KIND, RAD, EH, 2>(ahead, sink, p.taps.w2);
+            } else {
+                // wide supports: two sweeps, x generated again for the second
+                auto gen = [&](int i) {
+                    float fv;
+                    const float x = gen_x(i, fv);
+                    if (i >= HALO && i < HALO + TH && own_col) ccol[(i - HALO) * 2 * SC2] = x;
+                    return make_float2(x, x * fv);
+                };
+                auto sink = [&](int k, float2 y) {
+                    v0[k * 2 * SV2] = y.x;
+                    v0[(TH + k) * 2 * SV2] = y.y;
+                };
+                Ahead<kGenAhead, EH, decltype(gen)> ahead(gen);
+                filt2_stream<KIND, RAD, EH>(ahead, sink, p.taps.w2);
+                auto gen2 = [&](int i) {
+                    float fv;
+                    const float x = gen_x(i, fv);
+                    return make_float2(x * fv * fv, 0.f);
+                };
+                auto sink2 = [&](int k, float2 y) { v0[(2 * TH + k) * 2 * SV2] = y.x; };
+                Ahead<kGenAhead, EH, decltype(gen2)> ahead2(gen2);
+                filt2_stream<KIND, RAD, EH>(ahead2, sink2, p.taps.w2);
             }
         }
         __syncthreads();
@@ -156,124 +211,71 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
             for (int k = 0; k < TWT; ++k) {
                 const int ti = (pi + HALO) * G::SF + cx0 + k + HALO;
                 const float kk = am * wm * As[ti];
-                kc[k] = kk * Cc[pi * G::SC + cx0 + k];
-                ks[k] = kk * Cc[TH * G::SC + pi * G::SC + cx0 + k];
+                const float2 cs = *reinterpret_cast<const float2 *>(CC + 2 * (pi * SC2 + cx0 + k));
+                kc[k] = kk * cs.x;
+                ks[k] = kk * cs.y;
                 fp[k] = Fs[ti];
                 op[k] = Os[ti];
             }
-#pragma unroll 1
-            for (int pl = 0; pl < 6; ++pl) {
-                const float4 *src = reinterpret_cast<const float4 *>(V + pl * TH * G::SV +
-                                                                     pi * G::SV + cx0);
-                float yv[4 * G::LN4];
-#pragma unroll
-                for (int k = 0; k < G::LN4; ++k) {
-                    const float4 v4 = src[k];
-                    yv[4 * k] = v4.x;
-                    yv[4 * k + 1] = v4.y;
-                    yv[4 * k + 2] = v4.z;
-                    yv[4 * k + 3] = v4.w;
-                }
-                float yin[G::LN];
-#pragma unroll
-                for (int k = 0; k < G::LN; ++k) yin[k] = yv[k];
-                float z[TWT];
-                Filt<KIND, RAD, G::LN>::run(yin, z, p.taps.w);
-                // this plane's weights in dL/df (gc) and dL/dsigma_r (sc)
-                float gc[TWT], sc[TWT];
-                switch (pl) {
-                    case 0:  // W[c]
-#pragma unroll
-                        for (int k = 0; k < TWT; ++k) {
-                            gc[k] = ks[k] * op[k];
-                            sc[k] = -ks[k] * fp[k] * op[k];
-                        }
-                        break;
-                    case 1:  // W[s]
-#pragma unroll
-                        for (int k = 0; k < TWT; ++k) {
-                            gc[k] = -kc[k] * op[k];
-                            sc[k] = kc[k] * fp[k] * op[k];
-                        }
-                        break;
-                    case 2:  // W[f c]
-#pragma unroll
-                        for (int k = 0; k < TWT; ++k) {
-                            gc[k] = -ks[k];
-                            sc[k] = ks[k] * (fp[k] + op[k]);
-                        }
-                        break;
-                    case 3:  // W[f s]
-#pragma unroll
-                        for (int k = 0; k < TWT; ++k) {
-                            gc[k] = kc[k];
-                            sc[k] = -kc[k] * (fp[k] + op[k]);
-                        }
-                        break;
-                    case 4:  // W[f^2 c]
-#pragma unroll
-                        for (int k = 0; k < TWT; ++k) {
-                            gc[k] = 0.f;
-                            sc[k] = -ks[k];
-                        }
-                        break;
-                    default:  // W[f^2 s]
-#pragma unroll
-                        for (int k = 0; k < TWT; ++k) {
-                            gc[k] = 0.f;
-                            sc[k] = kc[k];
-                        }
-                        break;
-                }
-#pragma unroll
-                for (int k = 0; k < TWT; ++k) {
-                    gacc[k] = fmaf(gc[k], z[k], gacc[k]);
-                    sacc[k] = fmaf(sc[k], z[k], sacc[k]);
-                }
-            }
+            // (W[c], W[s])
+            hpass(0, [&](int k, float2 z) {
+                gacc[k] = fmaf(ks[k] * op[k], z.x, fmaf(-kc[k] * op[k], z.y, gacc[k]));
+                sacc[k] = fmaf(-ks[k] * fp[k] * op[k], z.x, fmaf(kc[k] * fp[k] * op[k], z.y, sacc[k]));
+            });
+            // (W[f c], W[f s])
+            hpass(1, [&](int k, float2 z) {
+                gacc[k] = fmaf(-ks[k], z.x, fmaf(kc[k], z.y, gacc[k]));
+                const float fo = fp[k] + op[k];
+                sacc[k] = fmaf(ks[k] * fo, z.x, fmaf(-kc[k] * fo, z.y, sacc[k]));
+            });
+            // (W[f^2 c], W[f^2 s])
+            hpass(2, [&](int k, float2 z) {
+                sacc[k] = fmaf(-ks[k], z.x, fmaf(kc[k], z.y, sacc[k]));
+            });
         }
-        // ================= round B: W^T of alpha c, alpha s, alpha o c, alpha o s
+        // ================= round B: W^T of (alpha c, alpha s), (alpha o c, alpha o s)
         __syncthreads();
-        for (int item = tid; item < 2 * EW; item += G::NT) {
-            const int qq = item >= EW ? 1 : 0;
-            const int j = item - qq * EW;
-            const float ph0 = qq ? 0.f : 0.25f;
-            float x[EH];
-#pragma unroll
-            for (int i = 0; i < EH; ++i)
-                x[i] = As[i * G::SF + j] * sin_turns(fmaf(tm, Fs[i * G::SF + j], ph0));
-            float y[TH];
-#pragma unroll 1
-            for (int pw = 0; pw < 2; ++pw) {
-                if (pw > 0) {
-#pragma unroll
-                    for (int i = 0; i < EH; ++i) x[i] *= Os[i * G::SF + j];
+        if (p1) {
+            const float *fcol = Fs + j1;
+            const float *acol = As + j1;
+            const float *ocol = Os + j1;
+            float *v0 = V + 2 * j1 + q1;
+            auto gen = [&](int i) {
+                const float g = acol[i * G::SF] * sin_turns(fmaf(tm, fcol[i * G::SF], ph0));
+                return make_float2(g, g * ocol[i * G::SF]);
+            };
+            auto sink = [&](int k, float2 y) {
+                v0[k * 2 * SV2] = y.x;
+                v0[(TH + k) * 2 * SV2] = y.y;
+            };
+            Ahead<kGenAhead, EH, decltype(gen)> ahead(gen);
+            filt2_stream<KIND, RAD, EH>(ahead, sink, p.taps.w2);
+            // tail fold at the image's first / last row (a one-row image
+            // keeps the whole mass on its only row); values regenerated
+            if (top >= 0 && bot == top) {
+                const float2 g = gen(HALO);
+                v0[top * 2 * SV2] = p.total * g.x;
+                v0[(TH + top) * 2 * SV2] = p.total * g.y;
+            } else if (top >= 0) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int d = 0; d <= HALO; ++d) {
+                    const float2 g = gen(HALO + d);
+                    acc.x = fmaf(p.tail[d], g.x, acc.x);
+                    acc.y = fmaf(p.tail[d], g.y, acc.y);
                 }
-                Filt<KIND, RAD, EH>::run(x, y, p.taps.w);
-                float *vd = V + (2 * pw + qq) * TH * G::SV + j;
-#pragma unroll
-                for (int i = 0; i < TH; ++i) vd[i * G::SV] = y[i];
-                // tail fold at the image's first / last row (a one-row image
-                // keeps the whole mass on its only row)
-                if (top >= 0 && bot == top) {
-                    vd[top * G::SV] = p.total * x[HALO];
-                } else if (top >= 0) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int d = 0; d <= HALO; ++d) acc = fmaf(p.tail[d], x[HALO + d], acc);
-                    vd[top * G::SV] = acc;
+                v0[top * 2 * SV2] = acc.x;
+                v0[(TH + top) * 2 * SV2] = acc.y;
+            }
+            if (bot >= 0 && bot != top) {
+                // image row H-1-d sits at extended row bot + HALO - d (>= 0)
+                float2 acc = make_float2(0.f, 0.f);
+                for (int d = 0; d <= HALO; ++d) {
+                    const float2 g = gen(bot + HALO - d);
+                    acc.x = fmaf(p.tail[d], g.x, acc.x);
+                    acc.y = fmaf(p.tail[d], g.y, acc.y);
                 }
-                if (bot >= 0 && bot != top) {
-                    // image row H-1-d sits at extended row bot + HALO - d (>= 0)
-                    float acc = 0.f;
-                    for (int d = 0; d <= HALO; ++d) {
-                        const int i = bot + HALO - d;
-                        float g = As[i * G::SF + j] * sin_turns(fmaf(tm, Fs[i * G::SF + j], ph0));
-                        if (pw > 0) g *= Os[i * G::SF + j];
-                        acc = fmaf(p.tail[d], g, acc);
-                    }
-                    vd[bot * G::SV] = acc;
-                }
+                v0[bot * 2 * SV2] = acc.x;
+                v0[(TH + bot) * 2 * SV2] = acc.y;
             }
         }
         __syncthreads();
@@ -282,8 +284,8 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
 #pragma unroll
             for (int k = 0; k < TWT; ++k) {
                 const int ti = (pi + HALO) * G::SF + cx0 + k + HALO;
-                const float c = Cc[pi * G::SC + cx0 + k];
-                const float s = Cc[TH * G::SC + pi * G::SC + cx0 + k];
+                const float2 cs = *reinterpret_cast<const float2 *>(CC + 2 * (pi * SC2 + cx0 + k));
+                const float c = cs.x, s = cs.y;
                 const float fv = Fs[ti];
                 const float aw = am * wm;
                 ca[k] = am * c - aw * s * fv;  // W^T[alpha c]
@@ -292,44 +294,40 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
                 cd[k] = -aw * c;               // W^T[alpha o s]
             }
 #pragma unroll 1
-            for (int pl = 0; pl < 4; ++pl) {
-                const float *row = V + pl * TH * G::SV + pi * G::SV;
-                const float4 *src = reinterpret_cast<const float4 *>(row + cx0);
-                float yv[4 * G::LN4];
-#pragma unroll
-                for (int k = 0; k < G::LN4; ++k) {
-                    const float4 v4 = src[k];
-                    yv[4 * k] = v4.x;
-                    yv[4 * k + 1] = v4.y;
-                    yv[4 * k + 2] = v4.z;
-                    yv[4 * k + 3] = v4.w;
-                }
-                float yin[G::LN];
-#pragma unroll
-                for (int k = 0; k < G::LN; ++k) yin[k] = yv[k];
-                float z[TWT];
-                Filt<KIND, RAD, G::LN>::run(yin, z, p.taps.w);
-                // tail fold at the image's first / last column
+            for (int pl = 0; pl < 2; ++pl) {
+                // tail fold at the image's first / last column: these outputs
+                // take the folded sums instead of the filter's
+                const float2 *row =
+                    reinterpret_cast<const float2 *>(V) + (size_t)pl * TH * SV2 + pi * SV2;
+                int kl = -1, kr = -1;
+                float2 zl = make_float2(0.f, 0.f), zr = zl;
                 if (lef >= 0 && rig == 0 && cx0 == 0) {
-                    z[0] = p.total * row[HALO];
+                    const float2 v = row[HALO];
+                    zl = make_float2(p.total * v.x, p.total * v.y);
+                    kl = 0;
                 } else if (lef >= 0 && cx0 == 0) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int d = 0; d <= HALO; ++d) acc = fmaf(p.tail[d], row[HALO + d], acc);
-                    z[0] = acc;
+                    for (int d = 0; d <= HALO; ++d) {
+                        const float2 v = row[HALO + d];
+                        zl.x = fmaf(p.tail[d], v.x, zl.x);
+                        zl.y = fmaf(p.tail[d], v.y, zl.y);
+                    }
+                    kl = 0;
                 }
                 if (rig >= cx0 && rig < cx0 + TWT && !(lef >= 0 && rig == 0)) {
-                    float acc = 0.f;
-                    for (int d = 0; d <= HALO; ++d) acc = fmaf(p.tail[d], row[rig + HALO - d], acc);
-#pragma unroll
-                    for (int k = 0; k < TWT; ++k)
-                        if (k == rig - cx0) z[k] = acc;
+                    for (int d = 0; d <= HALO; ++d) {
+                        const float2 v = row[rig + HALO - d];
+                        zr.x = fmaf(p.tail[d], v.x, zr.x);
+                        zr.y = fmaf(p.tail[d], v.y, zr.y);
+                    }
+                    kr = rig - cx0;
                 }
-#pragma unroll
-                for (int k = 0; k < TWT; ++k) {
-                    const float cf = pl == 0 ? ca[k] : pl == 1 ? cb[k] : pl == 2 ? cc[k] : cd[k];
-                    gacc[k] = fmaf(cf, z[k], gacc[k]);
-                }
+                hpass(pl, [&](int k, float2 z) {
+                    if (k == kl) z = zl;
+                    if (k == kr) z = zr;
+                    const float c0 = pl == 0 ? ca[k] : cc[k];
+                    const float c1 = pl == 0 ? cb[k] : cd[k];
+                    gacc[k] = fmaf(c0, z.x, fmaf(c1, z.y, gacc[k]));
+                });
             }
         }
     }

@@ -191,6 +191,122 @@ __device__ __forceinline__ void filt2_stream(Gen &&gen, Sink &&sink, const float
     }
 }
 
+// NP pairs per step, streamed together (the backward pass filters (x, f x) and
+// (f^2 x, 0) of one generated x in one sweep).
+template <int NP>
+struct Pairs {
+    float2 v[NP];
+};
+
+template <int NP>
+__device__ __forceinline__ Pairs<NP> padd(const Pairs<NP> &a, const Pairs<NP> &b) {
+    Pairs<NP> c;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) c.v[k] = f2add(a.v[k], b.v[k]);
+    return c;
+}
+
+template <int NP>
+__device__ __forceinline__ Pairs<NP> psub(const Pairs<NP> &a, const Pairs<NP> &b) {
+    Pairs<NP> c;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) c.v[k] = f2sub(a.v[k], b.v[k]);
+    return c;
+}
+
+template <int r, int NIN, int NP, class Gen, class Sink>
+__device__ __forceinline__ void box3_stream_n(Gen &&gen, Sink &&sink) {
+    constexpr int D = 2 * r;
+    Pairs<NP> a[NIN];
+    Pairs<NP> b[NIN - D];
+    Pairs<NP> c[NIN - 2 * D];
+    Pairs<NP> s1, s2, s3;
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+        a[i] = gen(i);
+        if (i >= D) {
+            const int k1 = i - D;
+            if (k1 == 0) {
+                s1 = a[0];
+#pragma unroll
+                for (int d = 1; d <= D; ++d) s1 = padd(s1, a[d]);
+            } else {
+                s1 = padd(s1, psub(a[k1 + D], a[k1 - 1]));
+            }
+            b[k1] = s1;
+            if (k1 >= D) {
+                const int k2 = k1 - D;
+                if (k2 == 0) {
+                    s2 = b[0];
+#pragma unroll
+                    for (int d = 1; d <= D; ++d) s2 = padd(s2, b[d]);
+                } else {
+                    s2 = padd(s2, psub(b[k2 + D], b[k2 - 1]));
+                }
+                c[k2] = s2;
+                if (k2 >= D) {
+                    const int k3 = k2 - D;
+                    if (k3 == 0) {
+                        s3 = c[0];
+#pragma unroll
+                        for (int d = 1; d <= D; ++d) s3 = padd(s3, c[d]);
+                    } else {
+                        s3 = padd(s3, psub(c[k3 + D], c[k3 - 1]));
+                    }
+                    sink(k3, s3);
+                }
+            }
+        }
+    }
+}
+
+template <int R, int NIN, int NP, class Gen, class Sink>
+__device__ __forceinline__ void gauss_stream_n(Gen &&gen, Sink &&sink,
+                                               const float2 *__restrict__ w2) {
+    Pairs<NP> a[NIN];
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+        a[i] = gen(i);
+        if (i >= 2 * R) {
+            const int k = i - 2 * R;
+            Pairs<NP> acc;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) acc.v[q] = f2mul(w2[0], a[k].v[q]);
+#pragma unroll
+            for (int d = 1; d <= 2 * R; ++d)
+#pragma unroll
+                for (int q = 0; q < NP; ++q) acc.v[q] = f2fma(w2[d], a[k + d].v[q], acc.v[q]);
+            sink(k, acc);
+        }
+    }
+}
+
+template <int KIND, int RAD, int NIN, int NP, class Gen, class Sink>
+__device__ __forceinline__ void filt2n_stream(Gen &&gen, Sink &&sink,
+                                              const float2 *__restrict__ w2) {
+    if constexpr (KIND == 0) {
+        gauss_stream_n<RAD, NIN, NP>(gen, sink, w2);
+    } else {
+        box3_stream_n<RAD, NIN, NP>(gen, sink);
+    }
+}
+
+// Generator adaptor for Pairs<NP> inputs, batches of GA as below.
+template <int GA, int NIN, int NP, class Gen>
+struct AheadN {
+    Gen &g;
+    Pairs<NP> buf[NIN];
+    __device__ __forceinline__ explicit AheadN(Gen &gen) : g(gen) {}
+    __device__ __forceinline__ Pairs<NP> operator()(int i) {
+        if (i % GA == 0) {
+#pragma unroll
+            for (int d = 0; d < GA; ++d)
+                if (i + d < NIN) buf[i + d] = g(i + d);
+        }
+        return buf[i];
+    }
+};
+
 // Generator adaptor: produces the inputs in batches of GA so that their
 // independent latency chains (shared-memory load, sine) overlap; measured
 // faster than generating one input per step (too little to overlap) or all of
