@@ -131,8 +131,8 @@ bf_status bf_plan_weights(const bf_plan *plan, double *w1, int cap, int *count);
  * Kernels: the fused tile kernel serves the truncated Gaussian (R <= 24) and
  * the box with r <= 8.  For the box with 8 < r <= 64 the support does not fit
  * on chip and the filter runs as streaming sweeps (vertical, then horizontal)
- * through a scratch buffer of about (4 * terms + 17) * H * W floats (terms
- * capped so that the vertical sweep's output stays within 4 GiB) that the
+ * through a scratch buffer of about (4 * terms + 2 * ceil(terms / 4) + 1) * H * W
+ * floats (terms capped so that the vertical sweep's output stays within 4 GiB) that the
  * library allocates on the current device the first time it is needed,
  * and keeps for reuse until bf_release_scratch().  The first such call on a
  * device must therefore not happen during stream capture.
@@ -155,17 +155,28 @@ bf_status bf_forward_stack(const bf_plan *plan, const void *in, bf_dtype dt, flo
 
 /*
  * Tile-shape autotuner for bf_forward (not in the paper).  Runs each tile
- * shape the fused kernel has for this plan's spatial support (32 x 64 tiles
- * always; 32 x 96 tiles with wider row segments for small radii) `reps`
- * times on the given buffers (out is overwritten), and keeps the fastest for
- * later bf_forward calls with the same kind, radius, degree, H, W and C
+ * shape the fused kernel has for this plan's spatial support `reps` times on
+ * the given buffers (out is overwritten), and keeps the fastest for later
+ * bf_forward calls with the same kind, radius, degree, H, W and C
  * (process-wide, thread-safe).  Synchronises `stream`.  *shape receives the
  * choice (-1 when the support runs on the streaming kernels, which have no
- * shape to choose), *ms its time per call; either may be NULL.
+ * shape to choose), *ms its time per call; either may be NULL.  Shape ids:
+ *   0  32 x 64 tiles (every support)
+ *   1  32 x 96 tiles, wider row segments (box r <= 4, Gaussian R <= 9)
+ *   2  64 x 64 tiles, one 512-thread block per SM (box 3 <= r <= 8,
+ *      Gaussian R >= 9)
  */
 bf_status bf_forward_tune(const bf_plan *plan, const void *in, bf_dtype dt, float *out, int H,
                           int W, int C, long long row_stride_elems, int reps,
                           cudaStream_t stream, int *shape, float *ms);
+
+/*
+ * Pins the tile shape (id as above) that later bf_forward calls use for this
+ * plan's kind, radius and degree at size H x W x C, as bf_forward_tune would
+ * after timing.  Host only.  Errors: BF_EINVAL for a shape the plan's support
+ * does not have (or a support without tile shapes) or bad sizes.
+ */
+bf_status bf_forward_set_shape(const bf_plan *plan, int H, int W, int C, int shape);
 
 /* Frees the scratch buffers bf_forward allocated (all devices).  Call only
  * when no work that uses them is in flight. */

@@ -55,6 +55,7 @@ def _declare(lib):
                                       c_void_p, c_int, c_int, c_int, c_void_p, c_size_t, c_void_p]),
         "bf_forward_tune": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_int, c_int, c_ll,
                                     c_int, c_void_p, _ip, ctypes.POINTER(ctypes.c_float)]),
+        "bf_forward_set_shape": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
         "bf_forward_unfused_workspace": (c_size_t, [c_int, c_int]),
         "bf_forward_unfused": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p,
                                        c_size_t, c_void_p]),

@@ -26,9 +26,9 @@ bf_status cuda_check(cudaError_t e, const char *what) {
 }
 
 int gauss_tile_radius(int R);
-int gauss_tile_shapes(int R);
+int gauss_tile_shape_ids(int R, int *ids);
 int box_tile_max_r();
-int box_tile_shapes(int r);
+int box_tile_shape_ids(int r, int *ids);
 cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape);
 cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape);
 
@@ -41,8 +41,10 @@ static TuneKey tune_key(const bf_plan *p, const BfImage &img) {
     return TuneKey(p->kind, p->R, p->N, img.H, img.W, img.C);
 }
 
-static int tile_shapes(const bf_plan *p) {
-    return p->kind == BF_SPATIAL_GAUSS_TRUNC ? gauss_tile_shapes(p->R) : box_tile_shapes(p->r_box);
+// Candidate tile-shape ids of a plan (at most 4); returns their number.
+static int tile_shapes(const bf_plan *p, int *ids) {
+    return p->kind == BF_SPATIAL_GAUSS_TRUNC ? gauss_tile_shape_ids(p->R, ids)
+                                             : box_tile_shape_ids(p->r_box, ids);
 }
 
 static cudaError_t launch_tile_shape(const bf_plan *p, const BfImage &img, cudaStream_t s,
@@ -309,6 +311,27 @@ extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const floa
 
 // ---- tile-shape autotuner ----------------------------------------------------
 
+extern "C" bf_status bf_forward_set_shape(const bf_plan *plan, int H, int W, int C, int shape) {
+    if (!plan) return fail(BF_EINVAL, "bf_forward_set_shape: NULL plan");
+    if (H < 1 || W < 1 || C < 1 || C > 4) return fail(BF_EINVAL, "bf_forward_set_shape: bad size");
+    if (!tile_supported(plan))
+        return fail(BF_EINVAL, "bf_forward_set_shape: this support runs on the streaming kernels");
+    int ids[4];
+    const int n = tile_shapes(plan, ids);
+    bool ok = false;
+    for (int i = 0; i < n; ++i) ok = ok || ids[i] == shape;
+    if (!ok) return fail(BF_EINVAL, "bf_forward_set_shape: shape " + std::to_string(shape) +
+                                         " is not available for this support");
+    BfImage img{};
+    img.H = H;
+    img.W = W;
+    img.C = C;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[tune_key(plan, img)] = shape;
+    return BF_OK;
+}
+
+
 extern "C" bf_status bf_forward_tune(const bf_plan *plan, const void *in, bf_dtype dt, float *out,
                                      int H, int W, int C, long long row_stride_elems, int reps,
                                      cudaStream_t stream, int *shape_out, float *ms_out) {
@@ -336,14 +359,16 @@ extern "C" bf_status bf_forward_tune(const bf_plan *plan, const void *in, bf_dty
         if (ms_out) *ms_out = 0.f;
         return BF_OK;
     }
-    const int n = tile_shapes(plan);
+    int ids[4];
+    const int n = tile_shapes(plan, ids);
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) return cuda_check(e, "bf_forward_tune");
     float best = 1e30f;
     int best_shape = 0;
-    for (int sh = 0; sh < n && e == cudaSuccess; ++sh) {
+    for (int si = 0; si < n && e == cudaSuccess; ++si) {
+        const int sh = ids[si];
         e = launch_tile_shape(plan, img, stream, sh);  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
         for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch_tile_shape(plan, img, stream, sh);

@@ -508,17 +508,18 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
     }
 }
 
-// Resident blocks per SM the register allocation is sized for: three for the
-// narrow tiles of the smallest boxes (whose shared memory allows three and
-// whose registers fit 80 without spilling), two otherwise.
-template <int KIND, int RAD, int TW>
+// Resident blocks per SM the register allocation is sized for: one for the
+// 512-thread blocks of the 64-row tiles, three for the 32 x 64 tiles of the
+// smallest boxes (whose shared memory allows three and whose registers fit 80
+// without spilling), two otherwise.
+template <int KIND, int RAD, int TH, int TW>
 struct TileMinBlocks {
-    static constexpr int value = (KIND == 1 && RAD <= 2 && TW == 64) ? 3 : 2;
+    static constexpr int value = TH > 32 ? 1 : (KIND == 1 && RAD <= 2 && TW == 64) ? 3 : 2;
 };
 
 template <int KIND, int RAD, int TH, int TW, int TWT>
 __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT,
-                                  TileMinBlocks<KIND, RAD, TW>::value)
+                                  TileMinBlocks<KIND, RAD, TH, TW>::value)
     bf_tile_fwd(const __grid_constant__ TileParams p) {
     extern __shared__ float4 smem4[];
     TileJob jb;

@@ -5,9 +5,17 @@ namespace bf {
 
 int box_tile_max_r() { return 8; }
 
-// Shape 0: 32 x 64 tiles, 16-pixel segments; shape 1 (r <= 4): 32 x 96
-// tiles, 24-pixel segments.
-int box_tile_shapes(int r) { return r >= 1 && r <= 4 ? 2 : 1; }
+// Tile shapes by id: 0 = 32 x 64 tiles, 16-pixel segments (two or three
+// blocks per SM); 1 (r <= 4) = 32 x 96 tiles, 24-pixel segments; 2 (r >= 3) =
+// 64 x 64 tiles, 16-pixel segments, one 512-thread block per SM (less halo
+// per output at the cost of occupancy).  Fills ids, returns their number.
+int box_tile_shape_ids(int r, int *ids) {
+    int n = 0;
+    ids[n++] = 0;
+    if (r >= 1 && r <= 4) ids[n++] = 1;
+    if (r >= 3 && r <= 8) ids[n++] = 2;
+    return n;
+}
 
 cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t s, int shape) {
     TileParams prm;
@@ -21,6 +29,17 @@ cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t
             case 2: return launch_tile<1, 2, 32, 96, 24>(prm, s);
             case 3: return launch_tile<1, 3, 32, 96, 24>(prm, s);
             case 4: return launch_tile<1, 4, 32, 96, 24>(prm, s);
+            default: break;
+        }
+    }
+    if (shape == 2) {
+        switch (pl->r_box) {
+            case 3: return launch_tile<1, 3, 64, 64, 16>(prm, s);
+            case 4: return launch_tile<1, 4, 64, 64, 16>(prm, s);
+            case 5: return launch_tile<1, 5, 64, 64, 16>(prm, s);
+            case 6: return launch_tile<1, 6, 64, 64, 16>(prm, s);
+            case 7: return launch_tile<1, 7, 64, 64, 16>(prm, s);
+            case 8: return launch_tile<1, 8, 64, 64, 16>(prm, s);
             default: break;
         }
     }

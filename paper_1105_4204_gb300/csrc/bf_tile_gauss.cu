@@ -14,12 +14,17 @@ int gauss_tile_radius(int R) {
     return -1;
 }
 
-// Shape 0: 32 x 64 tiles, 16-pixel segments; shape 1 (small radii only):
-// 32 x 96 tiles, 24-pixel segments (more phase-1 work items per block and
-// less halo, at the cost of registers).
-int gauss_tile_shapes(int R) {
+// Tile shapes by id: 0 = 32 x 64 tiles, 16-pixel segments; 1 (small radii
+// only) = 32 x 96 tiles, 24-pixel segments (more phase-1 work items per block
+// and less halo, at the cost of registers); 2 (radii >= 9) = 64 x 64 tiles,
+// one 512-thread block per SM.  Fills ids, returns their number.
+int gauss_tile_shape_ids(int R, int *ids) {
     const int Ri = gauss_tile_radius(R);
-    return Ri > 0 && Ri <= 9 ? 2 : 1;
+    int n = 0;
+    ids[n++] = 0;
+    if (Ri > 0 && Ri <= 9) ids[n++] = 1;
+    if (Ri >= 9) ids[n++] = 2;
+    return n;
 }
 
 cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape) {
@@ -36,6 +41,16 @@ cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_
             case 4: return launch_tile<0, 4, 32, 96, 24>(prm, s);
             case 6: return launch_tile<0, 6, 32, 96, 24>(prm, s);
             case 9: return launch_tile<0, 9, 32, 96, 24>(prm, s);
+            default: break;
+        }
+    }
+    if (shape == 2) {
+        switch (Ri) {
+            case 9: return launch_tile<0, 9, 64, 64, 16>(prm, s);
+            case 12: return launch_tile<0, 12, 64, 64, 16>(prm, s);
+            case 15: return launch_tile<0, 15, 64, 64, 16>(prm, s);
+            case 18: return launch_tile<0, 18, 64, 64, 16>(prm, s);
+            case 24: return launch_tile<0, 24, 64, 64, 16>(prm, s);
             default: break;
         }
     }

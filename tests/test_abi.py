@@ -143,3 +143,18 @@ def test_forward_rejects_bad_arguments_without_touching_a_gpu(bf):
     assert l.bf_forward(p.handle, fake, 0, fake, 16, 16, 5, 80, null, null) == 2  # C > 4
     assert l.bf_forward(p.handle, fake, 7, fake, 16, 16, 1, 16, null, null) == 1  # dtype
     assert l.bf_forward(None, fake, 0, fake, 16, 16, 1, 16, null, null) == 1
+
+
+def test_set_shape_accepts_only_the_supports_shapes(bf):
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    box2, box8 = bf.Plan(2.0, 20.0, kind="box"), bf.Plan(8.0, 20.0, kind="box")
+    assert l.bf_forward_set_shape(box2.handle, 64, 64, 1, 1) == 0   # 32 x 96
+    assert l.bf_forward_set_shape(box2.handle, 64, 64, 1, 2) == 1   # 64 x 64 needs r >= 3
+    assert l.bf_forward_set_shape(box8.handle, 64, 64, 1, 2) == 0
+    assert l.bf_forward_set_shape(box8.handle, 64, 64, 1, 1) == 1   # 32 x 96 needs r <= 4
+    assert l.bf_forward_set_shape(box8.handle, 64, 64, 1, 7) == 1
+    assert l.bf_forward_set_shape(box8.handle, 0, 64, 1, 0) == 1
+    big = bf.Plan(32.0, 20.0, kind="box")                          # streaming kernels
+    assert l.bf_forward_set_shape(big.handle, 64, 64, 1, 0) == 1
+    assert b"streaming" in l.bf_last_error()
