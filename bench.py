@@ -345,6 +345,7 @@ def run_ours(args):
             errs["sigma_s=%g" % SIGMA_S[i]] = float(np.abs(got - ref).max())
         extras["max_abs_err_vs_oracle"] = errs
         extras["max_abs_err_sample"] = "%d pixels (all borders + 1024 seeded)" % len(idx)
+    if rank == 0 and not args.no_extras:
         # ---- unfused baseline on the same workload (fused vs per-term materialised)
         if ws is None:
             ws = torch.empty(_l().bf_forward_unfused_workspace(H, W), dtype=torch.uint8,
@@ -362,12 +363,14 @@ def run_ours(args):
             torch.cuda.synchronize()
             uf_ms.append(a0.elapsed_time(a1) / 3)
         extras["unfused_ms_per_call"] = {"sigma_s=%g" % s: m for s, m in zip(SIGMA_S, uf_ms)}
+    if rank == 0:
         extras["fused_ms_per_call"] = {"sigma_s=%g" % s: float(m) for s, m in zip(SIGMA_S, call_ms)}
         extras["wall_s_timed_region"] = t_wall
 
     if rank == 0 and not args.no_extras:
         extras.update(measure_fwd_bwd(bf, torch, dev, stream))
         extras.update(measure_batch(bf, torch, dev, stream))
+        extras.update(measure_configs(bf, torch, dev, stream))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -436,6 +439,49 @@ def measure_fwd_bwd(bf, torch, dev, stream):
             "fwd_instr_per_px": gauss_instr_per_px(nz, bool(np.any(w == 0)), 12)}
 
 
+def measure_configs(bf, torch, dev, stream):
+    """Configs 1 and 3: the 256^2 Gaussian forward (N = 30, full-image error
+    against the oracle) and the 4096^2 x 3 u8 HWC Gaussian forward at
+    sigma_r = 10 (N = 264) and 50 (N = 11), errors on seeded pixels against the
+    raised-cosine oracle and against the Gaussian range kernel it
+    approximates."""
+    import oracle
+    import synth
+    res = {}
+    img1 = synth.rectangles(256, 256, n_rect=12, noise=10.0, seed=0)
+    p1 = bf.Plan(3.0, 30.0, 255.0, kind="gauss")
+    t1 = torch.from_numpy(img1).to(dev)
+    o1 = torch.empty_like(t1)
+    bf.tune(p1, t1, reps=3)
+    ms1 = _time(lambda: bf.forward(p1, t1, out=o1), torch, stream, 20)
+    ref1 = oracle.bf_brute(img1.astype(np.float64), sigma_s=3.0, sigma_r=30.0, kind="gauss")
+    res["c1_256_gauss_r9_n30"] = {"ms": ms1, "mpx_s": 256 * 256 / (ms1 * 1e-3) / 1e6,
+                                  "max_abs_err_full_image": float(np.abs(o1.cpu().numpy() - ref1).max())}
+    img3 = synth.rect_disk_u8(4096, 4096, 3, seed=0)
+    t3 = torch.from_numpy(img3).to(dev)
+    o3 = torch.empty(t3.shape, dtype=torch.float32, device=dev)
+    idx = synth.sample_indices(4096, 4096, 512, seed=11)
+    for sr in (10.0, 50.0):
+        p3 = bf.Plan(6.0, sr, 255.0, kind="gauss")
+        bf.tune(p3, t3, reps=2)
+        ms3 = _time(lambda: bf.forward(p3, t3, out=o3), torch, stream, 3)
+        out = o3.cpu().numpy()
+        w1 = oracle.spatial_w1("gauss", 6.0)
+        err = err_g = 0.0
+        for c in range(3):
+            ch = img3[..., c].astype(np.float64)
+            got = out[..., c].ravel()[idx]
+            err = max(err, float(np.abs(got - oracle.bf_brute_at(ch, idx, sigma_r=sr, w1=w1,
+                                                                 N=p3.N)).max()))
+            err_g = max(err_g, float(np.abs(got - oracle.bf_brute_at(
+                ch, idx, sigma_r=sr, w1=w1, range_mode="gaussian")).max()))
+        res["c3_4096x3_u8_gauss_r18_sr%g_n%d" % (sr, p3.N)] = {
+            "ms": ms3, "mpx_s": 3 * 4096 * 4096 / (ms3 * 1e-3) / 1e6,
+            "max_abs_err_vs_oracle": err, "max_abs_err_vs_gaussian_range_kernel": err_g,
+            "error_sample": "%d px x 3 channels (borders + 512 seeded)" % len(idx)}
+    return {"configs": res}
+
+
 def measure_batch(bf, torch, dev, stream):
     """Batched workload: 64 images, W ~ U[128,1920], H ~ U[128,1080], box
     sigma_s ~ U[2,16], sigma_r ~ U[15,60]; one persistent launch replayed from
@@ -465,6 +511,20 @@ def measure_batch(bf, torch, dev, stream):
             "batch_ms": t_batch, "batch_loop_ms": t_loop, "batch_tuned": tuned}
 
 
+def run_extras_only(which):
+    import torch
+
+    import paper_1105_4204_gb300 as bf
+    from paper_1105_4204_gb300 import build as _build
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    fn = {"fwd_bwd": measure_fwd_bwd, "batch": measure_batch, "configs": measure_configs}[which]
+    print(json.dumps({"extras_only": which, **fn(bf, torch, dev, stream)}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,8 +532,25 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the unfused baseline and the other workloads")
+    ap.add_argument("--sigma-s", default=None,
+                    help="comma-separated subset of the workload's sigma_s values (profiling runs)")
+    ap.add_argument("--extras-only", choices=["fwd_bwd", "batch", "configs"], default=None,
+                    help="time only that extra workload and print its figures (profiling runs; "
+                         "not the benchmark line)")
     args = ap.parse_args()
+    if args.extras_only:
+        return run_extras_only(args.extras_only)
+    if args.sigma_s:
+        global SIGMA_S, WORKLOAD
+        sub = [float(x) for x in args.sigma_s.split(",")]
+        bad = [x for x in sub if x not in SIGMA_S]
+        if bad:
+            ap.error("--sigma-s takes values from %s" % SIGMA_S)
+        SIGMA_S = sub
+        WORKLOAD = WORKLOAD.replace("3 forwards per step", "%d forward(s) per step, sigma_s in %s only"
+                                    % (len(sub), sub))
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
