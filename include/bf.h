@@ -86,6 +86,30 @@ typedef struct bf_plan bf_plan;
 bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_r, double T,
                          bf_spatial_kind kind, const bf_plan_opts *opts);
 
+/*
+ * A plan for a general trigonometric range kernel (Section 2.2, eq. (kernel)
+ * in its real form):
+ *     phi(s) = a[0] + a[1] cos(gamma s) + ... + a[N] cos(N gamma s),  N = n_coef - 1,
+ * of which the raised cosine of bf_plan_create is one instance.  Everything
+ * else -- spatial kernel, tile and streaming kernels, stacks, batches, the
+ * backward pass for dL/df -- is shared with raised-cosine plans.
+ *   sigma_s, kind, opts : as in bf_plan_create (opts->N_override must be 0)
+ *   gamma               : base angular frequency in radians per gray level, > 0
+ *   a                   : host array of n_coef real coefficients (copied)
+ *   n_coef              : 1 <= n_coef <= 1025
+ * Terms whose FP32 weight is 0 are dropped (they add exactly 0).  The caller
+ * chooses a kernel that is positive on the range of differences the image
+ * has (Section 2.1's conditions on a range kernel); otherwise the normaliser
+ * Q can vanish.  bf_plan_info reports N as the highest n with a[n] != 0 in
+ * FP32.  bf_backward and its variants reject grad_sigma_r for such a plan
+ * (BF_EINVAL): it has no sigma_r.
+ * Errors: BF_EINVAL for NULL pointers, gamma or sigma_s not finite and > 0,
+ *         non-finite coefficients, all coefficients 0, or N_override set;
+ *         BF_EUNSUPPORTED for n_coef > 1025 or a support beyond the kernels.
+ */
+bf_status bf_plan_create_cosine(bf_plan **out, double sigma_s, double gamma, const double *a,
+                                int n_coef, bf_spatial_kind kind, const bf_plan_opts *opts);
+
 void bf_plan_destroy(bf_plan *plan);
 
 /*

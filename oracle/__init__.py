@@ -17,6 +17,10 @@ The arithmetic lives in ``bf_oracle.c`` (plain C, double precision, OpenMP):
 * ``bf_grad`` -- exact gradient of ``sum(u * out)`` w.r.t. the image and
   sigma_r (N fixed), by the chain rule on eq. (BF).
 * ``fd_grad_f`` / ``loss`` -- central finite differences of the brute force.
+* ``bf_brute_cos`` / ``bf_brute_cos_at`` / ``bf_grad_cos`` / ``fd_grad_f_cos``
+  / ``phi_cos`` -- the same for a general trigonometric range kernel of
+  Section 2.2, ``phi(s) = a_0 + a_1 cos(gamma s) + ... + a_N cos(N gamma s)``,
+  evaluated term by term.
 
 This module only marshals numpy arrays into that library.
 """
@@ -91,6 +95,23 @@ def _load():
         lib.or_bf_loss.restype = ctypes.c_double
         lib.or_bf_loss.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_double, ctypes.c_int]
+        lib.or_bf_brute_cos.restype = None
+        lib.or_bf_brute_cos.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
+                                        ctypes.c_double, _dp, ctypes.c_int, _dp, _dp]
+        lib.or_bf_brute_cos_at.restype = None
+        lib.or_bf_brute_cos_at.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
+                                           ctypes.c_double, _dp, ctypes.c_int, _llp,
+                                           ctypes.c_longlong, _dp, _dp]
+        lib.or_bf_grad_cos.restype = None
+        lib.or_bf_grad_cos.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int,
+                                       ctypes.c_double, _dp, ctypes.c_int, _dp]
+        lib.or_bf_fd_grad_f_cos.restype = None
+        lib.or_bf_fd_grad_f_cos.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp,
+                                            ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int,
+                                            _llp, ctypes.c_longlong, ctypes.c_double, _dp]
+        lib.or_phi_cos_table.restype = None
+        lib.or_phi_cos_table.argtypes = [ctypes.c_double, _dp, ctypes.c_int, _dp,
+                                         ctypes.c_longlong, _dp]
         lib.or_phi_table.restype = None
         lib.or_phi_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
                                      ctypes.c_longlong, _dp]
@@ -281,4 +302,90 @@ def phi(s, sigma_r, N=None, T=255.0, range_mode="raised_cosine"):
     out = np.empty_like(s)
     lib.or_phi_table(_range_mode(range_mode), float(sigma_r), int(N), _ptr(s), len(s),
                      _ptr(out))
+    return out
+
+
+# ---- general trigonometric range kernel (Section 2.2) ----------------------
+
+def _cos_setup(sigma_s, kind, radius, passes, w1, coefs):
+    if w1 is None:
+        w1 = spatial_w1(kind, sigma_s, radius, passes)
+    w1 = _f64(w1)
+    a = _f64(coefs).ravel()
+    if len(a) < 1:
+        raise ValueError("at least one coefficient")
+    return w1, (len(w1) - 1) // 2, a
+
+
+def bf_brute_cos(f, gamma, coefs, sigma_s=3.0, kind="gauss", radius=0, passes=3, w1=None,
+                 return_q=False):
+    """Brute-force FP64 bilateral filter, eq. (BF), with the range kernel
+    phi(s) = sum_n coefs[n] cos(n gamma s); f is H x W or H x W x C."""
+    lib = _load()
+    w1, R, a = _cos_setup(sigma_s, kind, radius, passes, w1, coefs)
+    chans, multi = _channels(f)
+    outs, qs = [], []
+    for ch in chans:
+        x = _f64(ch)
+        H, W = x.shape
+        o = np.empty((H, W), dtype=np.float64)
+        q = np.empty((H, W), dtype=np.float64)
+        lib.or_bf_brute_cos(_ptr(x), H, W, _ptr(w1), R, float(gamma), _ptr(a), len(a),
+                            _ptr(o), _ptr(q))
+        outs.append(o)
+        qs.append(q)
+    out = np.stack(outs, axis=2) if multi else outs[0]
+    q = np.stack(qs, axis=2) if multi else qs[0]
+    return (out, q) if return_q else out
+
+
+def bf_brute_cos_at(f, idx, gamma, coefs, sigma_s=3.0, kind="gauss", radius=0, passes=3,
+                    w1=None):
+    """bf_brute_cos at flat pixel indices ``idx`` of a single-channel image."""
+    lib = _load()
+    w1, R, a = _cos_setup(sigma_s, kind, radius, passes, w1, coefs)
+    x = _f64(f)
+    H, W = x.shape
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    o = np.empty(len(idx), dtype=np.float64)
+    lib.or_bf_brute_cos_at(_ptr(x), H, W, _ptr(w1), R, float(gamma), _ptr(a), len(a),
+                           idx.ctypes.data_as(_llp), len(idx), _ptr(o), None)
+    return o
+
+
+def bf_grad_cos(f, u, gamma, coefs, sigma_s=4.0, kind="gauss", radius=0, passes=3, w1=None):
+    """Exact FP64 gradient of sum(u * out) w.r.t. f for the cosine-polynomial kernel."""
+    lib = _load()
+    w1, R, a = _cos_setup(sigma_s, kind, radius, passes, w1, coefs)
+    x = _f64(f)
+    uu = _f64(u)
+    H, W = x.shape
+    g = np.empty((H, W), dtype=np.float64)
+    lib.or_bf_grad_cos(_ptr(x), _ptr(uu), H, W, _ptr(w1), R, float(gamma), _ptr(a), len(a),
+                       _ptr(g))
+    return g
+
+
+def fd_grad_f_cos(f, u, idx, gamma, coefs, h=1e-3, sigma_s=4.0, kind="gauss", radius=0,
+                  passes=3, w1=None):
+    """Central finite differences of sum(u * out) for the cosine-polynomial kernel."""
+    lib = _load()
+    w1, R, a = _cos_setup(sigma_s, kind, radius, passes, w1, coefs)
+    x = _f64(f)
+    uu = _f64(u)
+    H, W = x.shape
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    out = np.empty(len(idx), dtype=np.float64)
+    lib.or_bf_fd_grad_f_cos(_ptr(x), _ptr(uu), H, W, _ptr(w1), R, float(gamma), _ptr(a),
+                            len(a), idx.ctypes.data_as(_llp), len(idx), float(h), _ptr(out))
+    return out
+
+
+def phi_cos(s, gamma, coefs):
+    """The cosine polynomial sum_n coefs[n] cos(n gamma s) at the points ``s``."""
+    lib = _load()
+    a = _f64(coefs).ravel()
+    s = _f64(s).ravel()
+    out = np.empty_like(s)
+    lib.or_phi_cos_table(float(gamma), _ptr(a), len(a), _ptr(s), len(s), _ptr(out))
     return out

@@ -20,7 +20,11 @@
  *                        every input pixel and to sigma_r (not in the paper;
  *                        the chain rule applied to the definition);
  *   - or_bf_fd_grad_f  : central finite differences of or_bf_brute for the
- *                        same gradient.
+ *                        same gradient;
+ *   - or_bf_*_cos      : the same filter, gradient and differences for a
+ *                        general trigonometric range kernel of Section 2.2,
+ *                        phi(s) = a_0 + a_1 cos(gamma s) + ... + a_N cos(N gamma s),
+ *                        evaluated term by term as written.
  *
  * Readings of the paper used here (each one also listed in the design notes):
  *   - Degree rule (Algorithm 1 step 2, Table 1 last row):
@@ -127,8 +131,13 @@ int or_spatial_w1(int kind, double sigma_s, int radius_override, int passes,
 }
 
 /* Range kernel and its derivatives.  mode 0: raised cosine of degree N with
- * k = 1/(sigma_r sqrt N); mode 1: Gaussian of standard deviation sigma_r. */
-typedef struct { int mode; int N; double k; double sigma_r; } or_range;
+ * k = 1/(sigma_r sqrt N); mode 1: Gaussian of standard deviation sigma_r;
+ * mode 2: the cosine polynomial sum_{n=0..N} a[n] cos(n gamma s) of
+ * Section 2.2 (a has N+1 entries). */
+typedef struct {
+    int mode; int N; double k; double sigma_r;
+    const double *a; double gamma;
+} or_range;
 
 static or_range or_make_range(int mode, double sigma_r, int N)
 {
@@ -137,12 +146,31 @@ static or_range or_make_range(int mode, double sigma_r, int N)
     r.N = N < 1 ? 1 : N;
     r.sigma_r = sigma_r;
     r.k = 1.0 / (sigma_r * sqrt((double)r.N));
+    r.a = NULL;
+    r.gamma = 0.0;
+    return r;
+}
+
+static or_range or_make_cos_range(double gamma, const double *a, int n_coef)
+{
+    or_range r;
+    r.mode = 2;
+    r.N = n_coef - 1;
+    r.sigma_r = 0.0;
+    r.k = 0.0;
+    r.a = a;
+    r.gamma = gamma;
     return r;
 }
 
 static double or_phi(const or_range *r, double s)
 {
     if (r->mode == 1) return exp(-s * s / (2.0 * r->sigma_r * r->sigma_r));
+    if (r->mode == 2) {
+        double v = 0.0;
+        for (int n = 0; n <= r->N; n++) v += r->a[n] * cos((double)n * r->gamma * s);
+        return v;
+    }
     return pow(cos(r->k * s), r->N);
 }
 
@@ -150,6 +178,12 @@ static double or_phi(const or_range *r, double s)
 static double or_dphi(const or_range *r, double s)
 {
     if (r->mode == 1) return -s / (r->sigma_r * r->sigma_r) * or_phi(r, s);
+    if (r->mode == 2) {
+        double v = 0.0;
+        for (int n = 1; n <= r->N; n++)
+            v -= r->a[n] * (double)n * r->gamma * sin((double)n * r->gamma * s);
+        return v;
+    }
     double c = cos(r->k * s);
     double cn1 = r->N == 1 ? 1.0 : pow(c, r->N - 1);
     return -(double)r->N * r->k * cn1 * sin(r->k * s);
@@ -182,20 +216,40 @@ static void or_pq_at(const double *f, int H, int W, const double *w1, int R,
     *Q = q;
 }
 
+static void or_brute_rg(const double *f, int H, int W, const double *w1, int R,
+                        const or_range *rg, double *out, double *q_out)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < H; i++) {
+        for (int j = 0; j < W; j++) {
+            double P, Q;
+            or_pq_at(f, H, W, w1, R, rg, i, j, &P, &Q);
+            out[(size_t)i * W + j] = P / Q;
+            if (q_out) q_out[(size_t)i * W + j] = Q;
+        }
+    }
+}
+
+static void or_brute_at_rg(const double *f, int H, int W, const double *w1, int R,
+                           const or_range *rg, const long long *idx, long long n_idx,
+                           double *out, double *q_out)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long t = 0; t < n_idx; t++) {
+        int i = (int)(idx[t] / W), j = (int)(idx[t] % W);
+        double P, Q;
+        or_pq_at(f, H, W, w1, R, rg, i, j, &P, &Q);
+        out[t] = P / Q;
+        if (q_out) q_out[t] = Q;
+    }
+}
+
 /* Brute-force filter of a whole single-channel image.  q_out may be NULL. */
 void or_bf_brute(const double *f, int H, int W, const double *w1, int R,
                  int mode, double sigma_r, int N, double *out, double *q_out)
 {
     or_range rg = or_make_range(mode, sigma_r, N);
-#pragma omp parallel for schedule(dynamic, 4)
-    for (int i = 0; i < H; i++) {
-        for (int j = 0; j < W; j++) {
-            double P, Q;
-            or_pq_at(f, H, W, w1, R, &rg, i, j, &P, &Q);
-            out[(size_t)i * W + j] = P / Q;
-            if (q_out) q_out[(size_t)i * W + j] = Q;
-        }
-    }
+    or_brute_rg(f, H, W, w1, R, &rg, out, q_out);
 }
 
 /* Brute-force filter at a list of flat pixel indices only. */
@@ -204,14 +258,24 @@ void or_bf_brute_at(const double *f, int H, int W, const double *w1, int R,
                     long long n_idx, double *out, double *q_out)
 {
     or_range rg = or_make_range(mode, sigma_r, N);
-#pragma omp parallel for schedule(dynamic, 16)
-    for (long long t = 0; t < n_idx; t++) {
-        int i = (int)(idx[t] / W), j = (int)(idx[t] % W);
-        double P, Q;
-        or_pq_at(f, H, W, w1, R, &rg, i, j, &P, &Q);
-        out[t] = P / Q;
-        if (q_out) q_out[t] = Q;
-    }
+    or_brute_at_rg(f, H, W, w1, R, &rg, idx, n_idx, out, q_out);
+}
+
+/* The same two with the cosine polynomial of Section 2.2,
+ * phi(s) = sum_{n=0..n_coef-1} a[n] cos(n gamma s). */
+void or_bf_brute_cos(const double *f, int H, int W, const double *w1, int R,
+                     double gamma, const double *a, int n_coef, double *out, double *q_out)
+{
+    or_range rg = or_make_cos_range(gamma, a, n_coef);
+    or_brute_rg(f, H, W, w1, R, &rg, out, q_out);
+}
+
+void or_bf_brute_cos_at(const double *f, int H, int W, const double *w1, int R,
+                        double gamma, const double *a, int n_coef, const long long *idx,
+                        long long n_idx, double *out, double *q_out)
+{
+    or_range rg = or_make_cos_range(gamma, a, n_coef);
+    or_brute_at_rg(f, H, W, w1, R, &rg, idx, n_idx, out, q_out);
 }
 
 /* Separable filtering of a complex image with clamp-to-edge extension:
@@ -295,11 +359,10 @@ double or_bf_trig(const double *f, int H, int W, const double *w1, int R,
  * where each neighbour z of x contributes through its clamped pixel
  * clamp(z) (value and range-kernel argument) and through x itself (the
  * argument f(z) - f(x)). */
-void or_bf_grad(const double *f, const double *u, int H, int W, const double *w1,
-                int R, int mode, double sigma_r, int N, double *grad_f,
-                double *grad_sigma_r)
+static void or_grad_rg(const double *f, const double *u, int H, int W, const double *w1,
+                       int R, const or_range *rgp, double *grad_f, double *grad_sigma_r)
 {
-    or_range rg = or_make_range(mode, sigma_r, N);
+    const or_range rg = *rgp;
     size_t n = (size_t)H * W;
     int nt = or_num_threads();
     double *buf = (double *)calloc(n * (size_t)nt, sizeof(double));
@@ -331,7 +394,7 @@ void or_bf_grad(const double *f, const double *u, int H, int W, const double *w1
                         double dph = or_dphi(&rg, s);
                         g[(size_t)zi * W + zj] += alpha * wt * (ph + dph * (v - o));
                         g[(size_t)i * W + j] -= alpha * wt * dph * (v - o);
-                        gsl += alpha * wt * or_dphi_dsigma(&rg, s) * (v - o);
+                        if (grad_sigma_r) gsl += alpha * wt * or_dphi_dsigma(&rg, s) * (v - o);
                     }
                 }
             }
@@ -350,15 +413,31 @@ void or_bf_grad(const double *f, const double *u, int H, int W, const double *w1
     free(gs);
 }
 
+void or_bf_grad(const double *f, const double *u, int H, int W, const double *w1,
+                int R, int mode, double sigma_r, int N, double *grad_f,
+                double *grad_sigma_r)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+    or_grad_rg(f, u, H, W, w1, R, &rg, grad_f, grad_sigma_r);
+}
+
+/* Image gradient for the cosine polynomial of Section 2.2 (no sigma_r). */
+void or_bf_grad_cos(const double *f, const double *u, int H, int W, const double *w1,
+                    int R, double gamma, const double *a, int n_coef, double *grad_f)
+{
+    or_range rg = or_make_cos_range(gamma, a, n_coef);
+    or_grad_rg(f, u, H, W, w1, R, &rg, grad_f, NULL);
+}
+
 /* Central finite differences of L = sum_x u(x) out(x) with respect to the
  * listed pixels.  Only outputs within R of the perturbed pixel change, so only
  * those are recomputed (with clamping, a neighbour that maps onto p lies
  * within R of every output that sees it). */
-void or_bf_fd_grad_f(const double *f, const double *u, int H, int W,
-                     const double *w1, int R, int mode, double sigma_r, int N,
+static void or_fd_rg(const double *f, const double *u, int H, int W,
+                     const double *w1, int R, const or_range *rgp,
                      const long long *idx, long long n_idx, double h, double *out)
 {
-    or_range rg = or_make_range(mode, sigma_r, N);
+    const or_range rg = *rgp;
     size_t n = (size_t)H * W;
 #pragma omp parallel
     {
@@ -389,6 +468,22 @@ void or_bf_fd_grad_f(const double *f, const double *u, int H, int W,
     }
 }
 
+void or_bf_fd_grad_f(const double *f, const double *u, int H, int W,
+                     const double *w1, int R, int mode, double sigma_r, int N,
+                     const long long *idx, long long n_idx, double h, double *out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+    or_fd_rg(f, u, H, W, w1, R, &rg, idx, n_idx, h, out);
+}
+
+void or_bf_fd_grad_f_cos(const double *f, const double *u, int H, int W,
+                         const double *w1, int R, double gamma, const double *a, int n_coef,
+                         const long long *idx, long long n_idx, double h, double *out)
+{
+    or_range rg = or_make_cos_range(gamma, a, n_coef);
+    or_fd_rg(f, u, H, W, w1, R, &rg, idx, n_idx, h, out);
+}
+
 /* L = sum_x u(x) out(x) for the whole image (used for sigma_r differences). */
 double or_bf_loss(const double *f, const double *u, int H, int W, const double *w1,
                   int R, int mode, double sigma_r, int N)
@@ -403,6 +498,14 @@ double or_bf_loss(const double *f, const double *u, int H, int W, const double *
             total += u[(size_t)i * W + j] * (P / Q);
         }
     return total;
+}
+
+/* The cosine polynomial itself. */
+void or_phi_cos_table(double gamma, const double *a, int n_coef, const double *s, long long n,
+                      double *out)
+{
+    or_range rg = or_make_cos_range(gamma, a, n_coef);
+    for (long long t = 0; t < n; t++) out[t] = or_phi(&rg, s[t]);
 }
 
 /* The range kernel itself, for tests of the convergence claim. */

@@ -42,6 +42,8 @@ def _declare(lib):
     sig = {
         "bf_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_double, c_double, c_double, c_int,
                                    ctypes.POINTER(PlanOpts)]),
+        "bf_plan_create_cosine": (c_int, [ctypes.POINTER(c_void_p), c_double, c_double, _dp,
+                                          c_int, c_int, ctypes.POINTER(PlanOpts)]),
         "bf_plan_destroy": (None, [c_void_p]),
         "bf_plan_info": (c_int, [c_void_p, _ip, _ip, _ip, _dp]),
         "bf_plan_terms": (c_int, [c_void_p, _dp, _dp, c_int, _ip]),

@@ -39,6 +39,29 @@ class Plan:
         check(self._lib.bf_plan_create(ctypes.byref(self._h), float(sigma_s), float(sigma_r),
                                        float(T), _kind(kind), ctypes.byref(opts)))
         self.sigma_s, self.sigma_r, self.T, self.kind = float(sigma_s), float(sigma_r), float(T), kind
+        self._info()
+
+    @classmethod
+    def cosine(cls, sigma_s: float, gamma: float, coefs, kind="gauss", radius: int = 0,
+               passes: int = 0) -> "Plan":
+        """Plan for the general trigonometric range kernel of Section 2.2,
+        phi(s) = sum_n coefs[n] cos(n gamma s) (gamma in radians per gray
+        level).  The spatial kernel is as for the raised cosine."""
+        self = cls.__new__(cls)
+        self._lib = lib()
+        self._h = ctypes.c_void_p()
+        a = np.ascontiguousarray(np.asarray(coefs, dtype=np.float64).ravel())
+        opts = PlanOpts(0, int(radius), int(passes))
+        check(self._lib.bf_plan_create_cosine(
+            ctypes.byref(self._h), float(sigma_s), float(gamma),
+            a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(a), _kind(kind),
+            ctypes.byref(opts)))
+        self.sigma_s, self.sigma_r, self.T, self.kind = float(sigma_s), None, None, kind
+        self.gamma, self.coefs = float(gamma), a.copy()
+        self._info()
+        return self
+
+    def _info(self):
         n, nf, rad = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         sig = ctypes.c_double()
         check(self._lib.bf_plan_info(self._h, ctypes.byref(n), ctypes.byref(nf),

@@ -268,6 +268,9 @@ extern "C" bf_status bf_backward_stack(const bf_plan *plan, const float *f, cons
     if (!bwd_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward_stack: no kernel for this spatial support "
                                      "(Gaussian R <= 24 or box r <= 8)");
+    if (grad_sigma_r && plan->cosine)
+        return fail(BF_EINVAL, "bf_backward_stack: a cosine-polynomial plan has no sigma_r; "
+                               "pass grad_sigma_r = NULL");
     const size_t need = bwd_blocks(H, W) * (size_t)count * sizeof(double);
     if (grad_sigma_r) {
         if (!workspace) return fail(BF_EINVAL, "bf_backward_stack: workspace is NULL");
@@ -295,6 +298,9 @@ extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const floa
     if (!bwd_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward: no kernel for this spatial support "
                                      "(Gaussian R <= 24 or box r <= 8)");
+    if (grad_sigma_r && plan->cosine)
+        return fail(BF_EINVAL, "bf_backward: a cosine-polynomial plan has no sigma_r; "
+                               "pass grad_sigma_r = NULL");
     if (grad_sigma_r) {
         if (!workspace) return fail(BF_EINVAL, "bf_backward: workspace is NULL");
         if (workspace_bytes < bwd_blocks(H, W) * sizeof(double))

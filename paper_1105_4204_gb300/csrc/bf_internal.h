@@ -31,6 +31,10 @@ struct bf_plan {
     // Normaliser scale: the kernels filter the box unnormalised (integer
     // weights) since the ratio P/Q does not depend on a common scale.
     float q_scale = 1.f;
+    // A general cosine polynomial of Section 2.2 (bf_plan_create_cosine):
+    // phi(s) = sum_n a_n cos(n gamma s); sigma_r and T are then 0.
+    bool cosine = false;
+    double gamma = 0.0;
 };
 
 // Per-launch term table, passed by value as a kernel parameter (constant bank).

@@ -54,6 +54,9 @@ extern "C" bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, co
     if (!bwd_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward_noalloc: no kernel for this spatial support "
                                      "(Gaussian R <= 24 or box r <= 8)");
+    if (grad_sigma_r && plan->cosine)
+        return fail(BF_EINVAL, "bf_backward_noalloc: a cosine-polynomial plan has no sigma_r; "
+                               "pass grad_sigma_r = NULL");
     double *partials = nullptr;
     if (grad_sigma_r) {
         const size_t need = bwd_blocks(H, W);

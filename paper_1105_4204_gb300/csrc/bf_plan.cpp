@@ -12,9 +12,11 @@
 // m = N - 2n > 0; for even N the middle term n = N/2 is the constant
 // 2^-N C(N, N/2) (Section 2.3).  A term whose FP32 weight rounds to exactly 0
 // contributes exactly 0 in the kernels' FP32 arithmetic and is dropped.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "bf_internal.h"
 
@@ -49,6 +51,83 @@ std::vector<double> binomial_weights(int N) {
 
 }  // namespace
 
+// Spatial kernel of a plan (the 1-D taps w1, support radius, achieved sigma
+// and the box normaliser).  On failure nothing needs freeing; the caller
+// deletes the plan.
+static bf_status set_spatial(bf_plan *p, double sigma_s, bf_spatial_kind kind,
+                             const bf_plan_opts &o, const std::string &who) {
+    if (kind == BF_SPATIAL_GAUSS_TRUNC) {
+        int R = o.radius_override > 0 ? o.radius_override : (int)std::ceil(3.0 * sigma_s);
+        if (R > BF_MAX_TAPS_R) {
+            return bf::fail(BF_EUNSUPPORTED, who + ": Gaussian support radius " +
+                                                 std::to_string(R) + " exceeds " +
+                                                 std::to_string(BF_MAX_TAPS_R));
+        }
+        p->R = R;
+        p->w1.resize(2 * R + 1);
+        double s = 0.0;
+        for (int i = -R; i <= R; ++i) {
+            double v = std::exp(-(double)i * i / (2.0 * sigma_s * sigma_s));
+            p->w1[i + R] = v;
+            s += v;
+        }
+        double var = 0.0;
+        for (int i = -R; i <= R; ++i) {
+            p->w1[i + R] /= s;
+            var += p->w1[i + R] * (double)i * i;
+        }
+        p->achieved_sigma = std::sqrt(var);
+        p->q_scale = 1.f;
+    } else {
+        int passes = o.box_passes > 0 ? o.box_passes : 3;
+        if (passes != 3) {
+            return bf::fail(BF_EUNSUPPORTED, who + ": only 3 box passes are implemented");
+        }
+        int r = o.radius_override;
+        if (r <= 0) {
+            // passes boxes of width 2r+1 have variance passes ((2r+1)^2 - 1) / 12
+            double L = std::sqrt(12.0 * sigma_s * sigma_s / passes + 1.0);
+            r = (int)std::floor((L - 1.0) / 2.0 + 0.5);
+            if (r < 1) r = 1;
+        }
+        if (r > 64) {
+            return bf::fail(BF_EUNSUPPORTED, who + ": box half-width " +
+                                                 std::to_string(r) + " exceeds 64");
+        }
+        p->passes = passes;
+        p->r_box = r;
+        p->R = passes * r;
+        // taps: convolution of `passes` boxes, exact integer counts / (2r+1)^passes
+        std::vector<double> c(1, 1.0);
+        for (int k = 0; k < passes; ++k) {
+            std::vector<double> n(c.size() + 2 * r, 0.0);
+            for (size_t i = 0; i < c.size(); ++i)
+                for (int d = 0; d <= 2 * r; ++d) n[i + d] += c[i];
+            c.swap(n);
+        }
+        double denom = std::pow(2.0 * r + 1.0, passes);
+        p->w1.resize(c.size());
+        for (size_t i = 0; i < c.size(); ++i) p->w1[i] = c[i] / denom;
+        double L = 2.0 * r + 1.0;
+        p->achieved_sigma = std::sqrt(passes * (L * L - 1.0) / 12.0);
+        // the kernels sum the 2-D box cascade without dividing: scale = L^(-2 passes)
+        p->q_scale = (float)std::pow(L, -2.0 * passes);
+    }
+    p->w1f.assign(p->w1.begin(), p->w1.end());
+    return BF_OK;
+}
+
+// FP32 copies of the term table; BF_EUNSUPPORTED above the kernels' limit.
+static bf_status finish_terms(bf_plan *p, const std::string &who) {
+    if ((int)p->a.size() > BF_MAX_TERMS)
+        return bf::fail(BF_EUNSUPPORTED, who + ": too many terms");
+    for (size_t k = 0; k < p->a.size(); ++k) {
+        p->a32.push_back((float)p->a[k]);
+        p->turns32.push_back((float)(p->omega[k] / (2.0 * kPi)));
+    }
+    return BF_OK;
+}
+
 extern "C" bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_r, double T,
                                     bf_spatial_kind kind, const bf_plan_opts *opts) {
     if (!out) return bf::fail(BF_EINVAL, "bf_plan_create: out is NULL");
@@ -82,68 +161,13 @@ extern "C" bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_
     }
     p->N = N;
 
-    // ---- spatial kernel
-    if (kind == BF_SPATIAL_GAUSS_TRUNC) {
-        int R = o.radius_override > 0 ? o.radius_override : (int)std::ceil(3.0 * sigma_s);
-        if (R > BF_MAX_TAPS_R) {
+    {
+        const bf_status st = set_spatial(p, sigma_s, kind, o, "bf_plan_create");
+        if (st != BF_OK) {
             delete p;
-            return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: Gaussian support radius " +
-                                                 std::to_string(R) + " exceeds " +
-                                                 std::to_string(BF_MAX_TAPS_R));
+            return st;
         }
-        p->R = R;
-        p->w1.resize(2 * R + 1);
-        double s = 0.0;
-        for (int i = -R; i <= R; ++i) {
-            double v = std::exp(-(double)i * i / (2.0 * sigma_s * sigma_s));
-            p->w1[i + R] = v;
-            s += v;
-        }
-        double var = 0.0;
-        for (int i = -R; i <= R; ++i) {
-            p->w1[i + R] /= s;
-            var += p->w1[i + R] * (double)i * i;
-        }
-        p->achieved_sigma = std::sqrt(var);
-        p->q_scale = 1.f;
-    } else {
-        int passes = o.box_passes > 0 ? o.box_passes : 3;
-        if (passes != 3) {
-            delete p;
-            return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: only 3 box passes are implemented");
-        }
-        int r = o.radius_override;
-        if (r <= 0) {
-            // passes boxes of width 2r+1 have variance passes ((2r+1)^2 - 1) / 12
-            double L = std::sqrt(12.0 * sigma_s * sigma_s / passes + 1.0);
-            r = (int)std::floor((L - 1.0) / 2.0 + 0.5);
-            if (r < 1) r = 1;
-        }
-        if (r > 64) {
-            delete p;
-            return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: box half-width " +
-                                                 std::to_string(r) + " exceeds 64");
-        }
-        p->passes = passes;
-        p->r_box = r;
-        p->R = passes * r;
-        // taps: convolution of `passes` boxes, exact integer counts / (2r+1)^passes
-        std::vector<double> c(1, 1.0);
-        for (int k = 0; k < passes; ++k) {
-            std::vector<double> n(c.size() + 2 * r, 0.0);
-            for (size_t i = 0; i < c.size(); ++i)
-                for (int d = 0; d <= 2 * r; ++d) n[i + d] += c[i];
-            c.swap(n);
-        }
-        double denom = std::pow(2.0 * r + 1.0, passes);
-        p->w1.resize(c.size());
-        for (size_t i = 0; i < c.size(); ++i) p->w1[i] = c[i] / denom;
-        double L = 2.0 * r + 1.0;
-        p->achieved_sigma = std::sqrt(passes * (L * L - 1.0) / 12.0);
-        // the kernels sum the 2-D box cascade without dividing: scale = L^(-2 passes)
-        p->q_scale = (float)std::pow(L, -2.0 * passes);
     }
-    p->w1f.assign(p->w1.begin(), p->w1.end());
 
     // ---- range kernel terms (folded conjugate pairs)
     std::vector<double> bw = binomial_weights(N);
@@ -161,13 +185,87 @@ extern "C" bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_
         p->omega.push_back(0.0);
         p->has_center = true;
     }
-    if ((int)p->a.size() > BF_MAX_TERMS) {
-        delete p;
-        return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: too many terms");
+    {
+        const bf_status st = finish_terms(p, "bf_plan_create");
+        if (st != BF_OK) {
+            delete p;
+            return st;
+        }
     }
-    for (size_t k = 0; k < p->a.size(); ++k) {
-        p->a32.push_back((float)p->a[k]);
-        p->turns32.push_back((float)(p->omega[k] / (2.0 * kPi)));
+    *out = p;
+    return BF_OK;
+}
+
+extern "C" bf_status bf_plan_create_cosine(bf_plan **out, double sigma_s, double gamma,
+                                           const double *a, int n_coef, bf_spatial_kind kind,
+                                           const bf_plan_opts *opts) {
+    const std::string who = "bf_plan_create_cosine";
+    if (!out) return bf::fail(BF_EINVAL, who + ": out is NULL");
+    *out = nullptr;
+    if (!a) return bf::fail(BF_EINVAL, who + ": coefficients are NULL");
+    if (!(sigma_s > 0) || !std::isfinite(sigma_s))
+        return bf::fail(BF_EINVAL, who + ": sigma_s must be finite and > 0");
+    if (!(gamma > 0) || !std::isfinite(gamma))
+        return bf::fail(BF_EINVAL, who + ": gamma must be finite and > 0");
+    if (n_coef < 1) return bf::fail(BF_EINVAL, who + ": n_coef must be >= 1");
+    if (n_coef > BF_MAX_N + 1)
+        return bf::fail(BF_EUNSUPPORTED, who + ": degree above " + std::to_string(BF_MAX_N));
+    for (int n = 0; n < n_coef; ++n)
+        if (!std::isfinite(a[n])) return bf::fail(BF_EINVAL, who + ": non-finite coefficient");
+    if (kind != BF_SPATIAL_GAUSS_TRUNC && kind != BF_SPATIAL_BOX_ITER)
+        return bf::fail(BF_EINVAL, who + ": unknown spatial kind");
+    bf_plan_opts o{};
+    if (opts) o = *opts;
+    if (o.N_override != 0) return bf::fail(BF_EINVAL, who + ": N_override does not apply");
+    if (o.radius_override < 0 || o.box_passes < 0)
+        return bf::fail(BF_EINVAL, who + ": negative option");
+
+    bf_plan *p = new (std::nothrow) bf_plan();
+    if (!p) return bf::fail(BF_ENOMEM, who + ": out of host memory");
+    p->sigma_s = sigma_s;
+    p->sigma_r = 0.0;  // no sigma_r: the kernel is given by its coefficients
+    p->T = 0.0;
+    p->kind = (int)kind;
+    p->cosine = true;
+    p->gamma = gamma;
+    {
+        const bf_status st = set_spatial(p, sigma_s, kind, o, who);
+        if (st != BF_OK) {
+            delete p;
+            return st;
+        }
+    }
+    // Terms cos(n gamma s) with a nonzero FP32 weight, smallest |a_n| first
+    // (a zero weight adds exactly 0 in the kernels), the constant a_0 last.
+    std::vector<int> order;
+    int degree = 0;
+    for (int n = 1; n < n_coef; ++n)
+        if ((float)a[n] != 0.0f) {
+            order.push_back(n);
+            degree = n;
+        }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return std::fabs(a[x]) < std::fabs(a[y]); });
+    for (int n : order) {
+        p->a.push_back(a[n]);
+        p->omega.push_back((double)n * gamma);
+    }
+    if ((float)a[0] != 0.0f) {
+        p->a.push_back(a[0]);
+        p->omega.push_back(0.0);
+        p->has_center = true;
+    }
+    if (p->a.empty()) {
+        delete p;
+        return bf::fail(BF_EINVAL, who + ": every coefficient is 0 in FP32");
+    }
+    p->N = degree;
+    {
+        const bf_status st = finish_terms(p, who);
+        if (st != BF_OK) {
+            delete p;
+            return st;
+        }
     }
     *out = p;
     return BF_OK;

@@ -158,3 +158,45 @@ def test_set_shape_accepts_only_the_supports_shapes(bf):
     big = bf.Plan(32.0, 20.0, kind="box")                          # streaming kernels
     assert l.bf_forward_set_shape(big.handle, 64, 64, 1, 0) == 1
     assert b"streaming" in l.bf_last_error()
+
+
+def test_cosine_plan_terms_reproduce_the_polynomial(bf):
+    # Section 2.2: phi(s) = sum_n a_n cos(n gamma s); the plan's folded term table must give
+    # the same function (terms of zero FP32 weight dropped, constant last)
+    gamma = math.pi / 510
+    coefs = [1.0, 0.8, 0.0, 0.3, 1e-50, 0.1]
+    p = bf.Plan.cosine(3.0, gamma, coefs, kind="gauss")
+    assert p.N == 3 + 2 and p.n_terms == 4 and p.radius == 9
+    a, w = p.terms()
+    assert w[-1] == 0.0 and a[-1] == 1.0
+    assert list(np.abs(a[:-1])) == sorted(np.abs(a[:-1]))
+    s = np.linspace(-255, 255, 101)
+    got = sum(ak * np.cos(wk * s) for ak, wk in zip(a, w))
+    ref = sum(c * np.cos(n * gamma * s) for n, c in enumerate(coefs) if n != 4)
+    np.testing.assert_allclose(got, ref, atol=1e-15)
+    box = bf.Plan.cosine(8.0, gamma, coefs, kind="box")
+    assert box.radius == 24
+
+
+def test_cosine_plan_rejects_bad_arguments(bf):
+    from paper_1105_4204_gb300._lib import BfError
+    gamma = math.pi / 510
+    for args in [(0.0, gamma, [1.0]), (3.0, 0.0, [1.0]), (3.0, -gamma, [1.0]),
+                 (3.0, gamma, [0.0, 0.0]), (3.0, gamma, [1.0, float("nan")]),
+                 (3.0, gamma, [])]:
+        with pytest.raises(BfError) as e:
+            bf.Plan.cosine(*args)
+        assert e.value.status == 1  # BF_EINVAL
+    with pytest.raises(BfError) as e:
+        bf.Plan.cosine(3.0, gamma, np.ones(1026))
+    assert e.value.status == 2  # BF_EUNSUPPORTED
+
+
+def test_cosine_plan_backward_has_no_sigma_r(bf):
+    # dL/dsigma_r is refused before any launch: a cosine-polynomial plan has no sigma_r
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    p = bf.Plan.cosine(2.0, math.pi / 510, [1.0, 0.5])
+    fake = ctypes.c_void_p(0x1000)
+    st = l.bf_backward(p.handle, fake, fake, fake, fake, fake, fake, 16, 16, fake, 1 << 20, None)
+    assert st == 1 and b"sigma_r" in l.bf_last_error()

@@ -267,3 +267,74 @@ def test_gradient_matches_torch_autograd(oracle):
     g, gs = oracle.bf_grad(f, u, sigma_s=ss, sigma_r=sr, w1=w1)
     np.testing.assert_allclose(g, ft.grad.numpy(), atol=1e-11)
     assert gs == pytest.approx(float(srt.grad), rel=1e-10)
+
+
+# ------------------------------------- general trigonometric range kernel (Section 2.2)
+
+def _raised_cosine_as_cosine_polynomial(N, sr):
+    # cos^N(k s) = 2^-N sum_n C(N, n) cos((N - 2n) k s), k = 1 / (sr sqrt N), written as
+    # a[m] cos(m k s): a[0] = 2^-N C(N, N/2) (N even), a[m] = 2^(1-N) C(N, (N-m)/2), m ≡ N mod 2
+    a = np.zeros(N + 1)
+    for n in range(N + 1):
+        a[abs(N - 2 * n)] += math.comb(N, n) / 2.0 ** N
+    return 1.0 / (sr * math.sqrt(N)), a
+
+
+def test_cosine_kernel_hand_examples(oracle):
+    g = {}
+    for l in open(os.path.join(os.path.dirname(__file__), "golden", "cosine_kernel_examples.txt")):
+        if l.strip() and not l.startswith("#"):
+            k, v = l.split()
+            g[k] = float(v)
+    # closed forms worked by hand from eq. (BF) with phi(0) = 1, phi(100) = 1/2
+    assert g["1d_p0"] == pytest.approx(50 / 2.5, abs=5e-8)
+    assert g["2d_00"] == pytest.approx(200 / 7, abs=5e-8)
+    w1 = oracle.spatial_w1("box", 1.0, radius=1, passes=1)
+    gam, a = math.pi / 200, [0.5, 0.5]
+    out1 = oracle.bf_brute_cos(np.array([[0.0, 100.0]]), gam, a, w1=w1)
+    np.testing.assert_allclose(out1[0], [g["1d_p0"], g["1d_p1"]], atol=1e-7)
+    out2 = oracle.bf_brute_cos(np.array([[0.0, 100.0], [100.0, 0.0]]), gam, a, w1=w1)
+    np.testing.assert_allclose(out2, [[g["2d_00"], g["2d_01"]], [g["2d_10"], g["2d_11"]]],
+                               atol=1e-7)
+
+
+@pytest.mark.parametrize("N", [1, 4, 7, 30])
+def test_cosine_kernel_reproduces_raised_cosine(oracle, N):
+    # the raised cosine is one cosine polynomial: its binomial coefficients (exact integers)
+    # fed to the general kernel give the power-form brute force
+    sr = 1.001 * 2 * 255.0 / (math.pi * math.sqrt(N))
+    gam, a = _raised_cosine_as_cosine_polynomial(N, sr)
+    s = np.linspace(-255, 255, 511)
+    np.testing.assert_allclose(oracle.phi_cos(s, gam, a), oracle.phi(s, sr, N=N), atol=1e-13)
+    f = _small_image()
+    w1 = oracle.spatial_w1("gauss", 1.5)
+    np.testing.assert_allclose(oracle.bf_brute_cos(f, gam, a, w1=w1),
+                               oracle.bf_brute(f, sigma_r=sr, N=N, w1=w1), atol=1e-9)
+
+
+def test_constant_cosine_kernel_is_the_clamped_convolution(oracle):
+    # phi = a0 (any a0 > 0): eq. (BF) reduces to eq. (averaging)
+    from scipy.ndimage import convolve1d
+    f = _small_image()
+    for kind, ss in [("gauss", 2.0), ("box", 1.0)]:
+        w1 = oracle.spatial_w1(kind, ss)
+        ref = convolve1d(convolve1d(f, w1, axis=0, mode="nearest"), w1, axis=1, mode="nearest")
+        np.testing.assert_allclose(oracle.bf_brute_cos(f, 0.01, [2.5], w1=w1), ref, atol=1e-9)
+
+
+def test_cosine_kernel_gradient(oracle):
+    # exact gradient against central differences, and against the raised-cosine gradient
+    # when the coefficients are the raised cosine's
+    f = _small_image()[:12, :14].copy()
+    u = synth.upstream(f.shape, seed=5).astype(np.float64)
+    w1 = oracle.spatial_w1("gauss", 1.0)
+    gam, a = math.pi / 510, [1.0, 0.8, 0.5, 0.3, 0.1]
+    g = oracle.bf_grad_cos(f, u, gam, a, w1=w1)
+    idx = np.arange(0, f.size, 7)
+    fd = oracle.fd_grad_f_cos(f, u, idx, gam, a, h=1e-4, w1=w1)
+    np.testing.assert_allclose(g.ravel()[idx], fd, rtol=1e-5, atol=1e-7 * np.abs(fd).max())
+    N, sr = 6, 60.0
+    gam2, a2 = _raised_cosine_as_cosine_polynomial(N, sr)
+    g2 = oracle.bf_grad_cos(f, u, gam2, a2, w1=w1)
+    g3, _ = oracle.bf_grad(f, u, sigma_r=sr, N=N, w1=w1)
+    np.testing.assert_allclose(g2, g3, atol=1e-10 * np.abs(g3).max())
