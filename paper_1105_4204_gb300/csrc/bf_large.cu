@@ -50,16 +50,9 @@ namespace {
 constexpr int kVB = 4;     // lr_vert: terms per block (they share the f ring)
 constexpr int kHT = 4;     // lr_horz: terms per block (summed on chip into one slot)
 constexpr int kVMax = 64;  // most terms one lr_vert launch filters
-#ifndef BF_LR_HORZ_L2_MB
-#define BF_LR_HORZ_L2_MB 56
-#endif
 // lr_horz: L2 bytes the lagged reads of all resident blocks may occupy
-constexpr size_t kHorzL2Bytes = (size_t)BF_LR_HORZ_L2_MB << 20;
+constexpr size_t kHorzL2Bytes = (size_t)56 << 20;
 constexpr int kHorzPrefetchR = 24;  // lr_horz prefetches the next chunk from this r on
-#ifndef BF_LR_VBANDS_MIN
-#define BF_LR_VBANDS_MIN 1
-#endif
-constexpr int kVBandsMin = BF_LR_VBANDS_MIN;  // lr_vert: fewest bands of rows
 __host__ __device__ __forceinline__ int L_of(int r) { return 2 * r + 1; }
 
 struct LrParams {
@@ -71,7 +64,6 @@ struct LrParams {
     int n_terms;          // terms of this launch (<= kVMax; lr_horz takes lr_vert's)
     float tv[kVMax];      // lr_vert: turns per gray level of its terms
     float th[kVMax], ah[kVMax];  // lr_horz: turns and weights of its terms
-    int h0;               // lr_horz: Vt slot of its first term
     int nyb;              // row blocks of the blocked column layout: ceil(H / kYB)
     float *Vt;            // [lr_vert's terms][4 planes] blocked planes: vertically filtered
     float *Acc;           // [slots][2] blocked planes: Q and P per group of kHT terms
@@ -330,7 +322,7 @@ __global__ void __launch_bounds__(64 * kHT, PF ? 1 : 2) lr_horz(const __grid_con
         const int y_lane = rb * kYB + (lane & (kYB - 1));
         const size_t row = blocked_at(W, 0, min(y_lane, p.H - 1));  // column 0 of this row
         const float2 *V =
-            reinterpret_cast<const float2 *>(p.Vt) + ((size_t)(p.h0 + tc) * 2 + q) * plane + row;
+            reinterpret_cast<const float2 *>(p.Vt) + ((size_t)tc * 2 + q) * plane + row;
         const float *F = p.ft + row;
         const int x0 = ix * p.band_w;
         const int x1 = min(x0 + p.band_w, W);
@@ -563,8 +555,7 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     const int min_band = 12 * p.r;
     const int ncb = (W + kVCols - 1) / kVCols;
     const int zb_max = (gv_max + kVB - 1) / kVB;
-    const int nbh_max = std::max(
-        1, std::min(std::max(kVBandsMin, resident_vert / (ncb * zb_max)), H / min_band));
+    const int nbh_max = std::max(1, std::min(resident_vert / (ncb * zb_max), H / min_band));
     p.band_h = ((H + nbh_max - 1) / nbh_max + 7) / 8 * 8;
     const int nbh = (H + p.band_h - 1) / p.band_h;
     const int nyb2 = (p.nyb + 1) / 2;
@@ -609,7 +600,6 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
                 p.th[g] = pl->turns32[m];
                 p.ah[g] = pl->a32[m];
             }
-            p.h0 = 0;
             p.first = m0 == 0;
             dim3 gv(ncb, nbh, (nv + kVB - 1) / kVB);
             kv<<<gv, kVCols * kVB, sm_v, s>>>(p);

@@ -200,3 +200,16 @@ def test_cosine_plan_backward_has_no_sigma_r(bf):
     fake = ctypes.c_void_p(0x1000)
     st = l.bf_backward(p.handle, fake, fake, fake, fake, fake, fake, 16, 16, fake, 1 << 20, None)
     assert st == 1 and b"sigma_r" in l.bf_last_error()
+
+
+def test_size_limits_are_checked_on_the_host(bf):
+    # 2^29 pixels is the largest image; one more pixel is refused before any launch
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    p = bf.Plan(2.0, 20.0, kind="box")
+    fake = ctypes.c_void_p(0x1000)
+    null = ctypes.c_void_p(0)
+    H, W = 16384, 32768 + 1
+    assert l.bf_forward(p.handle, fake, 0, fake, H, W, 1, W, null, null) == 2
+    assert b"too large" in l.bf_last_error()
+    assert l.bf_backward(p.handle, fake, fake, fake, fake, fake, null, H, W, null, 0, null) == 2

@@ -342,3 +342,52 @@ def test_tuned_tile_shape_stays_correct(bf, oracle, kind, ss):
     if ref is not None:
         assert np.abs(after - ref).max() <= TOL
     assert np.abs(after - before).max() <= TOL / 5
+
+
+@pytest.mark.parametrize("H,W,kind,ss,rad", [(3, 6000, "box", 12.0, 12), (6000, 3, "box", 12.0, 12),
+                                             (1, 70001, "box", 2.0, 2), (70001, 1, "gauss", 3.0, 9),
+                                             (2, 40000, "gauss", 6.0, 18)])
+def test_extreme_aspect_ratios(bf, oracle, H, W, kind, ss, rad):
+    # one or a few rows / columns: every tile and sweep is ragged in one direction
+    img = synth.rectangles(H, W, n_rect=20, noise=8.0, seed=H + W)
+    plan = bf.Plan(ss, 20.0, kind=kind, radius=rad)
+    out = _run(bf, img, plan)
+    idx = np.unique(np.concatenate([np.arange(0, H * W, max(1, H * W // 1500)),
+                                    [0, H * W - 1, W - 1, (H - 1) * W]]))
+    ref = oracle.bf_brute_at(img.astype(np.float64), idx, sigma_r=20.0,
+                             w1=plan_w1(oracle, plan), N=plan.N)
+    err = np.abs(out.ravel()[idx] - ref).max()
+    print("%dx%d %s rad=%d max abs err %.3e" % (H, W, kind, rad, err))
+    assert err <= TOL
+
+
+def test_largest_accepted_image(bf, oracle):
+    # H * W = 2^29 pixels, the largest single image the entry points accept
+    # (2 GiB in, 2 GiB out): generated on the device from the pixel coordinates,
+    # checked against the oracle on crops around corners, edges and seeded
+    # interior pixels (a crop of +-2R keeps every neighbour of its centre, and
+    # clamping happens only where the crop edge is the image edge)
+    import torch
+    H, W = 16384, 32768
+    plan = bf.Plan(2.0, 20.0, kind="box")
+    R = plan.radius
+    y = torch.arange(H, device="cuda", dtype=torch.float32).view(H, 1)
+    x = torch.arange(W, device="cuda", dtype=torch.float32).view(1, W)
+    img = torch.remainder(x * 0.37 + y * 0.11, 64.0) * 3.0 + \
+        torch.remainder(torch.floor(x / 37.0) + torch.floor(y / 53.0), 2.0) * 60.0
+    out = bf.forward(plan, img)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(17)
+    pts = [(0, 0), (0, W - 1), (H - 1, 0), (H - 1, W - 1), (0, W // 2), (H - 1, 12345),
+           (H // 3, 0), (777, W - 1)] + [(int(a), int(b)) for a, b in
+                                         zip(rng.integers(0, H, 40), rng.integers(0, W, 40))]
+    w1 = plan_w1(oracle, plan)
+    for (i, j) in pts:
+        i0, i1 = max(0, i - 2 * R), min(H, i + 2 * R + 1)
+        j0, j1 = max(0, j - 2 * R), min(W, j + 2 * R + 1)
+        crop = img[i0:i1, j0:j1].cpu().numpy().astype(np.float64)
+        ref = oracle.bf_brute_at(crop, [(i - i0) * (j1 - j0) + (j - j0)], sigma_r=20.0, w1=w1,
+                                 N=plan.N)
+        assert abs(float(out[i, j]) - ref[0]) <= TOL, (i, j)
+    del img, out
+    torch.cuda.empty_cache()
