@@ -53,7 +53,16 @@ typedef enum {
 
 typedef enum {
     BF_SPATIAL_GAUSS_TRUNC = 0,  /* w1(i) ~ exp(-i^2 / 2 sigma_s^2), |i| <= R, unit sum */
-    BF_SPATIAL_BOX_ITER = 1      /* box_passes boxes of half-width r, convolved */
+    BF_SPATIAL_BOX_ITER = 1,     /* box_passes boxes of half-width r, convolved */
+    BF_SPATIAL_GAUSS_RECURSIVE = 2
+    /* The recursive O(1) Gaussian the paper's experiments use (Section 3): the
+     * third-order causal + anticausal recursion of Young and van Vliet (1995)
+     * with their published design q(sigma_s), b0..b3, applied along columns
+     * and then rows; cost independent of sigma_s (0.5 <= sigma_s <= 256).
+     * Borders (clamp-to-edge): the causal pass starts from its steady state
+     * for the first sample, runs P = ceil(6 sigma_s) samples on into the
+     * constant extension after the last one, and the anticausal pass starts
+     * there from its steady state.  bf_plan_info reports P as the radius. */
 } bf_spatial_kind;
 
 typedef enum { BF_F32 = 0, BF_U8 = 1 } bf_dtype;

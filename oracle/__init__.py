@@ -17,6 +17,8 @@ The arithmetic lives in ``bf_oracle.c`` (plain C, double precision, OpenMP):
 * ``bf_grad`` -- exact gradient of ``sum(u * out)`` w.r.t. the image and
   sigma_r (N fixed), by the chain rule on eq. (BF).
 * ``fd_grad_f`` / ``loss`` -- central finite differences of the brute force.
+* ``rg_filter`` / ``bf_trig_rg`` -- the recursive O(1) Gaussian of Young and
+  van Vliet (the paper's spatial filter in Section 3) and Algorithm 1 with it.
 * ``bf_brute_cos`` / ``bf_brute_cos_at`` / ``bf_grad_cos`` / ``fd_grad_f_cos``
   / ``phi_cos`` -- the same for a general trigonometric range kernel of
   Section 2.2, ``phi(s) = a_0 + a_1 cos(gamma s) + ... + a_N cos(N gamma s)``,
@@ -112,6 +114,13 @@ def _load():
         lib.or_phi_cos_table.restype = None
         lib.or_phi_cos_table.argtypes = [ctypes.c_double, _dp, ctypes.c_int, _dp,
                                          ctypes.c_longlong, _dp]
+        lib.or_rg_coefs.restype = ctypes.c_int
+        lib.or_rg_coefs.argtypes = [ctypes.c_double, _dp]
+        lib.or_rg_filter.restype = None
+        lib.or_rg_filter.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]
+        lib.or_bf_trig_rg.restype = ctypes.c_double
+        lib.or_bf_trig_rg.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
         lib.or_phi_table.restype = None
         lib.or_phi_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
                                      ctypes.c_longlong, _dp]
@@ -389,3 +398,43 @@ def phi_cos(s, gamma, coefs):
     out = np.empty_like(s)
     lib.or_phi_cos_table(float(gamma), _ptr(a), len(a), _ptr(s), len(s), _ptr(out))
     return out
+
+
+# ---- recursive Gaussian (Young and van Vliet) -------------------------------
+
+def rg_coefs(sigma: float):
+    """(B, b1/b0, b2/b0, b3/b0) of the recursive Gaussian and the extension P."""
+    c = np.zeros(4, dtype=np.float64)
+    P = _load().or_rg_coefs(float(sigma), _ptr(c))
+    return c, int(P)
+
+
+def rg_filter(img, sigma: float) -> np.ndarray:
+    """The separable recursive Gaussian of an H x W image (columns, then rows)."""
+    x = _f64(img)
+    H, W = x.shape
+    y = np.empty_like(x)
+    _load().or_rg_filter(_ptr(x), H, W, float(sigma), _ptr(y))
+    return y
+
+
+def bf_trig_rg(f, sigma_s=10.0, sigma_r=30.0, T=255.0, N=None, return_q=False):
+    """Algorithm 1 (complex form) with the recursive Gaussian as the averaging;
+    f is H x W or H x W x C (channels filtered independently)."""
+    lib = _load()
+    if N is None:
+        N = n_rule(sigma_r, T)
+    chans, multi = _channels(f)
+    outs, qs = [], []
+    for ch in chans:
+        x = _f64(ch)
+        H, W = x.shape
+        o = np.empty((H, W), dtype=np.float64)
+        q = np.empty((H, W), dtype=np.float64)
+        lib.or_bf_trig_rg(_ptr(x), H, W, float(sigma_s), float(sigma_r), float(T), int(N),
+                          _ptr(o), _ptr(q))
+        outs.append(o)
+        qs.append(q)
+    out = np.stack(outs, axis=2) if multi else outs[0]
+    q = np.stack(qs, axis=2) if multi else qs[0]
+    return (out, q) if return_q else out

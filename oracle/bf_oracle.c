@@ -21,6 +21,10 @@
  *                        the chain rule applied to the definition);
  *   - or_bf_fd_grad_f  : central finite differences of or_bf_brute for the
  *                        same gradient;
+ *   - or_rg_* / or_bf_trig_rg : the recursive O(1) Gaussian of Young and van
+ *                        Vliet (the spatial filter of the paper's experiments,
+ *                        Section 3) and Algorithm 1 with it as the averaging
+ *                        of step 4;
  *   - or_bf_*_cos      : the same filter, gradient and differences for a
  *                        general trigonometric range kernel of Section 2.2,
  *                        phi(s) = a_0 + a_1 cos(gamma s) + ... + a_N cos(N gamma s),
@@ -514,4 +518,133 @@ void or_phi_table(int mode, double sigma_r, int N, const double *s, long long n,
 {
     or_range rg = or_make_range(mode, sigma_r, N);
     for (long long t = 0; t < n; t++) out[t] = or_phi(&rg, s[t]);
+}
+
+
+/* ------------------------------------------------------------------------
+ * Recursive Gaussian (Young and van Vliet, "Recursive implementation of the
+ * Gaussian filter", Signal Processing 44, 1995): a causal and an anticausal
+ * third-order recursion whose cascade approximates a Gaussian of standard
+ * deviation sigma (valid for sigma >= 0.5).  Published design:
+ *   q  = 0.98711 sigma - 0.96330                    (sigma >= 2.5)
+ *   q  = 3.97156 - 4.14554 sqrt(1 - 0.26891 sigma)  (0.5 <= sigma < 2.5)
+ *   b0 = 1.57825 + 2.44413 q + 1.4281 q^2 + 0.422205 q^3
+ *   b1 = 2.44413 q + 2.85619 q^2 + 1.26661 q^3
+ *   b2 = -(1.4281 q^2 + 1.26661 q^3)
+ *   b3 = 0.422205 q^3
+ *   B  = 1 - (b1 + b2 + b3) / b0
+ *   causal:     w[n] = B x[n] + (b1 w[n-1] + b2 w[n-2] + b3 w[n-3]) / b0
+ *   anticausal: y[n] = B w[n] + (b1 y[n+1] + b2 y[n+2] + b3 y[n+3]) / b0
+ * Boundary (the image extended by clamping, as everywhere here): the causal
+ * pass starts from its steady state for the constant x[0] (exact for a
+ * constant extension, the recursion having unit gain at DC); it then runs P
+ * further samples into the constant extension x[n-1], and the anticausal pass
+ * starts there from its steady state w[n-1+P].  P = ceil(6 sigma).
+ * coef[] = { B, b1/b0, b2/b0, b3/b0 }.  Returns P. */
+int or_rg_coefs(double sigma, double *coef)
+{
+    double q = sigma >= 2.5 ? 0.98711 * sigma - 0.96330
+                            : 3.97156 - 4.14554 * sqrt(1.0 - 0.26891 * sigma);
+    double b0 = 1.57825 + 2.44413 * q + 1.4281 * q * q + 0.422205 * q * q * q;
+    double b1 = 2.44413 * q + 2.85619 * q * q + 1.26661 * q * q * q;
+    double b2 = -(1.4281 * q * q + 1.26661 * q * q * q);
+    double b3 = 0.422205 * q * q * q;
+    coef[0] = 1.0 - (b1 + b2 + b3) / b0;
+    coef[1] = b1 / b0;
+    coef[2] = b2 / b0;
+    coef[3] = b3 / b0;
+    return (int)ceil(6.0 * sigma);
+}
+
+/* One line x[0 .. n-1] (stride `st`) -> y (stride `st`), work buffer of n + P. */
+static void or_rg_line(const double complex *x, long st, int n, const double *c, int P,
+                       double complex *w, double complex *y)
+{
+    double complex w1 = x[0], w2 = x[0], w3 = x[0];
+    for (int k = 0; k < n + P; k++) {
+        double complex xin = k < n ? x[(long)k * st] : x[(long)(n - 1) * st];
+        double complex v = c[0] * xin + c[1] * w1 + c[2] * w2 + c[3] * w3;
+        w[k] = v;
+        w3 = w2; w2 = w1; w1 = v;
+    }
+    double complex y1 = w[n + P - 1], y2 = y1, y3 = y1;
+    for (int k = n + P - 1; k >= 0; k--) {
+        double complex v = c[0] * w[k] + c[1] * y1 + c[2] * y2 + c[3] * y3;
+        if (k < n) y[(long)k * st] = v;
+        y3 = y2; y2 = y1; y1 = v;
+    }
+}
+
+/* Separable recursive Gaussian of a complex H x W image: columns, then rows. */
+static void or_rg_filter_c(const double complex *x, int H, int W, double sigma,
+                           double complex *tmp, double complex *y)
+{
+    double c[4];
+    int P = or_rg_coefs(sigma, c);
+#pragma omp parallel
+    {
+        double complex *w = (double complex *)malloc(sizeof(double complex) * (size_t)((H > W ? H : W) + P));
+#pragma omp for schedule(static)
+        for (int j = 0; j < W; j++) or_rg_line(x + j, W, H, c, P, w, tmp + j);
+#pragma omp for schedule(static)
+        for (int i = 0; i < H; i++) or_rg_line(tmp + (size_t)i * W, 1, W, c, P, w, y + (size_t)i * W);
+        free(w);
+    }
+}
+
+/* The recursive Gaussian of a real image (the spatial averaging alone). */
+void or_rg_filter(const double *x, int H, int W, double sigma, double *y)
+{
+    size_t n = (size_t)H * W;
+    double complex *a = (double complex *)malloc(n * sizeof(double complex));
+    double complex *t = (double complex *)malloc(n * sizeof(double complex));
+    double complex *b = (double complex *)malloc(n * sizeof(double complex));
+    for (size_t p = 0; p < n; p++) a[p] = x[p];
+    or_rg_filter_c(a, H, W, sigma, t, b);
+    for (size_t p = 0; p < n; p++) y[p] = creal(b[p]);
+    free(a); free(t); free(b);
+}
+
+/* Algorithm 1, steps 1-5, in the paper's complex notation (as or_bf_trig),
+ * with the recursive Gaussian as the O(1) averaging of step 4 (Section 3). */
+double or_bf_trig_rg(const double *f, int H, int W, double sigma_s, double sigma_r,
+                     double T, int N, double *out, double *q_out)
+{
+    size_t n = (size_t)H * W;
+    double gamma = OR_PI / (2.0 * T);
+    double rho = gamma * sigma_r;
+    double complex *h = (double complex *)malloc(n * sizeof(double complex));
+    double complex *g = (double complex *)malloc(n * sizeof(double complex));
+    double complex *hb = (double complex *)malloc(n * sizeof(double complex));
+    double complex *gb = (double complex *)malloc(n * sizeof(double complex));
+    double complex *tmp = (double complex *)malloc(n * sizeof(double complex));
+    double complex *num = (double complex *)calloc(n, sizeof(double complex));
+    double complex *den = (double complex *)calloc(n, sizeof(double complex));
+    for (int k = 0; k <= N; k++) {
+        double cn = exp(lgamma(N + 1.0) - lgamma(k + 1.0) - lgamma(N - k + 1.0) -
+                        N * log(2.0));
+        double freq = gamma * (double)(2 * k - N) / (rho * sqrt((double)N));
+        for (size_t p = 0; p < n; p++) {
+            h[p] = cexp(I * freq * f[p]);
+            g[p] = f[p] * h[p];
+        }
+        or_rg_filter_c(h, H, W, sigma_s, tmp, hb);
+        or_rg_filter_c(g, H, W, sigma_s, tmp, gb);
+        for (size_t p = 0; p < n; p++) {
+            double complex d = cn * cexp(-I * freq * f[p]);
+            num[p] += d * gb[p];
+            den[p] += d * hb[p];
+        }
+    }
+    double worst = 0.0;
+    for (size_t p = 0; p < n; p++) {
+        out[p] = creal(num[p]) / creal(den[p]);
+        if (q_out) q_out[p] = creal(den[p]);
+        double e1 = fabs(cimag(num[p])) / (fabs(creal(num[p])) + 1e-300);
+        double e2 = fabs(cimag(den[p])) / (fabs(creal(den[p])) + 1e-300);
+        if (e1 > worst) worst = e1;
+        if (e2 > worst) worst = e2;
+    }
+    free(h); free(g); free(hb); free(gb); free(tmp); free(num); free(den);
+    return worst;
 }

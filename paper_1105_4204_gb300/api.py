@@ -15,7 +15,8 @@ from ._lib import PlanOpts, check, lib
 
 GAUSS = 0
 BOX = 1
-_KINDS = {"gauss": GAUSS, "box": BOX}
+RECURSIVE = 2
+_KINDS = {"gauss": GAUSS, "box": BOX, "recursive": RECURSIVE}
 
 
 def _kind(kind) -> int:

@@ -154,6 +154,14 @@ static bf_status forward_planes(const bf_plan *plan, const BfImage &img, cudaStr
         if (e != cudaSuccess) return cuda_check(e, who);
         return cuda_check(launch_large_box(plan, img, ws, stream), who);
     }
+    if (plan->kind == BF_SPATIAL_GAUSS_RECURSIVE) {
+        void *ws = nullptr;
+        cudaError_t e = get_scratch(recursive_workspace(plan, H, W), &ws);
+        if (e == cudaErrorMemoryAllocation)
+            return fail(BF_ENOMEM, std::string(who) + ": cannot allocate the recursive scratch");
+        if (e != cudaSuccess) return cuda_check(e, who);
+        return cuda_check(launch_recursive(plan, img, ws, stream), who);
+    }
     return fail(BF_EUNSUPPORTED, std::string(who) + ": no kernel for this spatial support");
 }
 
@@ -216,6 +224,9 @@ extern "C" bf_status bf_forward_unfused(const bf_plan *plan, const float *in, fl
                                         int W, void *workspace, size_t workspace_bytes,
                                         cudaStream_t stream) {
     if (!plan) return fail(BF_EINVAL, "bf_forward_unfused: plan is NULL");
+    if (plan->kind == BF_SPATIAL_GAUSS_RECURSIVE)
+        return fail(BF_EUNSUPPORTED, "bf_forward_unfused: the unfused baseline has no "
+                                     "recursive Gaussian");
     if (!in || !out || !workspace)
         return fail(BF_EINVAL, "bf_forward_unfused: in/out/workspace is NULL");
     if (H < 1 || W < 1) return fail(BF_EINVAL, "bf_forward_unfused: H and W must be >= 1");

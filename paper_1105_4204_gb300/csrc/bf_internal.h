@@ -35,6 +35,9 @@ struct bf_plan {
     // phi(s) = sum_n a_n cos(n gamma s); sigma_r and T are then 0.
     bool cosine = false;
     double gamma = 0.0;
+    // Recursive Gaussian (kind 2): B, b1/b0, b2/b0, b3/b0 and the extension P.
+    double rg[4] = {0, 0, 0, 0};
+    int rg_P = 0;
 };
 
 // Per-launch term table, passed by value as a kernel parameter (constant bank).
@@ -83,5 +86,9 @@ cudaError_t launch_tile_forward(const bf_plan *p, const BfImage &img, cudaStream
 // turn) through a scratch buffer of large_workspace(p, H, W) bytes.
 size_t large_workspace(const bf_plan *p, int H, int W);
 cudaError_t launch_large_box(const bf_plan *p, const BfImage &img, void *ws, cudaStream_t s);
+// The recursive Gaussian (kind 2): a vertical and a horizontal recursive
+// sweep through a scratch buffer of recursive_workspace(p, H, W) bytes.
+size_t recursive_workspace(const bf_plan *p, int H, int W);
+cudaError_t launch_recursive(const bf_plan *p, const BfImage &img, void *ws, cudaStream_t s);
 
 }  // namespace bf

@@ -486,6 +486,262 @@ __global__ void lr_final(const float *__restrict__ Acc, int n_slots, float *__re
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Recursive Gaussian (the O(1) spatial filter of the paper's experiments,
+// Section 3): per axis a causal and an anticausal third-order recursion
+// (Young and van Vliet), B and a_k = b_k / b0:
+//   w(e) = B x(e) + a1 w(e-1) + a2 w(e-2) + a3 w(e-3)       (causal)
+//   y(e) = B w(e) + a1 y(e+1) + a2 y(e+2) + a3 y(e+3)       (anticausal)
+// evaluated in difference form: with d1 = w(e-1) - w(e-2), d2 = w(e-2) - w(e-3),
+//   w(e) = w(e-1) + [B (x(e) - w(e-1)) - ((a2 + a3) d1 + a3 d2)],
+// the same recursion (B = 1 - a1 - a2 - a3), but with unit DC gain exactly
+// whatever the FP32 rounding of its coefficients, and without the
+// cancellation of the direct form's large alternating terms (at sigma = 100,
+// a1 ~ 3: the direct form in FP32 is off by units of gray level, this form by
+// about 1e-3).  The causal pass starts from its steady state for x(0) (exact
+// for the clamped extension) and runs P samples past the last one on the
+// constant extension; the anticausal pass starts there from its steady state.
+// The vertical pass (rg_vert, a thread per column and term, four terms per
+// block) writes the filtered pairs (cos, sin) and (f cos, f sin) of every
+// term through the scratch (rows 0 .. H+P-1 of an extended blocked layout);
+// the horizontal pass (rg_horz, the lr_horz warp layout: a warp per term,
+// pair and two row blocks, four terms per block) filters them in place along
+// the rows (columns 0 .. W+P-1) and, on its way back, combines
+// eq. (final-form) per pixel and sums the block's four terms on chip into one
+// (Q, P) slot pair per group.
+
+struct RgParams {
+    const void *in;       // first pixel of the plane being filtered
+    long long in_stride;  // elements between rows
+    int dtype, in_px;
+    int H, W, P;
+    int We;               // columns of the extended planes, W + P rounded up to 8
+    int nybe;             // row blocks of the extended planes, ceil((H + P) / 16)
+    int nyb;              // row blocks of the image
+    int n_terms;
+    float tv[kVMax], ah[kVMax];  // turns per gray level and weights of the launch's terms
+    float cB, cD1, cD2;   // B, a2 + a3, a3 of the difference form
+    float *Vt;            // [terms][2 pairs] float2 planes of nybe * 16 * We
+    float *Acc;           // [slots][Q, P] blocked H x W planes
+    const float *ft;      // f, blocked H x W
+    int first;            // first launch of the plane (slots start from zero)
+};
+
+// One step of the difference form on a pair: state (w = last output,
+// d1, d2 = its last two increments).
+__device__ __forceinline__ float2 rg_step1(float2 cB, float2 cD1, float2 cD2, float2 x,
+                                           float2 &w, float2 &d1, float2 &d2) {
+    const float2 dw = f2sub(f2mul(cB, f2sub(x, w)), f2fma(cD2, d2, f2mul(cD1, d1)));
+    w = f2add(w, dw);
+    d2 = d1;
+    d1 = dw;
+    return w;
+}
+
+__device__ __forceinline__ void rg_step(const RgParams &p, const float2 (&x)[2], float2 (&w)[2],
+                                        float2 (&d1)[2], float2 (&d2)[2]) {
+    const float2 cB = make_float2(p.cB, p.cB), cD1 = make_float2(p.cD1, p.cD1);
+    const float2 cD2 = make_float2(p.cD2, p.cD2);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) rg_step1(cB, cD1, cD2, x[q], w[q], d1[q], d2[q]);
+}
+
+// grid: (ceil(W / 32), 1, ceil(terms / 4)); block 128: (column, term)
+template <int DT>
+__global__ void __launch_bounds__(kVCols * kVB) rg_vert(const __grid_constant__ RgParams p) {
+    const int tid = threadIdx.x;
+    const int col = tid % kVCols;
+    const int g = blockIdx.z * kVB + tid / kVCols;
+    const int x = blockIdx.x * kVCols + col;
+    const int xc = min(x, p.W - 1);
+    const bool col_ok = x < p.W && g < p.n_terms;
+    const float tm = p.tv[min(g, p.n_terms - 1)];
+    const int E = p.H + p.P;
+    const size_t plane = (size_t)p.nybe * kYB * p.We;
+    float2 *dst = reinterpret_cast<float2 *>(p.Vt) + (size_t)min(g, p.n_terms - 1) * 2 * plane;
+    auto fval = [&](int e) {
+        const long long off = (long long)min(e, p.H - 1) * p.in_stride + (long long)xc * p.in_px;
+        if constexpr (DT == 0) return __ldg(reinterpret_cast<const float *>(p.in) + off);
+        else return (float)__ldg(reinterpret_cast<const uint8_t *>(p.in) + off);
+    };
+    // state: last output (steady state x(0)) and its last two increments
+    float2 s1[2], s2[2], s3[2], x0[2];
+    aux4p(tm, fval(0), x0);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        s1[q] = x0[q];
+        s2[q] = s3[q] = make_float2(0.f, 0.f);
+    }
+    float cur[kChunk], nxt[kChunk];
+#pragma unroll
+    for (int d = 0; d < kChunk; ++d) cur[d] = fval(d);
+    float2 st[2][kChunk];
+    // causal, rows 0 .. E-1 (the last chunk's rows past E keep the state)
+    for (int e0 = 0; e0 < E; e0 += kChunk) {
+#pragma unroll
+        for (int d = 0; d < kChunk; ++d) nxt[d] = fval(e0 + kChunk + d);
+#pragma unroll
+        for (int d = 0; d < kChunk; ++d) {
+            if (e0 + d < E) {
+                float2 xi[2];
+                aux4p(tm, cur[d], xi);
+                rg_step(p, xi, s1, s2, s3);
+            }
+            st[0][d] = s1[0];
+            st[1][d] = s1[1];
+        }
+        if (col_ok) {
+            float2 *dc = dst + blocked_at(p.We, x, e0);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                float4 *d4 = reinterpret_cast<float4 *>(dc + q * plane);
+#pragma unroll
+                for (int k = 0; k < kChunk / 2; ++k)
+                    d4[k] = make_float4(st[q][2 * k].x, st[q][2 * k].y, st[q][2 * k + 1].x,
+                                        st[q][2 * k + 1].y);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < kChunk; ++d) cur[d] = nxt[d];
+    }
+    // anticausal, rows E-1 .. 0, from the steady state of w(E-1), in place
+    float2 t1[2], t2[2], t3[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        t1[q] = s1[q];
+        t2[q] = t3[q] = make_float2(0.f, 0.f);
+    }
+    if (!col_ok) return;
+    for (int e0 = (E - 1) / kChunk * kChunk; e0 >= 0; e0 -= kChunk) {
+        float2 *dc = dst + blocked_at(p.We, x, e0);
+        float2 wv[2][kChunk];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(dc + q * plane);
+#pragma unroll
+            for (int k = 0; k < kChunk / 2; ++k) {
+                const float4 v = s4[k];
+                wv[q][2 * k] = make_float2(v.x, v.y);
+                wv[q][2 * k + 1] = make_float2(v.z, v.w);
+            }
+        }
+#pragma unroll
+        for (int d = kChunk - 1; d >= 0; --d) {
+            if (e0 + d < E) {
+                float2 wi[2] = {wv[0][d], wv[1][d]};
+                rg_step(p, wi, t1, t2, t3);
+                wv[0][d] = t1[0];
+                wv[1][d] = t1[1];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float4 *d4 = reinterpret_cast<float4 *>(dc + q * plane);
+#pragma unroll
+            for (int k = 0; k < kChunk / 2; ++k)
+                d4[k] = make_float4(wv[q][2 * k].x, wv[q][2 * k].y, wv[q][2 * k + 1].x,
+                                    wv[q][2 * k + 1].y);
+        }
+    }
+}
+
+// grid: (ceil(nyb / 2), 1, ceil(terms / kHT)); block: 2 kHT warps, as lr_horz
+__global__ void __launch_bounds__(64 * kHT) rg_horz(const __grid_constant__ RgParams p) {
+    __shared__ float hs_sm[2][2 * kHT][kChunkH][32];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int q = warp & 1;
+    const int tl = warp >> 1;
+    const int term = blockIdx.z * kHT + tl;
+    const bool term_ok = term < p.n_terms;
+    const int tc = min(term, p.n_terms - 1);
+    const int W = p.W;
+    const size_t plane = (size_t)p.nybe * kYB * p.We;
+    const size_t fplane = blocked_plane(p.H, W);
+    const int rb = min((int)blockIdx.x * 2 + (lane >> 4), p.nyb - 1);
+    const int y_own = (int)blockIdx.x * 2 * kYB + lane;  // the lane's row (may be past H)
+    const int y_lane = min(rb * kYB + (lane & (kYB - 1)), p.H - 1);
+    // lanes past the last row read the last row's data and store nothing
+    const bool row_ok = y_own < p.H;
+    float2 *V = reinterpret_cast<float2 *>(p.Vt) + ((size_t)tc * 2 + q) * plane +
+                blocked_at(p.We, 0, y_lane);
+    const float *F = p.ft + blocked_at(W, 0, y_lane);
+    const float am = term_ok ? p.ah[tc] : 0.f, tm = p.tv[tc];
+    const int E = W + p.P;
+    constexpr int NOUT = 2 * kChunkH * 32;
+    constexpr int PER = NOUT / (64 * kHT);
+    // causal, columns 0 .. E-1, in place (inputs past W-1 are the last one)
+    float2 s1 = V[0], s2 = make_float2(0.f, 0.f), s3 = s2;
+    const float2 last = V[(size_t)(W - 1) * kYB];
+    const float2 cB = make_float2(p.cB, p.cB), cD1 = make_float2(p.cD1, p.cD1);
+    const float2 cD2 = make_float2(p.cD2, p.cD2);
+    float2 cur[kChunkH], nxt[kChunkH];
+#pragma unroll
+    for (int d = 0; d < kChunkH; ++d) cur[d] = d < W ? V[(size_t)d * kYB] : last;
+    for (int e0 = 0; e0 < E; e0 += kChunkH) {
+#pragma unroll
+        for (int d = 0; d < kChunkH; ++d) {
+            const int e = e0 + kChunkH + d;
+            nxt[d] = e < W ? V[(size_t)e * kYB] : last;
+        }
+#pragma unroll
+        for (int d = 0; d < kChunkH; ++d) {
+            if (e0 + d < E) {
+                const float2 v = rg_step1(cB, cD1, cD2, cur[d], s1, s2, s3);
+                if (row_ok) V[(size_t)(e0 + d) * kYB] = v;
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < kChunkH; ++d) cur[d] = nxt[d];
+    }
+    // anticausal, columns E-1 .. 0, combining at the image's columns
+    float2 t1 = s1, t2 = make_float2(0.f, 0.f), t3 = t2;
+    int buf = 0;
+    for (int e0 = (E - 1) / kChunkH * kChunkH; e0 >= 0; e0 -= kChunkH) {
+        float2 wv[kChunkH];
+        float cf[kChunkH];
+#pragma unroll
+        for (int d = 0; d < kChunkH; ++d) {
+            const int e = e0 + d;
+            wv[d] = e < E ? V[(size_t)e * kYB] : make_float2(0.f, 0.f);
+            cf[d] = __ldg(F + (size_t)min(e, W - 1) * kYB);
+        }
+#pragma unroll
+        for (int d = kChunkH - 1; d >= 0; --d) {
+            if (e0 + d < E) wv[d] = rg_step1(cB, cD1, cD2, wv[d], t1, t2, t3);
+        }
+        if (e0 >= W) continue;  // extension only: no outputs (uniform)
+#pragma unroll
+        for (int d = 0; d < kChunkH; ++d) {
+            float rr = tm * cf[d];
+            rr = rr - rintf(rr);
+            float sn, cs;
+            __sincosf(kTwoPi * rr, &sn, &cs);
+            hs_sm[buf][warp][d][lane] = am * fmaf(cs, wv[d].x, sn * wv[d].y);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int o = k * 64 * kHT + threadIdx.x;
+            const int rq = o / (kChunkH * 32);
+            const int rd = (o / 32) % kChunkH;
+            const int rl = o % 32;
+            float v = hs_sm[buf][rq][rd][rl];
+#pragma unroll
+            for (int t = 1; t < kHT; ++t) v += hs_sm[buf][2 * t + rq][rd][rl];
+            const int tcol = e0 + rd;
+            const int orb = blockIdx.x * 2 + (rl >> 4);
+            const int oy = orb * kYB + (rl & (kYB - 1));
+            if (tcol < W && orb < p.nyb && oy < p.H) {
+                float *A = p.Acc + ((size_t)blockIdx.z * 2 + rq) * fplane + blocked_at(W, tcol, oy);
+                *A = p.first ? v : *A + v;
+            }
+        }
+        buf ^= 1;
+    }
+}
+
 }  // namespace
 
 // Terms per lr_vert launch: all of them while their filtered planes stay
@@ -605,6 +861,94 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
             kv<<<gv, kVCols * kVB, sm_v, s>>>(p);
             const int items = nyb2 * nbw * ((nv + kHT - 1) / kHT);
             kh<<<std::min(items, horz_grid), 64 * kHT, 0, s>>>(p);
+        }
+        dim3 gf((W + 31) / 32, (H + 31) / 32);
+        lr_final<<<gf, dim3(32, 8), 0, s>>>(
+            p.Acc, n_slots, img.out + (long long)ch * img.out_z,
+            img.q_out ? img.q_out + (long long)ch * img.out_z : nullptr, H, W, img.out_px,
+            img.q_scale);
+    }
+    return cudaGetLastError();
+}
+
+
+// ---- recursive Gaussian: scratch and launches -------------------------------
+
+static size_t rg_plane(const bf_plan *pl, int H, int W) {  // float2 elements
+    const int P = pl->rg_P;
+    const size_t nybe = (size_t)(H + P + kYB - 1) / kYB;
+    const size_t We = (size_t)(W + P + kChunkH - 1) / kChunkH * kChunkH;
+    return nybe * kYB * We;
+}
+
+static int rg_terms(const bf_plan *pl, int H, int W) {
+    const size_t term_bytes = 2 * rg_plane(pl, H, W) * sizeof(float2);
+    const size_t budget = (size_t)4 << 30;
+    const int nt = (int)pl->a32.size();
+    const int cap = (int)std::max<size_t>(kHT, std::min<size_t>(kVMax, budget / term_bytes));
+    return std::min(nt, cap);
+}
+
+size_t recursive_workspace(const bf_plan *pl, int H, int W) {
+    const int m = rg_terms(pl, H, W);
+    const size_t slots = (size_t)(m + kHT - 1) / kHT;
+    return (size_t)m * 2 * rg_plane(pl, H, W) * sizeof(float2) +
+           (2 * slots + 1) * blocked_plane(H, W) * sizeof(float) + 256;
+}
+
+cudaError_t launch_recursive(const bf_plan *pl, const BfImage &img, void *ws, cudaStream_t s) {
+    const int H = img.H, W = img.W;
+    const int nt = (int)pl->a32.size();
+    const int gv_max = rg_terms(pl, H, W);
+    const int n_slots = (gv_max + kHT - 1) / kHT;
+    char *base = reinterpret_cast<char *>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    RgParams p{};
+    p.in_stride = img.in_row_stride;
+    p.dtype = img.dtype;
+    p.in_px = img.in_px;
+    p.H = H;
+    p.W = W;
+    p.P = pl->rg_P;
+    p.We = (W + p.P + kChunkH - 1) / kChunkH * kChunkH;
+    p.nybe = (H + p.P + kYB - 1) / kYB;
+    p.nyb = (H + kYB - 1) / kYB;
+    p.cB = (float)pl->rg[0];
+    p.cD1 = (float)(pl->rg[2] + pl->rg[3]);
+    p.cD2 = (float)pl->rg[3];
+    const size_t fplane = blocked_plane(H, W);
+    p.Vt = reinterpret_cast<float *>(base);
+    p.Acc = p.Vt + (size_t)gv_max * 2 * rg_plane(pl, H, W) * 2;
+    float *ft = p.Acc + (size_t)2 * n_slots * fplane;
+    p.ft = ft;
+    LrParams lp{};  // for the shared transpose and final kernels
+    lp.in_stride = img.in_row_stride;
+    lp.dtype = img.dtype;
+    lp.in_px = img.in_px;
+    lp.H = H;
+    lp.W = W;
+    lp.ft = ft;
+    auto kv = img.dtype == 0 ? rg_vert<0> : rg_vert<1>;
+    auto kt = img.dtype == 0 ? lr_transpose<0> : lr_transpose<1>;
+    const int ncb = (W + kVCols - 1) / kVCols;
+    const int esz = img.dtype == 0 ? 4 : 1;
+    for (int ch = 0; ch < img.C; ++ch) {
+        p.in = reinterpret_cast<const char *>(img.in) + (long long)ch * img.in_z * esz;
+        lp.in = p.in;
+        dim3 gt((W + 31) / 32, (H + 31) / 32);
+        kt<<<gt, dim3(32, 8), 0, s>>>(lp);
+        for (int m0 = 0; m0 < nt; m0 += gv_max) {
+            const int nv = std::min(gv_max, nt - m0);
+            p.n_terms = nv;
+            for (int g = 0; g < kVMax; ++g) {
+                const int m = m0 + std::min(g, nv - 1);
+                p.tv[g] = pl->turns32[m];
+                p.ah[g] = pl->a32[m];
+            }
+            p.first = m0 == 0;
+            dim3 gv(ncb, 1, (nv + kVB - 1) / kVB);
+            kv<<<gv, kVCols * kVB, 0, s>>>(p);
+            dim3 gh((p.nyb + 1) / 2, 1, (nv + kHT - 1) / kHT);
+            rg_horz<<<gh, 64 * kHT, 0, s>>>(p);
         }
         dim3 gf((W + 31) / 32, (H + 31) / 32);
         lr_final<<<gf, dim3(32, 8), 0, s>>>(

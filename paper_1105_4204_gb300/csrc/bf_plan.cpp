@@ -56,6 +56,37 @@ std::vector<double> binomial_weights(int N) {
 // deletes the plan.
 static bf_status set_spatial(bf_plan *p, double sigma_s, bf_spatial_kind kind,
                              const bf_plan_opts &o, const std::string &who) {
+    if (kind == BF_SPATIAL_GAUSS_RECURSIVE) {
+        // Young and van Vliet (1995), published design (valid for sigma >= 0.5)
+        if (sigma_s < 0.5 || sigma_s > 256.0)
+            return bf::fail(BF_EUNSUPPORTED, who + ": the recursive Gaussian takes "
+                                                   "0.5 <= sigma_s <= 256");
+        if (o.radius_override != 0 || o.box_passes != 0)
+            return bf::fail(BF_EINVAL, who + ": radius and passes do not apply to the "
+                                             "recursive Gaussian");
+        const double q = sigma_s >= 2.5 ? 0.98711 * sigma_s - 0.96330
+                                        : 3.97156 - 4.14554 * std::sqrt(1.0 - 0.26891 * sigma_s);
+        const double q2 = q * q, q3 = q2 * q;
+        const double b0 = 1.57825 + 2.44413 * q + 1.4281 * q2 + 0.422205 * q3;
+        const double b1 = 2.44413 * q + 2.85619 * q2 + 1.26661 * q3;
+        const double b2 = -(1.4281 * q2 + 1.26661 * q3);
+        const double b3 = 0.422205 * q3;
+        p->rg[0] = 1.0 - (b1 + b2 + b3) / b0;
+        p->rg[1] = b1 / b0;
+        p->rg[2] = b2 / b0;
+        p->rg[3] = b3 / b0;
+        p->rg_P = (int)std::ceil(6.0 * sigma_s);
+        p->R = p->rg_P;
+        // standard deviation of the cascade's impulse response, from the
+        // cumulants of the causal part: mean S'/B, variance S''/B + (S'/B)^2
+        // with S' = sum k a_k, S'' = sum k^2 a_k, doubled for the cascade
+        const double s1 = p->rg[1] + 2 * p->rg[2] + 3 * p->rg[3];
+        const double s2 = p->rg[1] + 4 * p->rg[2] + 9 * p->rg[3];
+        const double B = p->rg[0];
+        p->achieved_sigma = std::sqrt(2.0 * (s2 / B + (s1 / B) * (s1 / B)));
+        p->q_scale = 1.f;
+        return BF_OK;
+    }
     if (kind == BF_SPATIAL_GAUSS_TRUNC) {
         int R = o.radius_override > 0 ? o.radius_override : (int)std::ceil(3.0 * sigma_s);
         if (R > BF_MAX_TAPS_R) {
@@ -138,7 +169,8 @@ extern "C" bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_
         return bf::fail(BF_EINVAL, "bf_plan_create: sigma_r must be finite and > 0");
     if (!(T > 0) || !std::isfinite(T))
         return bf::fail(BF_EINVAL, "bf_plan_create: T must be finite and > 0");
-    if (kind != BF_SPATIAL_GAUSS_TRUNC && kind != BF_SPATIAL_BOX_ITER)
+    if (kind != BF_SPATIAL_GAUSS_TRUNC && kind != BF_SPATIAL_BOX_ITER &&
+        kind != BF_SPATIAL_GAUSS_RECURSIVE)
         return bf::fail(BF_EINVAL, "bf_plan_create: unknown spatial kind");
     bf_plan_opts o{};
     if (opts) o = *opts;
@@ -212,7 +244,8 @@ extern "C" bf_status bf_plan_create_cosine(bf_plan **out, double sigma_s, double
         return bf::fail(BF_EUNSUPPORTED, who + ": degree above " + std::to_string(BF_MAX_N));
     for (int n = 0; n < n_coef; ++n)
         if (!std::isfinite(a[n])) return bf::fail(BF_EINVAL, who + ": non-finite coefficient");
-    if (kind != BF_SPATIAL_GAUSS_TRUNC && kind != BF_SPATIAL_BOX_ITER)
+    if (kind != BF_SPATIAL_GAUSS_TRUNC && kind != BF_SPATIAL_BOX_ITER &&
+        kind != BF_SPATIAL_GAUSS_RECURSIVE)
         return bf::fail(BF_EINVAL, who + ": unknown spatial kind");
     bf_plan_opts o{};
     if (opts) o = *opts;

@@ -213,3 +213,24 @@ def test_size_limits_are_checked_on_the_host(bf):
     assert l.bf_forward(p.handle, fake, 0, fake, H, W, 1, W, null, null) == 2
     assert b"too large" in l.bf_last_error()
     assert l.bf_backward(p.handle, fake, fake, fake, fake, fake, null, H, W, null, 0, null) == 2
+
+
+def test_recursive_gaussian_plan(bf, oracle):
+    # radius reports the extension P = ceil(6 sigma_s); achieved sigma is the cascade's
+    # (closed form from the coefficients), equal to the oracle's measured impulse response
+    for ss in (0.5, 2.4, 2.5, 10.0, 100.0):
+        p = bf.Plan(ss, 30.0, kind="recursive")
+        assert p.radius == math.ceil(6 * ss) and p.N == 30
+        n = int(40 * ss) + 81
+        x = np.zeros((1, n))
+        x[0, n // 2] = 1.0
+        y = oracle.rg_filter(x, ss)[0]
+        k = np.arange(n) - n // 2
+        assert p.achieved_sigma_s == pytest.approx(math.sqrt((y * k * k).sum()), rel=1e-5)
+    from paper_1105_4204_gb300._lib import BfError
+    with pytest.raises(BfError) as e:
+        bf.Plan(0.4, 30.0, kind="recursive")
+    assert e.value.status == 2
+    with pytest.raises(BfError) as e:
+        bf.Plan(3.0, 30.0, kind="recursive", radius=5)
+    assert e.value.status == 1

@@ -338,3 +338,70 @@ def test_cosine_kernel_gradient(oracle):
     g2 = oracle.bf_grad_cos(f, u, gam2, a2, w1=w1)
     g3, _ = oracle.bf_grad(f, u, sigma_r=sr, N=N, w1=w1)
     np.testing.assert_allclose(g2, g3, atol=1e-10 * np.abs(g3).max())
+
+
+# ------------------------------------------------ recursive Gaussian (Section 3)
+
+def _impulse_response(oracle, sigma, n=None):
+    n = n or int(24 * sigma) + 61
+    x = np.zeros((1, n))
+    x[0, n // 2] = 1.0
+    return oracle.rg_filter(x, sigma)[0], np.arange(n) - n // 2
+
+
+@pytest.mark.parametrize("sigma,bound", [(0.5, 0.08), (1.0, 0.10), (3.0, 0.05), (10.0, 0.025),
+                                         (50.0, 0.025)])
+def test_recursive_gaussian_approximates_the_gaussian(oracle, sigma, bound):
+    # unit mass, symmetric, and within a few percent of the sampled Gaussian of the same
+    # sigma (the third-order recursion approximates it; its tails are heavier)
+    y, k = _impulse_response(oracle, sigma)
+    g = np.exp(-k * k / (2 * sigma * sigma))
+    g /= g.sum()
+    assert abs(y.sum() - 1.0) < 1e-5
+    np.testing.assert_allclose(y, y[::-1], atol=1e-12)
+    assert np.abs(y - g).max() <= bound * g.max()
+    assert int(np.argmax(y)) == len(y) // 2
+
+
+def test_recursive_gaussian_variance_closed_form(oracle):
+    # the cascade's variance from the cumulants of the causal recursion
+    # (2 (S''/B + (S'/B)^2), S' = sum k a_k, S'' = sum k^2 a_k) equals the measured one
+    for sigma in (0.7, 2.0, 6.0, 20.0):
+        c, _ = oracle.rg_coefs(sigma)
+        B, a = c[0], c[1:]
+        kk = np.array([1.0, 2.0, 3.0])
+        var = 2 * ((kk * kk * a).sum() / B + ((kk * a).sum() / B) ** 2)
+        y, k = _impulse_response(oracle, sigma, int(40 * sigma) + 81)
+        assert (y * k * k).sum() == pytest.approx(var, rel=1e-6)
+        assert c.sum() == pytest.approx(1.0, abs=1e-12)
+
+
+def test_recursive_gaussian_borders(oracle):
+    # constant rows and columns stay constant (unit gain, steady-state starts); a signal
+    # that is constant near the first sample is filtered there as if extended forever
+    f = np.full((7, 40), 42.0)
+    np.testing.assert_allclose(oracle.rg_filter(f, 3.0), 42.0, atol=1e-9)
+    x = np.concatenate([np.full(60, 10.0), np.linspace(10, 200, 40)])[None, :]
+    ext = np.concatenate([np.full(300, 10.0), x[0]])[None, :]
+    np.testing.assert_allclose(oracle.rg_filter(x, 4.0)[0, :30], oracle.rg_filter(ext, 4.0)[0, 300:330],
+                               atol=1e-9)
+
+
+def test_algorithm1_with_the_recursive_filter(oracle):
+    # sigma_r -> infinity: the bilateral filter is the spatial averaging itself; and in the
+    # interior, Algorithm 1 with the recursive filter equals eq. (BF) with the recursive
+    # filter's impulse response as w (a separable kernel there)
+    f = synth.rectangles(70, 80, n_rect=6, noise=6.0, seed=2).astype(np.float64)
+    np.testing.assert_allclose(oracle.bf_trig_rg(f, sigma_s=2.0, sigma_r=1e9, N=1),
+                               oracle.rg_filter(f, 2.0), atol=1e-8)
+    sigma = 1.5
+    y, k = _impulse_response(oracle, sigma, 161)
+    keep = np.abs(y) > 1e-13 * y.max()
+    w1 = y[keep] / y[keep].sum()
+    R = (len(w1) - 1) // 2
+    assert R < 40
+    f = synth.rectangles(120, 130, n_rect=8, noise=6.0, seed=4).astype(np.float64)
+    out = oracle.bf_trig_rg(f, sigma_s=sigma, sigma_r=30.0)
+    idx = [i * 130 + j for i in range(R, 120 - R, 3) for j in range(R, 130 - R, 3)]
+    ref = oracle.bf_brute_at(f, idx, sigma_r=30.0, w1=w1)
+    np.testing.assert_allclose(out.ravel()[idx], ref, atol=1e-6)
