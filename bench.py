@@ -371,6 +371,7 @@ def run_ours(args):
         extras.update(measure_fwd_bwd(bf, torch, dev, stream))
         extras.update(measure_batch(bf, torch, dev, stream))
         extras.update(measure_configs(bf, torch, dev, stream))
+        extras.update(measure_table2(bf, torch, dev, stream))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,6 +483,35 @@ def measure_configs(bf, torch, dev, stream):
     return {"configs": res}
 
 
+# Table 2 of the paper: ms per 720 x 540 grayscale image with the recursive
+# Gaussian spatial filter, Java ImageJ plugin on a 2 x quad-core 2.66 GHz
+# Mac OS X machine, multithreaded (context for the rates here, not a target).
+PAPER_TABLE2_MS = {
+    10.0: [3604, 452, 195, 120, 74, 61, 49, 34, 32, 27],
+    100.0: [3755, 482, 217, 127, 89, 69, 54, 43, 37, 28],
+}
+TABLE2_SIGMA_R = [10.0, 20.0, 30.0, 40.0, 50.0, 60.0, 70.0, 80.0, 90.0, 100.0]
+
+
+def measure_table2(bf, torch, dev, stream):
+    """The paper's timing workload (Table 2): a 720 x 540 grayscale image
+    (synthetic stand-in: rectangles + noise 10), recursive Gaussian spatial
+    filter sigma_s = 10 and 100, sigma_r = 10 ... 100 (T = 255, N from the
+    rule); ms per image on one GB300 beside the paper's CPU times."""
+    import synth
+    img = torch.from_numpy(synth.rectangles(540, 720, n_rect=20, noise=10.0, seed=0)).to(dev)
+    out = torch.empty_like(img)
+    res = {}
+    for ss, paper in PAPER_TABLE2_MS.items():
+        row = {}
+        for sr, pm in zip(TABLE2_SIGMA_R, paper):
+            p = bf.Plan(ss, sr, 255.0, kind="recursive")
+            ms = _time(lambda: bf.forward(p, img, out=out), torch, stream, 5)
+            row["sigma_r=%g" % sr] = {"N": p.N, "ms": ms, "paper_ms": pm, "speedup": pm / ms}
+        res["sigma_s=%g" % ss] = row
+    return {"paper_table2_720x540_recursive_gauss": res}
+
+
 def measure_batch(bf, torch, dev, stream):
     """Batched workload: 64 images, W ~ U[128,1920], H ~ U[128,1080], box
     sigma_s ~ U[2,16], sigma_r ~ U[15,60]; one persistent launch replayed from
@@ -520,7 +550,8 @@ def run_extras_only(which):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    fn = {"fwd_bwd": measure_fwd_bwd, "batch": measure_batch, "configs": measure_configs}[which]
+    fn = {"fwd_bwd": measure_fwd_bwd, "batch": measure_batch, "configs": measure_configs,
+          "table2": measure_table2}[which]
     print(json.dumps({"extras_only": which, **fn(bf, torch, dev, stream)}), flush=True)
     return 0
 
@@ -536,7 +567,8 @@ def main():
                     help="skip the unfused baseline and the other workloads")
     ap.add_argument("--sigma-s", default=None,
                     help="comma-separated subset of the workload's sigma_s values (profiling runs)")
-    ap.add_argument("--extras-only", choices=["fwd_bwd", "batch", "configs"], default=None,
+    ap.add_argument("--extras-only", choices=["fwd_bwd", "batch", "configs", "table2"],
+                    default=None,
                     help="time only that extra workload and print its figures (profiling runs; "
                          "not the benchmark line)")
     args = ap.parse_args()

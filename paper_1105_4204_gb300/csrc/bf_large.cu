@@ -613,9 +613,9 @@ __global__ void __launch_bounds__(kVCols * kVB) rg_vert(const __grid_constant__ 
         t2[q] = t3[q] = make_float2(0.f, 0.f);
     }
     if (!col_ok) return;
-    for (int e0 = (E - 1) / kChunk * kChunk; e0 >= 0; e0 -= kChunk) {
-        float2 *dc = dst + blocked_at(p.We, x, e0);
-        float2 wv[2][kChunk];
+    // the chunk at e0 of both pairs (rows e0 .. e0+7 are contiguous)
+    auto load_chunk = [&](int e0, float2 (&wv)[2][kChunk]) {
+        const float2 *dc = dst + blocked_at(p.We, x, e0);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const float4 *s4 = reinterpret_cast<const float4 *>(dc + q * plane);
@@ -626,6 +626,12 @@ __global__ void __launch_bounds__(kVCols * kVB) rg_vert(const __grid_constant__ 
                 wv[q][2 * k + 1] = make_float2(v.z, v.w);
             }
         }
+    };
+    float2 wv[2][kChunk], nv[2][kChunk];
+    const int e_top = (E - 1) / kChunk * kChunk;
+    load_chunk(e_top, wv);
+    for (int e0 = e_top; e0 >= 0; e0 -= kChunk) {
+        if (e0 >= kChunk) load_chunk(e0 - kChunk, nv);  // next chunk, issued ahead
 #pragma unroll
         for (int d = kChunk - 1; d >= 0; --d) {
             if (e0 + d < E) {
@@ -635,6 +641,7 @@ __global__ void __launch_bounds__(kVCols * kVB) rg_vert(const __grid_constant__ 
                 wv[1][d] = t1[1];
             }
         }
+        float2 *dc = dst + blocked_at(p.We, x, e0);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             float4 *d4 = reinterpret_cast<float4 *>(dc + q * plane);
@@ -643,6 +650,10 @@ __global__ void __launch_bounds__(kVCols * kVB) rg_vert(const __grid_constant__ 
                 d4[k] = make_float4(wv[q][2 * k].x, wv[q][2 * k].y, wv[q][2 * k + 1].x,
                                     wv[q][2 * k + 1].y);
         }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int d = 0; d < kChunk; ++d) wv[q][d] = nv[q][d];
     }
 }
 
@@ -698,20 +709,32 @@ __global__ void __launch_bounds__(64 * kHT) rg_horz(const __grid_constant__ RgPa
     // anticausal, columns E-1 .. 0, combining at the image's columns
     float2 t1 = s1, t2 = make_float2(0.f, 0.f), t3 = t2;
     int buf = 0;
-    for (int e0 = (E - 1) / kChunkH * kChunkH; e0 >= 0; e0 -= kChunkH) {
-        float2 wv[kChunkH];
-        float cf[kChunkH];
+    auto load_back = [&](int e0, float2 (&wv)[kChunkH], float (&cf)[kChunkH]) {
 #pragma unroll
         for (int d = 0; d < kChunkH; ++d) {
             const int e = e0 + d;
             wv[d] = e < E ? V[(size_t)e * kYB] : make_float2(0.f, 0.f);
             cf[d] = __ldg(F + (size_t)min(e, W - 1) * kYB);
         }
+    };
+    float2 wv[kChunkH], nwv[kChunkH];
+    float cf[kChunkH], ncf[kChunkH];
+    const int e_top = (E - 1) / kChunkH * kChunkH;
+    load_back(e_top, wv, cf);
+    for (int e0 = e_top; e0 >= 0; e0 -= kChunkH) {
+        if (e0 >= kChunkH) load_back(e0 - kChunkH, nwv, ncf);  // next chunk, issued ahead
 #pragma unroll
         for (int d = kChunkH - 1; d >= 0; --d) {
             if (e0 + d < E) wv[d] = rg_step1(cB, cD1, cD2, wv[d], t1, t2, t3);
         }
-        if (e0 >= W) continue;  // extension only: no outputs (uniform)
+        if (e0 >= W) {  // extension only: no outputs (uniform)
+#pragma unroll
+            for (int d = 0; d < kChunkH; ++d) {
+                wv[d] = nwv[d];
+                cf[d] = ncf[d];
+            }
+            continue;
+        }
 #pragma unroll
         for (int d = 0; d < kChunkH; ++d) {
             float rr = tm * cf[d];
@@ -739,6 +762,11 @@ __global__ void __launch_bounds__(64 * kHT) rg_horz(const __grid_constant__ RgPa
             }
         }
         buf ^= 1;
+#pragma unroll
+        for (int d = 0; d < kChunkH; ++d) {
+            wv[d] = nwv[d];
+            cf[d] = ncf[d];
+        }
     }
 }
 
