@@ -128,8 +128,10 @@ void bf_plan_destroy(bf_plan *plan);
  *                      frequencies whose FP32 weight is not 0, plus one for
  *                      the constant term when N is even
  *   radius           : support half-width of the 2-D spatial kernel per axis
- *                      (R for the Gaussian, box_passes*r for the box)
+ *                      (R for the Gaussian, box_passes*r for the box; for the
+ *                      recursive Gaussian the extension P past the last sample)
  *   achieved_sigma_s : standard deviation of the 1-D spatial kernel in use
+ *                      (for the recursive Gaussian: of its impulse response)
  */
 bf_status bf_plan_info(const bf_plan *plan, int *N, int *n_freq, int *radius,
                        double *achieved_sigma_s);
@@ -165,10 +167,12 @@ bf_status bf_plan_weights(const bf_plan *plan, double *w1, int cap, int *count);
  * the box with r <= 8.  For the box with 8 < r <= 64 the support does not fit
  * on chip and the filter runs as streaming sweeps (vertical, then horizontal)
  * through a scratch buffer of about (4 * terms + 2 * ceil(terms / 4) + 1) * H * W
- * floats (terms capped so that the vertical sweep's output stays within 4 GiB) that the
- * library allocates on the current device the first time it is needed,
- * and keeps for reuse until bf_release_scratch().  The first such call on a
- * device must therefore not happen during stream capture.
+ * floats (terms capped so that the vertical sweep's output stays within
+ * 4 GiB); the recursive Gaussian streams the same way through about
+ * 4 * terms * (H + P) * (W + P) floats.  The library allocates the scratch on
+ * the current device the first time it is needed and keeps it for reuse
+ * until bf_release_scratch(); the first such call on a device must therefore
+ * not happen during stream capture.
  * Errors: BF_EINVAL (NULL pointers, sizes), BF_EUNSUPPORTED (C > 4),
  *         BF_ENOMEM (scratch allocation), BF_ECUDA (launch failure).
  */

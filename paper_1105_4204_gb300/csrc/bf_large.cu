@@ -1,8 +1,11 @@
-// Forward filter for the 3-pass box at large half-widths r (support 3r > 24).
+// Streaming forward filters: the 3-pass box at large half-widths r (support
+// 3r > 24) and, further down, the recursive Gaussian (rg_*), which share the
+// blocked layout, the transpose, the horizontal warp layout with its on-chip
+// term reduction, and the final division.
 //
-// A tile plus a 3r halo no longer fits on chip, so the separable filter is
-// run as two streaming sweeps, the terms' filtered auxiliary images passing
-// through device memory once:
+// Large box.  A tile plus a 3r halo no longer fits on chip, so the separable
+// filter is run as two streaming sweeps, the terms' filtered auxiliary images
+// passing through device memory once:
 //
 //   lr_vert : one thread per image column and term (four terms per block,
 //             sharing a ring of f; all terms in one launch while their planes
