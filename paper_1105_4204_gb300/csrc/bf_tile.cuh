@@ -45,56 +45,6 @@ __device__ __forceinline__ float sin_turns(float r) {
     return __sinf(kTwoPi * r);
 }
 
-// ---- 1-D filters on register arrays (all indices compile-time) -------------
-
-template <int R, int NIN>
-__device__ __forceinline__ void gauss_taps(const float (&x)[NIN], float (&y)[NIN - 2 * R],
-                                           const float *__restrict__ w) {
-#pragma unroll
-    for (int i = 0; i < NIN - 2 * R; ++i) {
-        float acc = w[0] * x[i];
-#pragma unroll
-        for (int d = 1; d <= 2 * R; ++d) acc = fmaf(w[d], x[i + d], acc);
-        y[i] = acc;
-    }
-}
-
-template <int r, int NIN>
-__device__ __forceinline__ void box_pass(const float (&x)[NIN], float (&y)[NIN - 2 * r]) {
-    float s = x[0];
-#pragma unroll
-    for (int d = 1; d <= 2 * r; ++d) s += x[d];
-    y[0] = s;
-#pragma unroll
-    for (int i = 1; i < NIN - 2 * r; ++i) {
-        s += x[i + 2 * r] - x[i - 1];
-        y[i] = s;
-    }
-}
-
-template <int r, int NIN>
-__device__ __forceinline__ void box3(const float (&x)[NIN], float (&y)[NIN - 6 * r]) {
-    float t1[NIN - 2 * r];
-    float t2[NIN - 4 * r];
-    box_pass<r, NIN>(x, t1);
-    box_pass<r, NIN - 2 * r>(t1, t2);
-    box_pass<r, NIN - 4 * r>(t2, y);
-}
-
-template <int KIND, int RAD, int NIN>
-struct Filt {
-    static constexpr int HALO = KIND == 0 ? RAD : 3 * RAD;
-    static constexpr int NOUT = NIN - 2 * HALO;
-    __device__ __forceinline__ static void run(const float (&x)[NIN], float (&y)[NOUT],
-                                               const float *__restrict__ w) {
-        if constexpr (KIND == 0) {
-            gauss_taps<RAD, NIN>(x, y, w);
-        } else {
-            box3<RAD, NIN>(x, y);
-        }
-    }
-};
-
 // ---- paired FP32 arithmetic (sm_100+: one instruction, two lanes of work) --
 //
 // The four auxiliary images of a term are filtered in pairs: (x, f x) in the
