@@ -74,13 +74,18 @@ struct LrParams {
     int first;            // lr_horz: first launch of the channel (the slots start from zero)
 };
 
+// lr_vert / rg_vert: steps between barriers / whose loads are issued together
+// (a divisor of the 16-row blocks; 16 measured slower: fewer resident blocks)
+constexpr int kChunk = 8;
+static_assert(16 % kChunk == 0, "chunks must not straddle row blocks");
+
 // Power-of-two size of lr_vert's shared f ring (which has kChunk more slots
 // mirroring its first kChunk): the 3L + 1 values a stream needs, plus slack for the warps sharing it to be up to two chunks apart
 // (they meet at a barrier every chunk) without overwriting a value another
 // warp still has to read.
 __host__ __device__ __forceinline__ int ring_size(int r) {
     int n = 1;
-    while (n < 3 * (2 * r + 1) + 1 + 16) n <<= 1;
+    while (n < 3 * (2 * r + 1) + 1 + 2 * kChunk) n <<= 1;
     return n;
 }
 
@@ -109,7 +114,6 @@ __device__ __forceinline__ float load_px(const LrParams &p, int y, int x) {
 }
 
 constexpr int kVCols = 32;    // lr_vert: columns per block
-constexpr int kChunk = 8;     // lr_vert: steps between barriers / whose loads are issued together
 
 // The four auxiliary planes of one pixel value (cos, sin, f cos, f sin).
 // The products are rounded explicitly (__fmul_rn is never fused into an
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(kVCols * kVB) lr_vert(const __grid_constant__ 
 #pragma unroll
         for (int d = 0; d < kChunk; ++d)
             nxt[d] = load_px<DT>(p, min(max(e0 + kChunk + d, 0), p.H - 1), xc);
-        const int tb = e0 - 3 * r;  // output row of step d = 0 (tb - y0 is a multiple of 8)
+        const int tb = e0 - 3 * r;  // output row of step d = 0 (tb - y0 is a multiple of kChunk)
         const bool fast = e0 >= p0 + 3 * L && e0 + kChunk <= e_end;  // uniform
         if (fast) {
             r1 = ring + ((e0 - L) & M) * kVCols;
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(kVCols * kVB) lr_vert(const __grid_constant__ 
                 if (e0 + d < e_end) step(e0 + d, d, std::true_type{});
         }
         if (col_ok && tb >= y0) {
-            // tb is a multiple of 8: the chunk's rows lie in one row block
+            // tb is a multiple of kChunk: the chunk's rows lie in one row block
             float2 *dc = dst + blocked_at(p.W, xb + col, tb);
             if (tb + kChunk <= y1) {
 #pragma unroll
@@ -836,14 +840,14 @@ cudaError_t launch_large_box(const bf_plan *pl, const BfImage &img, void *ws, cu
     if (e != cudaSuccess) return e;
     const int resident_vert = std::max(1, n_sm * per_sm);
 
-    // lr_vert's bands (multiples of 8 rows): as many as one wave of resident
+    // lr_vert's bands (multiples of kChunk rows): as many as one wave of resident
     // blocks holds (a partial second wave costs a whole band's time), at
     // least 12r long (the 6r warm-up at most half a band).
     const int min_band = 12 * p.r;
     const int ncb = (W + kVCols - 1) / kVCols;
     const int zb_max = (gv_max + kVB - 1) / kVB;
     const int nbh_max = std::max(1, std::min(resident_vert / (ncb * zb_max), H / min_band));
-    p.band_h = ((H + nbh_max - 1) / nbh_max + 7) / 8 * 8;
+    p.band_h = ((H + nbh_max - 1) / nbh_max + kChunk - 1) / kChunk * kChunk;
     const int nbh = (H + p.band_h - 1) / p.band_h;
     const int nyb2 = (p.nyb + 1) / 2;
     // lr_horz: resident blocks as many as fit the SMs -- for large r (the

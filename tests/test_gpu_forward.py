@@ -391,3 +391,14 @@ def test_largest_accepted_image(bf, oracle):
         assert abs(float(out[i, j]) - ref[0]) <= TOL, (i, j)
     del img, out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("kind,ss,rad", [("box", 12.0, 12), ("box", 32.0, 32), ("recursive", 5.0, 0)])
+def test_streaming_paths_are_deterministic(bf, kind, ss, rad):
+    # the streaming sweeps sum their terms in a fixed order (on chip, then slot by slot):
+    # repeated calls give the same bits
+    img = synth.smooth_field(150, 170, noise=5.0, seed=9)
+    plan = bf.Plan(ss, 20.0, kind=kind, radius=rad)
+    a = _run(bf, img, plan)
+    b = _run(bf, img, plan)
+    np.testing.assert_array_equal(a, b)
