@@ -402,3 +402,20 @@ def test_streaming_paths_are_deterministic(bf, kind, ss, rad):
     a = _run(bf, img, plan)
     b = _run(bf, img, plan)
     np.testing.assert_array_equal(a, b)
+
+
+def test_prefetching_horizontal_sweep_with_two_vertical_rounds(bf, oracle):
+    # r = 32 on a full-size image takes the prefetching, L2-capped horizontal sweep; N = 200
+    # makes its second round add to the slots the first one wrote.  Sampled pixels.
+    N = 200
+    sigma_r = 1.001 * 2 * 255.0 / (np.pi * np.sqrt(N))
+    img = synth.smooth_field(2048, 2048, noise=5.0, seed=6)
+    plan = bf.Plan(32.0, sigma_r, kind="box", radius=32, N=N)
+    assert plan.n_terms > 64
+    out = _run(bf, img, plan)
+    idx = synth.sample_indices(2048, 2048, 256, seed=8)[::8]
+    ref = oracle.bf_brute_at(img.astype(np.float64), idx, sigma_r=sigma_r, w1=plan_w1(oracle, plan),
+                             N=N)
+    err = np.abs(out.ravel()[idx] - ref).max()
+    print("r=32 N=200 max abs err %.3e on %d px" % (err, len(idx)))
+    assert err <= TOL
