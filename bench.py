@@ -429,14 +429,19 @@ def measure_fwd_bwd(bf, torch, dev, stream):
         fwd()
         bf.backward_stack(plan, imgs, outs, qs, u, grad_in=grads, workspace=ws)
 
+    def fwd_bwd_df_only():
+        fwd()
+        bf.backward_stack(plan, imgs, outs, qs, u, need_sigma=False, grad_in=grads)
+
     t_f = _time(fwd, torch, stream, 5)
     t_fb = _time(fwd_bwd, torch, stream, 5)
+    t_fbd = _time(fwd_bwd_df_only, torch, stream, 5)
     px = B * HH * WW
     a, w = plan.terms()
     nz = int(np.sum(w > 0))
     return {"fwd_bwd_config": "16 x 512^2, gauss sigma_s=4 (R=12), sigma_r=25 (N=43)",
             "fwd_mpx_s": px / (t_f * 1e-3) / 1e6, "fwd_bwd_mpx_s": px / (t_fb * 1e-3) / 1e6,
-            "fwd_ms": t_f, "fwd_bwd_ms": t_fb,
+            "fwd_ms": t_f, "fwd_bwd_ms": t_fb, "fwd_bwd_image_gradient_only_ms": t_fbd,
             "fwd_instr_per_px": gauss_instr_per_px(nz, bool(np.any(w == 0)), 12)}
 
 

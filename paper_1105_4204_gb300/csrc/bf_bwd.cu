@@ -6,9 +6,11 @@
 
 namespace bf {
 
+// Box instantiations live in bf_bwd_box.cu (compiled in parallel).
+cudaError_t launch_bwd_box(int r, const BwdParams &prm, int count, cudaStream_t s);
+
 namespace {
 
-constexpr int kBwdTH = 32, kBwdTW = 64, kBwdTWT = 8;
 
 // One block sums the partials in a fixed order (per-thread strided sums, then
 // a tree), so repeated runs give the same bits.
@@ -104,17 +106,7 @@ cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, c
             default: return cudaErrorInvalidValue;
         }
     } else {
-        switch (pl->r_box) {
-            case 1: e = launch_bwd<1, 1, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
-            case 2: e = launch_bwd<1, 2, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
-            case 3: e = launch_bwd<1, 3, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
-            case 4: e = launch_bwd<1, 4, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
-            case 5: e = launch_bwd<1, 5, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
-            case 6: e = launch_bwd<1, 6, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
-            case 7: e = launch_bwd<1, 7, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
-            case 8: e = launch_bwd<1, 8, kBwdTH, kBwdTW, kBwdTWT>(prm, count, s); break;
-            default: return cudaErrorInvalidValue;
-        }
+        e = launch_bwd_box(pl->r_box, prm, count, s);
     }
     if (e != cudaSuccess) return e;
     if (grad_sigma_r) {

@@ -30,6 +30,8 @@
 
 namespace bf {
 
+constexpr int kBwdTH = 32, kBwdTW = 64, kBwdTWT = 8;  // backward tile and segment
+
 struct BwdParams {
     const float *f, *o, *q, *u;
     float *grad;         // dL/df, H x W per image; blockIdx.z selects the image of a stack
@@ -72,7 +74,9 @@ struct BwdGeom {
     static_assert(2 * EW <= NT, "one phase-1 item per thread");
 };
 
-template <int KIND, int RAD, int TH, int TW, int TWT>
+// SIG: dL/dsigma_r requested.  Without it the f^2 planes, which only that
+// derivative needs, are neither filtered nor combined.
+template <int KIND, int RAD, int TH, int TW, int TWT, bool SIG>
 __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
     bf_tile_bwd(const __grid_constant__ BwdParams p) {
     using G = BwdGeom<KIND, RAD, TH, TW, TWT>;
@@ -160,7 +164,21 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
                 fv = fcol[i * G::SF];
                 return sin_turns(fmaf(tm, fv, ph0));
             };
-            if constexpr (kOneSweep) {
+            if constexpr (!SIG) {
+                // dL/df only: (x, f x)
+                auto gen = [&](int i) {
+                    float fv;
+                    const float x = gen_x(i, fv);
+                    if (i >= HALO && i < HALO + TH && own_col) ccol[(i - HALO) * 2 * SC2] = x;
+                    return make_float2(x, x * fv);
+                };
+                auto sink = [&](int k, float2 y) {
+                    v0[k * 2 * SV2] = y.x;
+                    v0[(TH + k) * 2 * SV2] = y.y;
+                };
+                Ahead<kGenAhead, EH, decltype(gen)> ahead(gen);
+                filt2_stream<KIND, RAD, EH>(ahead, sink, p.taps.w2);
+            } else if constexpr (kOneSweep) {
                 // (x, f x) and (f^2 x, 0) of one generated x in one sweep
                 auto gen = [&](int i) {
                     float fv;
@@ -220,18 +238,24 @@ __global__ void __launch_bounds__(BwdGeom<KIND, RAD, TH, TW, TWT>::NT)
             // (W[c], W[s])
             hpass(0, [&](int k, float2 z) {
                 gacc[k] = fmaf(ks[k] * op[k], z.x, fmaf(-kc[k] * op[k], z.y, gacc[k]));
-                sacc[k] = fmaf(-ks[k] * fp[k] * op[k], z.x, fmaf(kc[k] * fp[k] * op[k], z.y, sacc[k]));
+                if constexpr (SIG)
+                    sacc[k] = fmaf(-ks[k] * fp[k] * op[k], z.x,
+                                   fmaf(kc[k] * fp[k] * op[k], z.y, sacc[k]));
             });
             // (W[f c], W[f s])
             hpass(1, [&](int k, float2 z) {
                 gacc[k] = fmaf(-ks[k], z.x, fmaf(kc[k], z.y, gacc[k]));
-                const float fo = fp[k] + op[k];
-                sacc[k] = fmaf(ks[k] * fo, z.x, fmaf(-kc[k] * fo, z.y, sacc[k]));
+                if constexpr (SIG) {
+                    const float fo = fp[k] + op[k];
+                    sacc[k] = fmaf(ks[k] * fo, z.x, fmaf(-kc[k] * fo, z.y, sacc[k]));
+                }
             });
             // (W[f^2 c], W[f^2 s])
-            hpass(2, [&](int k, float2 z) {
-                sacc[k] = fmaf(-ks[k], z.x, fmaf(kc[k], z.y, sacc[k]));
-            });
+            if constexpr (SIG) {
+                hpass(2, [&](int k, float2 z) {
+                    sacc[k] = fmaf(-ks[k], z.x, fmaf(kc[k], z.y, sacc[k]));
+                });
+            }
         }
         // ================= round B: W^T of (alpha c, alpha s), (alpha o c, alpha o s)
         __syncthreads();
@@ -361,14 +385,19 @@ cudaError_t launch_bwd(const BwdParams &prm, int count, cudaStream_t s) {
     using G = BwdGeom<KIND, RAD, TH, TW, TWT>;
     static_assert(G::SMEM <= 227 * 1024, "shared memory");
     static_assert((G::NT & (G::NT - 1)) == 0, "reduction needs a power-of-two block");
-    auto kern = bf_tile_bwd<KIND, RAD, TH, TW, TWT>;
+    auto kern = prm.partials ? bf_tile_bwd<KIND, RAD, TH, TW, TWT, true>
+                             : bf_tile_bwd<KIND, RAD, TH, TW, TWT, false>;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-        if (e != cudaSuccess) return e;
+        for (auto k : {bf_tile_bwd<KIND, RAD, TH, TW, TWT, true>,
+                       bf_tile_bwd<KIND, RAD, TH, TW, TWT, false>}) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)G::SMEM);
+            if (e != cudaSuccess) return e;
+        }
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     dim3 grid((prm.W + TW - 1) / TW, (prm.H + TH - 1) / TH, count);

@@ -162,3 +162,19 @@ def test_stack_calls_match_per_image_calls(bf):
             torch.testing.assert_close(g[b], gb, rtol=0, atol=0)
             total += float(gsb)
         assert float(gs) == pytest.approx(total, rel=1e-9, abs=1e-12)
+
+
+@pytest.mark.parametrize("kind,ss,r", [("gauss", 4.0, 0), ("gauss", 8.0, 24), ("box", 2.0, 2),
+                                       ("box", 8.0, 8)])
+def test_image_gradient_alone_matches(bf, kind, ss, r):
+    # without dL/dsigma_r the kernel skips the f^2 planes: dL/df is unchanged, bit for bit
+    import torch
+    img = synth.rectangles(70, 90, n_rect=6, noise=8.0, seed=r + 1)
+    u = torch.from_numpy(synth.upstream(img.shape, seed=r + 2)).cuda()
+    plan = bf.Plan(ss, 25.0, kind=kind, radius=r)
+    f = torch.from_numpy(img).cuda()
+    out, q = bf.forward(plan, f, return_q=True)
+    g1, gs = bf.backward(plan, f, out, q, u, need_sigma=True)
+    g2, none = bf.backward(plan, f, out, q, u, need_sigma=False)
+    assert none is None and gs is not None
+    assert torch.equal(g1, g2)
