@@ -243,6 +243,10 @@ def run_ours(args):
             one(i)
     torch.cuda.synchronize()
 
+    # measured FP32-pipe rate (scalar FFMA and paired FFMA2), outside the timed region
+    pipe_rate = bf.fp32_pipe_rate(paired=False)
+    pipe_rate2 = bf.fp32_pipe_rate(paired=True)
+
     # per-call CUDA events on the launching stream; L2 flushed before every step
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in plans] for _ in range(args.steps)]
@@ -294,7 +298,12 @@ def run_ours(args):
                 "frac": rl[dom]["frac"], "traffic": None,
                 "kernel": rl[dom]["kernel"], "per_call": rl,
                 "peak_note": "SMs x 128 FP32 lanes x max SM clock %.0f MHz (%s)" % (
-                    peaks.get("sm_max_mhz", SM_MAX_MHZ), peak_kind)}
+                    peaks.get("sm_max_mhz", SM_MAX_MHZ), peak_kind),
+                "peak_ffma_loop": pipe_rate / 1e12,
+                "peak_ffma2_loop": pipe_rate2 / 1e12,
+                "frac_of_ffma_loop": rl[dom]["achieved_tinstr_s"] * 1e12 / pipe_rate,
+                "ffma_loop_note": "measured: independent FMA chains on every SM, "
+                                  "5 timed launches (lane ops/s; FFMA2 counts 2)"}
 
     # ---- end to end through the public API with host buffers
     host_in = torch.from_numpy(img_np).pin_memory()

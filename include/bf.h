@@ -67,12 +67,33 @@ typedef enum {
 
 typedef enum { BF_F32 = 0, BF_U8 = 1 } bf_dtype;
 
+/*
+ * How the plan picks the degree N when N_override is 0 (Algorithm 1 step 2:
+ * "set N = (gamma sigma_r)^-2, or use a look-up table").
+ *   BF_DEGREE_ESTIMATE: N = max(1, ceil((gamma sigma_r)^-2)), the smallest N
+ *     that keeps every phase within [-pi/2, pi/2], so phi >= 0 and monotone
+ *     on [0, T] (Section 2.4).
+ *   BF_DEGREE_TABLE1: the empirical minimum degrees N_0 of Table 1 (T = 255;
+ *     sigma_r in {200, 150, 100, 80, 60, 50, 40} -> N_0 = 1, 2, 3, 4, 5, 7, 9),
+ *     applied at sigma' = 255 sigma_r / T (the approximation problem is the
+ *     same after scaling s by 255 / T).  Between two tabulated values the plan
+ *     takes the smaller of the N_0 listed for the next smaller tabulated sigma
+ *     and the estimate; at sigma' >= 200, N = 1; below 40, where the table
+ *     lists nothing, the estimate.  Such degrees let phases exceed pi/2: phi
+ *     then takes values slightly below 0 (at most 3.6e-3 in magnitude, at
+ *     sigma' = 60, N = 5), which the method reproduces exactly as it does any
+ *     other trigonometric kernel; the caller accepts that P / Q is then no
+ *     longer a convex combination.
+ */
+typedef enum { BF_DEGREE_ESTIMATE = 0, BF_DEGREE_TABLE1 = 1 } bf_degree_rule;
+
 typedef struct {
-    int N_override;      /* degree N; 0 = the rule N = max(1, ceil((gamma sigma_r)^-2)) */
+    int N_override;      /* degree N; 0 = chosen by degree_rule */
     int radius_override; /* Gaussian: support half-width R (0 = ceil(3 sigma_s));
                             box: half-width r of one box (0 = the r whose
                             box_passes-fold variance is closest to sigma_s^2) */
     int box_passes;      /* box only; 0 = 3.  Only 3 is implemented. */
+    int degree_rule;     /* bf_degree_rule; 0 = BF_DEGREE_ESTIMATE */
 } bf_plan_opts;
 
 /* Opaque, host-owned plan.  Creating one never touches a GPU. */
@@ -341,6 +362,20 @@ void bf_batch_destroy(bf_batch *batch);
  */
 bf_status bf_batch_tune(bf_batch *batch, cudaStream_t stream, int reps, int *grid,
                         int *order, float *ms);
+
+/*
+ * Measured FP32 FMA-pipe throughput of the current device (not in the paper;
+ * a measuring aid, not part of the filter).  The filter's kernels are bound by
+ * plain FP32 arithmetic, so their roofline denominator is the rate of FP32
+ * lane operations.  This call launches a kernel of independent FMA chains on
+ * every SM (2048 resident threads each; paired != 0: FFMA2, two lane
+ * operations per instruction), times five launches after two warm-up launches
+ * with CUDA events on `stream`, synchronises `stream` and stores lane
+ * operations per second (an FFMA counts as one) in the HOST double
+ * *lane_ops_per_s.  About 10 ms of GPU time.  BF_EINVAL for a NULL output,
+ * BF_ECUDA for a failed launch or event.
+ */
+bf_status bf_fp32_pipe_rate(int paired, double *lane_ops_per_s, cudaStream_t stream);
 
 /* Message for the last non-OK status returned on the calling thread. */
 const char *bf_last_error(void);

@@ -146,6 +146,25 @@ def n_rule(sigma_r: float, T: float = 255.0) -> int:
     return int(_load().or_n_rule(float(sigma_r), float(T)))
 
 
+# Table 1 (Section 2.5): empirical minimum degrees N_0 of the raised cosine
+# for T = 255, listed for these sigma values.
+_TABLE1 = ((200.0, 1), (150.0, 2), (100.0, 3), (80.0, 4), (60.0, 5), (50.0, 7), (40.0, 9))
+
+
+def n_table1(sigma_r: float, T: float = 255.0) -> int:
+    """Degree by the look-up table Algorithm 1 step 2 allows: Table 1's N_0
+    read at sigma' = 255 sigma_r / T (the same approximation problem after
+    scaling s by 255 / T).  Between listed sigmas, the N_0 of the next smaller
+    listed sigma; never above the estimate n_rule; below the smallest listed
+    sigma the table says nothing and the estimate is used."""
+    est = n_rule(sigma_r, T)
+    sp = float(sigma_r) * 255.0 / float(T)
+    listed = [n0 for sig, n0 in _TABLE1 if sig <= sp]
+    if not listed:
+        return est
+    return min(listed[0], est)
+
+
 def _kind(kind) -> int:
     if isinstance(kind, str):
         return {"gauss": GAUSS, "box": BOX}[kind]

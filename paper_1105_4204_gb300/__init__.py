@@ -4,9 +4,9 @@ The compute path is the CUDA library ``libbf.so`` (built from ``csrc/`` for
 sm_103a by ``build.build()``); this package is its thin Python binding.
 """
 from .api import (BOX, GAUSS, Batch, BilateralFunction, Plan, backward, bilateral,  # noqa: F401
-                  backward_stack, forward, forward_host, forward_stack, forward_unfused, set_shape,
-                  tune)
+                  backward_stack, forward, forward_host, forward_stack, forward_unfused,
+                  fp32_pipe_rate, set_shape, tune)
 
 __all__ = ["Plan", "forward", "forward_stack", "forward_host", "forward_unfused", "backward",
-           "backward_stack", "bilateral", "tune", "set_shape",
+           "backward_stack", "bilateral", "tune", "set_shape", "fp32_pipe_rate",
            "BilateralFunction", "Batch", "GAUSS", "BOX"]

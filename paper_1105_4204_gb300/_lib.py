@@ -35,7 +35,8 @@ class BfError(RuntimeError):
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("N_override", c_int), ("radius_override", c_int), ("box_passes", c_int)]
+    _fields_ = [("N_override", c_int), ("radius_override", c_int), ("box_passes", c_int),
+                ("degree_rule", c_int)]
 
 
 def _declare(lib):
@@ -76,6 +77,7 @@ def _declare(lib):
         "bf_release_scratch": (None, []),
         "bf_last_error": (c_char_p, []),
         "bf_version": (c_int, []),
+        "bf_fp32_pipe_rate": (c_int, [c_int, ctypes.POINTER(ctypes.c_double), c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

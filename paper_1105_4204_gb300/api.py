@@ -32,11 +32,15 @@ class Plan:
     """Host-side plan: degree N, folded binomial term table, spatial taps
     (Algorithm 1 steps 1-3).  Creating it never touches the GPU."""
 
+    DEGREE_RULES = {"estimate": 0, "table1": 1}
+
     def __init__(self, sigma_s: float, sigma_r: float, T: float = 255.0, kind="gauss",
-                 N: int = 0, radius: int = 0, passes: int = 0):
+                 N: int = 0, radius: int = 0, passes: int = 0, degree_rule: str = "estimate"):
+        """``degree_rule`` (when N is 0): "estimate" N = max(1, ceil((gamma
+        sigma_r)^-2)), or "table1", the empirical minimum degrees of Table 1."""
         self._lib = lib()
         self._h = ctypes.c_void_p()
-        opts = PlanOpts(int(N), int(radius), int(passes))
+        opts = PlanOpts(int(N), int(radius), int(passes), self.DEGREE_RULES[degree_rule])
         check(self._lib.bf_plan_create(ctypes.byref(self._h), float(sigma_s), float(sigma_r),
                                        float(T), _kind(kind), ctypes.byref(opts)))
         self.sigma_s, self.sigma_r, self.T, self.kind = float(sigma_s), float(sigma_r), float(T), kind
@@ -165,6 +169,15 @@ def set_shape(plan: Plan, img: torch.Tensor, shape: str):
     this plan at img's size, as ``tune`` would after timing."""
     dt, H, W, C, rs = _image_args(img)
     check(lib().bf_forward_set_shape(plan.handle, H, W, C, SHAPES[shape]))
+
+
+def fp32_pipe_rate(paired: bool = False, stream=None) -> float:
+    """Measured FP32 lane operations per second of the current device (an FMA
+    counts as one; ``paired`` issues them as FFMA2).  Synchronises the
+    stream; about 10 ms of GPU time.  A measuring aid for the ALU roofline."""
+    r = ctypes.c_double()
+    check(lib().bf_fp32_pipe_rate(int(bool(paired)), ctypes.byref(r), _stream_ptr(stream)))
+    return r.value
 
 
 def forward_host(plan: Plan, img_host: torch.Tensor, out_host: torch.Tensor | None = None,

@@ -34,6 +34,21 @@ int degree_rule(double sigma_r, double T) {
     return n < 1.0 ? 1 : (int)n;
 }
 
+// Table 1: empirical minimum degrees N_0 for T = 255, by decreasing sigma.
+constexpr double kTable1Sigma[] = {200.0, 150.0, 100.0, 80.0, 60.0, 50.0, 40.0};
+constexpr int kTable1N0[] = {1, 2, 3, 4, 5, 7, 9};
+
+// Degree from Table 1 at sigma' = 255 sigma_r / T: the N_0 of the largest
+// tabulated sigma not above sigma', capped by the estimate; the estimate
+// below the table's smallest sigma.
+int degree_table1(double sigma_r, double T) {
+    const double sp = sigma_r * 255.0 / T;
+    const int est = degree_rule(sigma_r, T);
+    for (int k = 0; k < 7; ++k)
+        if (sp >= kTable1Sigma[k]) return kTable1N0[k] < est ? kTable1N0[k] : est;
+    return est;
+}
+
 // p[n] = 2^-N C(N, n), n = 0..N, by the ratio C(N,n-1)/C(N,n) = n/(N-n+1)
 // walked outward from the middle and normalised to unit sum (the binomial
 // weights sum to 1).  Tails below the double range become 0.
@@ -176,6 +191,8 @@ extern "C" bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_
     if (opts) o = *opts;
     if (o.N_override < 0 || o.radius_override < 0 || o.box_passes < 0)
         return bf::fail(BF_EINVAL, "bf_plan_create: negative option");
+    if (o.degree_rule != BF_DEGREE_ESTIMATE && o.degree_rule != BF_DEGREE_TABLE1)
+        return bf::fail(BF_EINVAL, "bf_plan_create: unknown degree_rule");
 
     bf_plan *p = new (std::nothrow) bf_plan();
     if (!p) return bf::fail(BF_ENOMEM, "bf_plan_create: out of host memory");
@@ -184,7 +201,9 @@ extern "C" bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_
     p->T = T;
     p->kind = (int)kind;
 
-    int N = o.N_override > 0 ? o.N_override : degree_rule(sigma_r, T);
+    int N = o.N_override > 0                        ? o.N_override
+            : o.degree_rule == BF_DEGREE_TABLE1 ? degree_table1(sigma_r, T)
+                                                : degree_rule(sigma_r, T);
     if (N > BF_MAX_N) {
         delete p;
         return bf::fail(BF_EUNSUPPORTED, "bf_plan_create: degree N = " + std::to_string(N) +
@@ -249,7 +268,8 @@ extern "C" bf_status bf_plan_create_cosine(bf_plan **out, double sigma_s, double
         return bf::fail(BF_EINVAL, who + ": unknown spatial kind");
     bf_plan_opts o{};
     if (opts) o = *opts;
-    if (o.N_override != 0) return bf::fail(BF_EINVAL, who + ": N_override does not apply");
+    if (o.N_override != 0 || o.degree_rule != 0)
+        return bf::fail(BF_EINVAL, who + ": N_override and degree_rule do not apply");
     if (o.radius_override < 0 || o.box_passes < 0)
         return bf::fail(BF_EINVAL, who + ": negative option");
 

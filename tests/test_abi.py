@@ -51,6 +51,28 @@ def test_plan_degree_rule_matches_table1(bf):
         assert bf.Plan(3.0, float(sigma), 255.0).N == int(n_rule)
 
 
+def test_plan_table1_degree_rule_matches_the_oracle(bf, oracle):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table1_degree.txt"))
+            if l.strip() and not l.startswith("#")]
+    for sigma, n0, _n_rule in rows:
+        assert bf.Plan(3.0, float(sigma), 255.0, degree_rule="table1").N == int(n0)
+    for T in [100.0, 255.0, 4095.0]:
+        for sr in np.linspace(0.05, 1.0, 97) * T:
+            p = bf.Plan(2.0, float(sr), T, kind="box", degree_rule="table1")
+            assert p.N == oracle.n_table1(float(sr), T), (T, sr)
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    h = ctypes.c_void_p()
+    bad = _lib.PlanOpts(0, 0, 0, 2)
+    assert l.bf_plan_create(ctypes.byref(h), 2.0, 40.0, 255.0, 0, ctypes.byref(bad)) == 1
+    assert b"degree_rule" in l.bf_last_error()
+    a = np.array([1.0, 0.5])
+    cos_opts = _lib.PlanOpts(0, 0, 0, 1)
+    assert l.bf_plan_create_cosine(ctypes.byref(h), 2.0, 0.01,
+                                   a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 2, 0,
+                                   ctypes.byref(cos_opts)) == 1
+
+
 @pytest.mark.parametrize("sr,N", [(10.0, 264), (15.0, 118), (20.0, 66), (25.0, 43), (30.0, 30),
                                   (50.0, 11), (60.0, 8)])
 def test_plan_degree_at_workload_sigmas(bf, sr, N):
@@ -234,3 +256,10 @@ def test_recursive_gaussian_plan(bf, oracle):
     with pytest.raises(BfError) as e:
         bf.Plan(3.0, 30.0, kind="recursive", radius=5)
     assert e.value.status == 1
+
+
+def test_fp32_pipe_rate_rejects_null_output_without_touching_a_gpu(bf):
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    assert l.bf_fp32_pipe_rate(0, None, None) == 1
+    assert b"NULL" in l.bf_last_error()

@@ -71,6 +71,20 @@ def test_gauss_ragged_sizes(bf, oracle, H, W, sigma_s, sigma_r):
     assert np.abs(out - ref).max() <= TOL
 
 
+@pytest.mark.parametrize("sigma_r,N0", [(40.0, 9), (50.0, 7), (60.0, 5), (80.0, 4)])
+@pytest.mark.parametrize("kind,sigma_s", [("gauss", 3.0), ("box", 4.0)])
+def test_table1_degrees(bf, oracle, sigma_r, N0, kind, sigma_s):
+    # Table 1's empirical degrees let the phase pass pi / 2 (phi dips below 0);
+    # the expansion is still exact, so the kernels match the definition at that N
+    img = synth.rectangles(83, 141, n_rect=7, noise=10.0, seed=int(sigma_r))
+    plan = bf.Plan(sigma_s, sigma_r, kind=kind, degree_rule="table1")
+    assert plan.N == N0
+    assert 255.0 / (sigma_r * np.sqrt(N0)) > np.pi / 2
+    out = _run(bf, img, plan)
+    ref = _oracle_full(oracle, img, plan)
+    assert np.abs(out - ref).max() <= TOL
+
+
 @pytest.mark.parametrize("R", [1, 3, 4, 5, 9, 12, 16, 18, 24])
 def test_gauss_every_radius(bf, oracle, R):
     img = synth.rectangles(45, 77, n_rect=6, noise=10.0, seed=R)
@@ -419,3 +433,26 @@ def test_prefetching_horizontal_sweep_with_two_vertical_rounds(bf, oracle):
     err = np.abs(out.ravel()[idx] - ref).max()
     print("r=32 N=200 max abs err %.3e on %d px" % (err, len(idx)))
     assert err <= TOL
+
+
+def _max_sm_mhz():
+    import subprocess
+    try:
+        r = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                            "-i", "0"], capture_output=True, text=True, timeout=30)
+        return float(r.stdout.strip().splitlines()[0])
+    except Exception:
+        return 2070.0  # GB300's maximum SM clock
+
+
+def test_fp32_pipe_rate_is_physical(bf):
+    # the measured FMA-pipe rate lies below SMs x 128 lanes x the maximum SM clock
+    # (FFMA2 may retire up to two lane operations per lane and cycle) and well above zero
+    import torch
+    nominal = torch.cuda.get_device_properties(0).multi_processor_count * 128 * _max_sm_mhz() * 1e6
+    r1 = bf.fp32_pipe_rate(paired=False)
+    r2 = bf.fp32_pipe_rate(paired=True)
+    assert 0.3 * nominal < r1 <= 1.02 * nominal, (r1, nominal)
+    assert 0.3 * nominal < r2 <= 2.04 * nominal, (r2, nominal)
+    print("FP32 pipe: FFMA %.2f, FFMA2 %.2f T lane-ops/s; nominal %.2f" % (
+        r1 / 1e12, r2 / 1e12, nominal / 1e12))

@@ -32,6 +32,43 @@ def test_degree_rule_matches_table1(oracle):
         assert oracle.n_rule(float(sigma), 255.0) == int(n_rule), sigma
 
 
+def test_table1_lookup_reproduces_the_printed_degrees(oracle):
+    # Table 1's N_0 row at its own sigmas; the look-up reading in between
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table1_degree.txt"))
+            if l.strip() and not l.startswith("#")]
+    for sigma, n0, _n_rule in rows:
+        assert oracle.n_table1(float(sigma), 255.0) == int(n0), sigma
+    # between listed sigmas: the next smaller listed sigma's N_0, capped by the estimate
+    assert oracle.n_table1(45.0) == 9 and oracle.n_table1(55.0) == 7
+    assert oracle.n_table1(90.0) == 4 and oracle.n_table1(180.0) == 1
+    grid = np.linspace(1.0, 400.0, 4000)
+    ns = [oracle.n_table1(float(s)) for s in grid]
+    assert all(a >= b for a, b in zip(ns, ns[1:]))            # non-increasing in sigma
+    for s, n in zip(grid, ns):
+        assert 1 <= n <= oracle.n_rule(float(s))
+        if s < 40.0:
+            assert n == oracle.n_rule(float(s))                # below the table: the estimate
+    for T in [1.0, 100.0, 1000.0, 65535.0]:                   # sigma / T is what matters
+        for s in [45.0, 52.0, 75.0, 130.0, 300.0]:
+            assert oracle.n_table1(s * T / 255.0, T) == oracle.n_table1(s, 255.0)
+
+
+def test_table1_degrees_keep_the_kernel_nearly_non_negative(oracle):
+    # Section 2.5: below the estimate the phase passes pi / 2 and cos^N can dip
+    # below 0; over the look-up's whole range the dip stays under 3.6e-3 (the
+    # deepest at sigma = 60, N = 5: cos(1.9007)^5 = -3.566e-3), and it is absent
+    # wherever the look-up returns the estimate
+    s = np.linspace(-255.0, 255.0, 20001)
+    worst = 0.0
+    for sigma in np.linspace(30.0, 400.0, 741):
+        N = oracle.n_table1(float(sigma))
+        phi_min = (np.cos(s / (sigma * math.sqrt(N))) ** N).min()
+        worst = min(worst, phi_min)
+        if N == oracle.n_rule(float(sigma)):
+            assert phi_min >= -1e-15, sigma
+    assert -3.6e-3 <= worst < -3.5e-3
+
+
 def test_degree_rule_keeps_phase_in_half_period(oracle):
     # Section 2.5: N must make the argument of cos stay in [-pi/2, pi/2] on
     # [-T, T], i.e. T / (sigma_r sqrt N) <= pi / 2.
