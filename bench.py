@@ -158,6 +158,29 @@ def oracle_rate(step_seconds_budget: float, seed: int = 0):
     return mpx, cores, "; ".join(desc) + " (brute force of eq. (BF), extrapolated per pixel)"
 
 
+def oracle_table2_rate():
+    """The paper's own timing workload (Table 2: 720 x 540, recursive Gaussian,
+    sigma_s = 10 and 100) run by the oracle's FP64 O(1) formulation (Algorithm
+    1 in the complex form with the recursive Gaussian as the averaging) on the
+    host cores, for a subset of sigma_r: the paper-like CPU figure beside the
+    paper's own CPU times and the GPU's."""
+    import oracle
+    import synth
+    img = synth.rectangles(540, 720, n_rect=20, noise=10.0, seed=0).astype(np.float64)
+    res = {}
+    for ss, paper in PAPER_TABLE2_MS.items():
+        row = {}
+        for sr, pm in zip(TABLE2_SIGMA_R, paper):
+            if sr not in (30.0, 50.0, 100.0):
+                continue
+            t0 = time.perf_counter()
+            oracle.bf_trig_rg(img, sigma_s=ss, sigma_r=sr, T=T_RANGE)
+            row["sigma_r=%g" % sr] = {"N": oracle.n_rule(sr, T_RANGE),
+                                      "ms": (time.perf_counter() - t0) * 1e3, "paper_ms": pm}
+        res["sigma_s=%g" % ss] = row
+    return res
+
+
 # ------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -386,6 +409,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_rate(float(os.environ.get("BF_CPU_SECONDS", "15")))
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        if not args.no_extras:
+            cpu["table2_fp64_o1_720x540_ms"] = oracle_table2_rate()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -72,13 +72,15 @@ def test_gauss_ragged_sizes(bf, oracle, H, W, sigma_s, sigma_r):
 
 
 @pytest.mark.parametrize("sigma_r,N0", [(40.0, 9), (50.0, 7), (60.0, 5), (80.0, 4)])
-@pytest.mark.parametrize("kind,sigma_s", [("gauss", 3.0), ("box", 4.0)])
+@pytest.mark.parametrize("kind,sigma_s", [("gauss", 3.0), ("box", 4.0), ("box", 12.0)])
 def test_table1_degrees(bf, oracle, sigma_r, N0, kind, sigma_s):
     # Table 1's empirical degrees let the phase pass pi / 2 (phi dips below 0);
     # the expansion is still exact, so the kernels match the definition at that N
     img = synth.rectangles(83, 141, n_rect=7, noise=10.0, seed=int(sigma_r))
     plan = bf.Plan(sigma_s, sigma_r, kind=kind, degree_rule="table1")
     assert plan.N == N0
+    if sigma_s == 12.0:
+        assert plan.radius // 3 > 8  # the streaming sweeps
     assert 255.0 / (sigma_r * np.sqrt(N0)) > np.pi / 2
     out = _run(bf, img, plan)
     ref = _oracle_full(oracle, img, plan)
