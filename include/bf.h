@@ -223,6 +223,8 @@ bf_status bf_forward_stack(const bf_plan *plan, const void *in, bf_dtype dt, flo
  *   1  32 x 96 tiles, wider row segments (box r <= 4, Gaussian R <= 9)
  *   2  64 x 64 tiles, one 512-thread block per SM (box 3 <= r <= 8,
  *      Gaussian R >= 9)
+ *   3  64 x 64 tiles, 32-pixel row segments, one 256-thread block per SM
+ *      (box 7 <= r <= 8)
  */
 bf_status bf_forward_tune(const bf_plan *plan, const void *in, bf_dtype dt, float *out, int H,
                           int W, int C, long long row_stride_elems, int reps,

@@ -157,16 +157,18 @@ def tune(plan: Plan, img: torch.Tensor, reps: int = 3, stream=None):
     check(lib().bf_forward_tune(plan.handle, ctypes.c_void_p(img.data_ptr()), dt,
                                 ctypes.c_void_p(out.data_ptr()), H, W, C, rs, int(reps),
                                 _stream_ptr(stream), ctypes.byref(shape), ctypes.byref(ms)))
-    return {"shape": {-1: "streaming", 0: "32x64", 1: "32x96", 2: "64x64"}[shape.value],
+    return {"shape": {-1: "streaming", 0: "32x64", 1: "32x96", 2: "64x64",
+                      3: "64x64-seg32"}[shape.value],
             "ms": ms.value}
 
 
-SHAPES = {"32x64": 0, "32x96": 1, "64x64": 2}
+SHAPES = {"32x64": 0, "32x96": 1, "64x64": 2, "64x64-seg32": 3}
 
 
 def set_shape(plan: Plan, img: torch.Tensor, shape: str):
-    """Pin the fused kernel's tile shape ("32x64", "32x96" or "64x64") for
-    this plan at img's size, as ``tune`` would after timing."""
+    """Pin the fused kernel's tile shape ("32x64", "32x96", "64x64" or
+    "64x64-seg32") for this plan at img's size, as ``tune`` would after
+    timing."""
     dt, H, W, C, rs = _image_args(img)
     check(lib().bf_forward_set_shape(plan.handle, H, W, C, SHAPES[shape]))
 

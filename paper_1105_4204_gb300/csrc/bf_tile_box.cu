@@ -8,14 +8,20 @@ int box_tile_max_r() { return 8; }
 // Tile shapes by id: 0 = 32 x 64 tiles, 16-pixel segments (two or three
 // blocks per SM); 1 (r <= 4) = 32 x 96 tiles, 24-pixel segments; 2 (r >= 3) =
 // 64 x 64 tiles, 16-pixel segments, one 512-thread block per SM (less halo
-// per output at the cost of occupancy).  Fills ids, returns their number.
+// per output at the cost of occupancy); 3 (r >= 7) = 64 x 64 tiles, 32-pixel
+// segments, one 256-thread block per SM (also less warm-up per segment, at
+// half the warps; measured 4 % faster than id 0 at r = 8 on 2048 x 2048,
+// slower below r = 7).  Fills ids, returns their number.
 int box_tile_shape_ids(int r, int *ids) {
     int n = 0;
     ids[n++] = 0;
     if (r >= 1 && r <= 4) ids[n++] = 1;
     if (r >= 3 && r <= 8) ids[n++] = 2;
+    if (r >= 7 && r <= 8) ids[n++] = 3;
     return n;
 }
+
+cudaError_t launch_tile_box_long_segments(int r, const TileParams &prm, cudaStream_t s);
 
 cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t s, int shape) {
     TileParams prm;
@@ -32,6 +38,7 @@ cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t
             default: break;
         }
     }
+    if (shape == 3) return launch_tile_box_long_segments(pl->r_box, prm, s);
     if (shape == 2) {
         switch (pl->r_box) {
             case 3: return launch_tile<1, 3, 64, 64, 16>(prm, s);

@@ -175,6 +175,8 @@ def test_set_shape_accepts_only_the_supports_shapes(bf):
     assert l.bf_forward_set_shape(box2.handle, 64, 64, 1, 2) == 1   # 64 x 64 needs r >= 3
     assert l.bf_forward_set_shape(box8.handle, 64, 64, 1, 2) == 0
     assert l.bf_forward_set_shape(box8.handle, 64, 64, 1, 1) == 1   # 32 x 96 needs r <= 4
+    assert l.bf_forward_set_shape(box8.handle, 64, 64, 1, 3) == 0   # 64 x 64, 32-px segments
+    assert l.bf_forward_set_shape(box2.handle, 64, 64, 1, 3) == 1   # needs r >= 7
     assert l.bf_forward_set_shape(box8.handle, 64, 64, 1, 7) == 1
     assert l.bf_forward_set_shape(box8.handle, 0, 64, 1, 0) == 1
     big = bf.Plan(32.0, 20.0, kind="box")                          # streaming kernels

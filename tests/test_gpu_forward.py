@@ -106,8 +106,10 @@ def test_box_every_radius(bf, oracle, r):
     assert np.abs(out - ref).max() <= TOL
 
 
-_SHAPE_CASES = ([("box", r, sh) for r in range(1, 9) for sh in ("32x64", "32x96", "64x64")
-                 if not (sh == "32x96" and r > 4) and not (sh == "64x64" and r < 3)] +
+_SHAPE_CASES = ([("box", r, sh) for r in range(1, 9)
+                  for sh in ("32x64", "32x96", "64x64", "64x64-seg32")
+                  if not (sh == "32x96" and r > 4) and not (sh == "64x64" and r < 3)
+                  and not (sh == "64x64-seg32" and r < 7)] +
                 [("gauss", R, sh) for R in (2, 9, 12, 18, 24) for sh in ("32x64", "32x96", "64x64")
                  if not (sh == "32x96" and R > 9) and not (sh == "64x64" and R < 9)])
 
@@ -352,7 +354,7 @@ def test_tuned_tile_shape_stays_correct(bf, oracle, kind, ss):
     plan = bf.Plan(ss, 25.0, kind=kind)
     before = bf.forward(plan, t).cpu().numpy()
     info = bf.tune(plan, t, reps=2)
-    assert info["shape"] in ("32x64", "32x96", "64x64", "streaming")
+    assert info["shape"] in ("32x64", "32x96", "64x64", "64x64-seg32", "streaming")
     after = bf.forward(plan, t).cpu().numpy()
     ref = _oracle_full(oracle, img, plan) if plan.radius <= 24 else None
     if ref is not None:
