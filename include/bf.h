@@ -202,6 +202,32 @@ bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *ou
                      cudaStream_t stream);
 
 /*
+ * bf_forward for an image in HOST memory (not in the paper): in stream order,
+ * copies host_in into the caller's device buffer dev_in, filters dev_in into
+ * the caller's device buffer dev_out as bf_forward does, and copies dev_out
+ * back into host_out.
+ *   host_in  : host image laid out as bf_forward's `in` (H rows of
+ *              row_stride_elems elements of type dt, the last row W*C long),
+ *              or NULL when dev_in already holds the image (another filter of
+ *              the same image: no copy)
+ *   dev_in   : device buffer of at least ((H-1)*row_stride_elems + W*C)
+ *              elements of type dt
+ *   dev_out  : device float buffer of H*W*C elements
+ *   host_out : host float buffer of H*W*C elements receiving the result, or
+ *              NULL to leave it in dev_out only
+ * The copies are cudaMemcpyAsync on `stream`: asynchronous (the call returns
+ * before they finish) when the host buffers are page-locked
+ * (cudaHostAlloc/cudaHostRegister), otherwise the runtime's pageable-copy
+ * rules apply.  The host buffers must stay valid, and host_out unread, until
+ * `stream` has reached the end of the call's work.  The library owns none of
+ * the four buffers.  Errors: as bf_forward, plus BF_EINVAL for a NULL dev_in
+ * or dev_out, BF_ECUDA for a failed copy.
+ */
+bf_status bf_forward_host(const bf_plan *plan, const void *host_in, bf_dtype dt, void *dev_in,
+                          float *dev_out, float *host_out, int H, int W, int C,
+                          long long row_stride_elems, cudaStream_t stream);
+
+/*
  * bf_forward over a stack of `count` single-channel images of one size, laid
  * out contiguously (image k at in + k*H*W elements, out + k*H*W floats),
  * all filtered with the same plan in one launch (channels are independent,

@@ -107,9 +107,11 @@ class Plan:
             self._h = ctypes.c_void_p()
 
 
-def _image_args(img: torch.Tensor):
-    if not img.is_cuda:
+def _image_args(img: torch.Tensor, where: str = "cuda"):
+    if where == "cuda" and not img.is_cuda:
         raise ValueError("image must be a CUDA tensor")
+    if where == "host" and img.is_cuda:
+        raise ValueError("image must be a host tensor")
     if img.dtype == torch.float32:
         dt = 0
     elif img.dtype == torch.uint8:
@@ -182,18 +184,36 @@ def fp32_pipe_rate(paired: bool = False, stream=None) -> float:
     return r.value
 
 
-def forward_host(plan: Plan, img_host: torch.Tensor, out_host: torch.Tensor | None = None,
-                 stream=None) -> torch.Tensor:
-    """End-to-end call for host images: copy in (pinned host -> device), filter,
-    copy the result back (device -> host)."""
+def forward_host(plan: Plan, img_host: torch.Tensor | None, out_host: torch.Tensor | None = None,
+                 stream=None, dev_in: torch.Tensor | None = None,
+                 dev_out: torch.Tensor | None = None) -> torch.Tensor | None:
+    """End-to-end call for a host image (``bf_forward_host``): copies img_host
+    (pinned for asynchrony) into ``dev_in``, filters it into ``dev_out`` and
+    copies the result into ``out_host`` (a new pinned tensor when None), in
+    order on the stream.  ``img_host=None`` filters what ``dev_in`` already
+    holds (no copy in); the device buffers are allocated when not given.
+    Returns out_host; it is complete once the stream reaches the call's end."""
+    src = img_host if img_host is not None else dev_in
+    if src is None:
+        raise ValueError("forward_host needs img_host or a filled dev_in")
+    dt, H, W, C, rs = _image_args(src, "host" if img_host is not None else "cuda")
     dev = torch.device("cuda", torch.cuda.current_device())
-    s = stream if stream is not None else torch.cuda.current_stream()
-    with torch.cuda.stream(s):
-        d_in = img_host.to(dev, non_blocking=True)
-        d_out = forward(plan, d_in, stream=s)
-        if out_host is None:
-            out_host = torch.empty(tuple(img_host.shape), dtype=torch.float32, pin_memory=True)
-        out_host.copy_(d_out, non_blocking=True)
+    shape = tuple(src.shape)
+    if dev_in is None:
+        dev_in = torch.empty(shape, dtype=src.dtype, device=dev)
+    if dev_out is None:
+        dev_out = torch.empty(shape, dtype=torch.float32, device=dev)
+    if out_host is None:
+        out_host = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+    if img_host is not None and (tuple(dev_in.stride()) != tuple(img_host.stride())
+                                 or dev_in.dtype != img_host.dtype):
+        raise ValueError("dev_in must have img_host's dtype and strides")
+    if not out_host.is_contiguous() or not dev_out.is_contiguous():
+        raise ValueError("out_host and dev_out must be contiguous")
+    check(lib().bf_forward_host(
+        plan.handle, ctypes.c_void_p(img_host.data_ptr() if img_host is not None else 0), dt,
+        ctypes.c_void_p(dev_in.data_ptr()), ctypes.c_void_p(dev_out.data_ptr()),
+        ctypes.c_void_p(out_host.data_ptr()), H, W, C, rs, _stream_ptr(stream)))
     return out_host
 
 

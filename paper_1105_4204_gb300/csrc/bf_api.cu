@@ -140,6 +140,36 @@ extern "C" bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt
     return forward_planes(plan, img, stream, "bf_forward");
 }
 
+extern "C" bf_status bf_forward_host(const bf_plan *plan, const void *host_in, bf_dtype dt,
+                                     void *dev_in, float *dev_out, float *host_out, int H, int W,
+                                     int C, long long row_stride_elems, cudaStream_t stream) {
+    if (!dev_in || !dev_out) return fail(BF_EINVAL, "bf_forward_host: dev_in/dev_out is NULL");
+    if (!plan) return fail(BF_EINVAL, "bf_forward_host: plan is NULL");
+    if (H < 1 || W < 1 || C < 1) return fail(BF_EINVAL, "bf_forward_host: H, W, C must be >= 1");
+    if (C > 4) return fail(BF_EUNSUPPORTED, "bf_forward_host: at most 4 channels");
+    if (dt != BF_F32 && dt != BF_U8) return fail(BF_EINVAL, "bf_forward_host: unknown dtype");
+    if (row_stride_elems < (long long)W * C)
+        return fail(BF_EINVAL, "bf_forward_host: row_stride_elems < W*C");
+    if ((long long)H * W > (1LL << 31) / 4)
+        return fail(BF_EUNSUPPORTED, "bf_forward_host: image too large");
+    const size_t esz = dt == BF_F32 ? 4 : 1;
+    const size_t in_bytes = ((size_t)(H - 1) * (size_t)row_stride_elems + (size_t)W * C) * esz;
+    const size_t out_bytes = (size_t)H * W * C * sizeof(float);
+    if (host_in) {
+        cudaError_t e = cudaMemcpyAsync(dev_in, host_in, in_bytes, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_check(e, "bf_forward_host: host -> device copy");
+    }
+    const bf_status st =
+        bf_forward(plan, dev_in, dt, dev_out, H, W, C, row_stride_elems, nullptr, stream);
+    if (st != BF_OK) return st;
+    if (host_out) {
+        cudaError_t e =
+            cudaMemcpyAsync(host_out, dev_out, out_bytes, cudaMemcpyDeviceToHost, stream);
+        if (e != cudaSuccess) return cuda_check(e, "bf_forward_host: device -> host copy");
+    }
+    return BF_OK;
+}
+
 // Runs one BfImage description (interleaved channels or a stack).
 static bf_status forward_planes(const bf_plan *plan, const BfImage &img, cudaStream_t stream,
                                 const char *who) {

@@ -265,3 +265,15 @@ def test_fp32_pipe_rate_rejects_null_output_without_touching_a_gpu(bf):
     l = _lib.lib()
     assert l.bf_fp32_pipe_rate(0, None, None) == 1
     assert b"NULL" in l.bf_last_error()
+
+
+def test_forward_host_rejects_bad_arguments_without_touching_a_gpu(bf):
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    p = bf.Plan(2.0, 20.0, kind="box")
+    fake = ctypes.c_void_p(0x1000)
+    null = ctypes.c_void_p(0)
+    assert l.bf_forward_host(p.handle, fake, 0, null, fake, fake, 16, 16, 1, 16, null) == 1
+    assert b"dev_in" in l.bf_last_error()
+    assert l.bf_forward_host(p.handle, fake, 0, fake, fake, fake, 16, 16, 1, 8, null) == 1
+    assert l.bf_forward_host(p.handle, fake, 0, fake, fake, fake, 16, 16, 5, 80, null) == 2

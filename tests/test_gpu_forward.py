@@ -164,6 +164,33 @@ def test_u8_interleaved_channels(bf, oracle):
     np.testing.assert_array_equal(out, out_f)
 
 
+def test_forward_host_matches_the_device_call(bf, oracle):
+    # the C-ABI call with host buffers: copy in, filter, copy back, in stream
+    # order; bit-identical to bf_forward on the same image, for u8 HWC and f32,
+    # and for a second filter of the image already on the device (no copy in)
+    import torch
+    img = synth.rect_disk_u8(70, 93, C=3, n_shapes=10, noise=8.0, seed=21)
+    host = torch.from_numpy(img).pin_memory()
+    plans = [bf.Plan(2.0, 30.0, kind="gauss"), bf.Plan(12.0, 30.0, kind="box")]
+    d_in = torch.empty_like(host, device="cuda")
+    outs = []
+    for i, p in enumerate(plans):
+        o = bf.forward_host(p, host if i == 0 else None, dev_in=d_in)
+        torch.cuda.synchronize()
+        outs.append(o.numpy().copy())
+    for p, o in zip(plans, outs):
+        ref = bf.forward(p, torch.from_numpy(img).cuda()).cpu().numpy()
+        np.testing.assert_array_equal(o, ref)
+    ref0 = oracle.bf_brute(img.astype(np.float64), sigma_r=30.0, w1=plan_w1(oracle, plans[0]),
+                           N=plans[0].N)
+    assert np.abs(outs[0] - ref0).max() <= TOL
+    f = synth.smooth_field(65, 130, noise=5.0, seed=3)
+    of = bf.forward_host(plans[1], torch.from_numpy(f).pin_memory())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(of.numpy(), bf.forward(plans[1], torch.from_numpy(f).cuda())
+                                  .cpu().numpy())
+
+
 def test_row_stride_and_channels_f32(bf, oracle):
     import torch
     base = synth.rect_disk_u8(33, 40, C=2, n_shapes=6, seed=9).astype(np.float32)
