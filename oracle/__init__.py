@@ -23,6 +23,8 @@ The arithmetic lives in ``bf_oracle.c`` (plain C, double precision, OpenMP):
   / ``phi_cos`` -- the same for a general trigonometric range kernel of
   Section 2.2, ``phi(s) = a_0 + a_1 cos(gamma s) + ... + a_N cos(N gamma s)``,
   evaluated term by term.
+* ``bf_brute_sv`` -- the space-variant extension of Section 4: each pixel's
+  own box of half-width r(x), eq. (BF) summed directly over it.
 
 This module only marshals numpy arrays into that library.
 """
@@ -48,6 +50,7 @@ GAUSSIAN_RANGE = 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _llp = ctypes.POINTER(ctypes.c_longlong)
+_ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
@@ -121,6 +124,9 @@ def _load():
         lib.or_bf_trig_rg.restype = ctypes.c_double
         lib.or_bf_trig_rg.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
+        lib.or_bf_brute_sv.restype = None
+        lib.or_bf_brute_sv.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
         lib.or_phi_table.restype = None
         lib.or_phi_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
                                      ctypes.c_longlong, _dp]
@@ -227,6 +233,28 @@ def bf_brute(f, sigma_s=3.0, sigma_r=30.0, T=255.0, kind="gauss", radius=0, pass
     out = np.stack(outs, axis=2) if multi else outs[0]
     q = np.stack(qs, axis=2) if multi else qs[0]
     return (out, q) if return_q else out
+
+
+def bf_brute_sv(f, radius, sigma_r=30.0, T=255.0, r_max=None, N=None,
+                range_mode="raised_cosine", return_q=False):
+    """Space-variant brute force (Section 4): at each pixel a box of half-width
+    radius[i, j] (clamped into [0, r_max]; r_max defaults to radius.max()),
+    eq. (BF) summed directly over it; single-channel H x W."""
+    lib = _load()
+    if N is None:
+        N = n_rule(sigma_r, T)
+    x = _f64(f)
+    H, W = x.shape
+    rad = np.ascontiguousarray(np.asarray(radius, dtype=np.int32))
+    if rad.shape != (H, W):
+        raise ValueError("radius must be H x W")
+    if r_max is None:
+        r_max = int(rad.max()) if rad.size else 0
+    o = np.empty((H, W), dtype=np.float64)
+    q = np.empty((H, W), dtype=np.float64)
+    lib.or_bf_brute_sv(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max),
+                       _range_mode(range_mode), float(sigma_r), int(N), _ptr(o), _ptr(q))
+    return (o, q) if return_q else o
 
 
 def bf_brute_at(f, idx, sigma_s=3.0, sigma_r=30.0, T=255.0, kind="gauss", radius=0,

@@ -25,6 +25,9 @@
  *                        Vliet (the spatial filter of the paper's experiments,
  *                        Section 3) and Algorithm 1 with it as the averaging
  *                        of step 4;
+ *   - or_bf_brute_sv   : the space-variant extension (Section 4): at each
+ *                        pixel its own box of half-width r(x), eq. (BF)
+ *                        summed directly over it;
  *   - or_bf_*_cos      : the same filter, gradient and differences for a
  *                        general trigonometric range kernel of Section 2.2,
  *                        phi(s) = a_0 + a_1 cos(gamma s) + ... + a_N cos(N gamma s),
@@ -254,6 +257,37 @@ void or_bf_brute(const double *f, int H, int W, const double *w1, int R,
 {
     or_range rg = or_make_range(mode, sigma_r, N);
     or_brute_rg(f, H, W, w1, R, &rg, out, q_out);
+}
+
+/* Space-variant extension (Section 4): the spatial kernel at pixel (i, j) is
+ * the (2 r + 1) x (2 r + 1) box centred there, r = radius[i * W + j] clamped
+ * into [0, r_max]; its constant weight cancels in the ratio, so eq. (BF) is
+ * summed directly over the box of the clamp-extended image.  q_out (may be
+ * NULL) receives the normaliser with unit-mass weights, Q / (2 r + 1)^2. */
+void or_bf_brute_sv(const double *f, int H, int W, const int *radius, int r_max, int mode,
+                    double sigma_r, int N, double *out, double *q_out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < H; i++) {
+        for (int j = 0; j < W; j++) {
+            int r = or_clamp(radius[(size_t)i * W + j], 0, r_max);
+            double fx = f[(size_t)i * W + j];
+            double p = 0.0, q = 0.0;
+            for (int a = -r; a <= r; a++) {
+                int zi = or_clamp(i + a, 0, H - 1);
+                for (int b = -r; b <= r; b++) {
+                    int zj = or_clamp(j + b, 0, W - 1);
+                    double v = f[(size_t)zi * W + zj];
+                    double ph = or_phi(&rg, v - fx);
+                    p += ph * v;
+                    q += ph;
+                }
+            }
+            out[(size_t)i * W + j] = p / q;
+            if (q_out) q_out[(size_t)i * W + j] = q / ((2.0 * r + 1.0) * (2.0 * r + 1.0));
+        }
+    }
 }
 
 /* Brute-force filter at a list of flat pixel indices only. */

@@ -442,3 +442,84 @@ def test_algorithm1_with_the_recursive_filter(oracle):
     idx = [i * 130 + j for i in range(R, 120 - R, 3) for j in range(R, 130 - R, 3)]
     ref = oracle.bf_brute_at(f, idx, sigma_r=30.0, w1=w1)
     np.testing.assert_allclose(out.ravel()[idx], ref, atol=1e-6)
+
+
+# ------------------------------------------------------ space-variant (Section 4)
+
+def _golden_sv():
+    vals = {}
+    for l in open(os.path.join(GOLDEN, "space_variant_examples.txt")):
+        if l.strip() and not l.startswith("#"):
+            k, v = l.split()
+            vals[k] = float(v)
+    return vals
+
+
+def test_space_variant_hand_examples(oracle):
+    g = _golden_sv()
+    c, c2 = math.cos(0.5), math.cos(0.25)
+    # closed forms worked by hand from eq. (BF) over each pixel's own box
+    assert g["sv1d_0"] == pytest.approx((500 * c + 250 * c2) / (15 + 5 * c + 5 * c2), abs=5e-8)
+    assert g["sv1d_1"] == pytest.approx((300 + 150 * c2) / (3 * c + 3 + 3 * c2), abs=5e-8)
+    out = oracle.bf_brute_sv(np.array([[0.0, 100.0], [100.0, 0.0]]), [[1, 0], [0, 1]],
+                             sigma_r=200.0)
+    np.testing.assert_allclose(out, [[g["sv2d_00"], g["sv2d_01"]], [g["sv2d_10"], g["sv2d_11"]]],
+                               atol=1e-7)
+    out1 = oracle.bf_brute_sv(np.array([[0.0, 100.0, 50.0]]), [[2, 1, 0]], sigma_r=200.0)
+    np.testing.assert_allclose(out1[0], [g["sv1d_0"], g["sv1d_1"], g["sv1d_2"]], atol=1e-7)
+
+
+def test_space_variant_constant_radius_is_the_one_box_filter(oracle):
+    # r(x) = r0 everywhere is the plain filter with one box of half-width r0
+    f = _small_image(17, 23, seed=8)
+    for r0 in (0, 1, 3):
+        w1 = oracle.spatial_w1("box", 1.0, radius=max(r0, 1), passes=1) if r0 else np.ones(1)
+        ref = oracle.bf_brute(f, sigma_r=25.0, w1=w1)
+        out = oracle.bf_brute_sv(f, np.full(f.shape, r0), sigma_r=25.0)
+        np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-10)
+    np.testing.assert_array_equal(oracle.bf_brute_sv(f, np.zeros(f.shape, int), sigma_r=25.0), f)
+
+
+def test_space_variant_wide_range_kernel_is_the_box_mean(oracle):
+    # sigma_r -> infinity: phi -> 1, so out(x) is the mean of the clamp-extended image
+    # over x's box; the means here come from a summed-area table of the padded image
+    f = _small_image(19, 26, seed=9)
+    rng = np.random.default_rng(4)
+    rad = rng.integers(0, 5, size=f.shape)
+    out = oracle.bf_brute_sv(f, rad, sigma_r=1e9)
+    R = 4
+    fp = np.pad(f, R, mode="edge")
+    sat = np.zeros((fp.shape[0] + 1, fp.shape[1] + 1))
+    sat[1:, 1:] = fp.cumsum(0).cumsum(1)
+    H, W = f.shape
+    ref = np.empty_like(f)
+    for i in range(H):
+        for j in range(W):
+            r = rad[i, j]
+            a0, a1, b0, b1 = i + R - r, i + R + r + 1, j + R - r, j + R + r + 1
+            ref[i, j] = (sat[a1, b1] - sat[a0, b1] - sat[a1, b0] + sat[a0, b0]) / (2 * r + 1) ** 2
+    np.testing.assert_allclose(out, ref, rtol=1e-9)
+
+
+def test_space_variant_matches_a_python_loop(oracle):
+    # tiny mixed-radius case against plain Python loops of eq. (BF)
+    f = _small_image(6, 7, seed=10)
+    rad = np.random.default_rng(5).integers(0, 4, size=f.shape)
+    sr, N = 30.0, oracle.n_rule(30.0)
+    k = 1.0 / (sr * math.sqrt(N))
+    H, W = f.shape
+    out = oracle.bf_brute_sv(f, rad, sigma_r=sr)
+    for i in range(H):
+        for j in range(W):
+            r = int(rad[i, j])
+            p = q = 0.0
+            for a in range(-r, r + 1):
+                for b in range(-r, r + 1):
+                    v = f[min(max(i + a, 0), H - 1), min(max(j + b, 0), W - 1)]
+                    ph = math.cos(k * (v - f[i, j])) ** N
+                    p += ph * v
+                    q += ph
+            assert out[i, j] == pytest.approx(p / q, rel=1e-12)
+    # radii are clamped into [0, r_max]
+    np.testing.assert_array_equal(oracle.bf_brute_sv(f, rad + 10, sigma_r=sr, r_max=3),
+                                  oracle.bf_brute_sv(f, np.full(f.shape, 3), sigma_r=sr))
