@@ -127,6 +127,10 @@ def _load():
         lib.or_bf_brute_sv.restype = None
         lib.or_bf_brute_sv.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
+        lib.or_bf_brute_sv_at.restype = None
+        lib.or_bf_brute_sv_at.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_int, _llp,
+                                          ctypes.c_longlong, _dp]
         lib.or_phi_table.restype = None
         lib.or_phi_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
                                      ctypes.c_longlong, _dp]
@@ -255,6 +259,23 @@ def bf_brute_sv(f, radius, sigma_r=30.0, T=255.0, r_max=None, N=None,
     lib.or_bf_brute_sv(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max),
                        _range_mode(range_mode), float(sigma_r), int(N), _ptr(o), _ptr(q))
     return (o, q) if return_q else o
+
+
+def bf_brute_sv_at(f, radius, idx, r_max, sigma_r=30.0, T=255.0, N=None,
+                   range_mode="raised_cosine"):
+    """bf_brute_sv at flat pixel indices ``idx`` only."""
+    lib = _load()
+    if N is None:
+        N = n_rule(sigma_r, T)
+    x = _f64(f)
+    H, W = x.shape
+    rad = np.ascontiguousarray(np.asarray(radius, dtype=np.int32))
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    o = np.empty(len(ix), dtype=np.float64)
+    lib.or_bf_brute_sv_at(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max),
+                          _range_mode(range_mode), float(sigma_r), int(N),
+                          ix.ctypes.data_as(_llp), len(ix), _ptr(o))
+    return o
 
 
 def bf_brute_at(f, idx, sigma_s=3.0, sigma_r=30.0, T=255.0, kind="gauss", radius=0,

@@ -264,30 +264,47 @@ void or_bf_brute(const double *f, int H, int W, const double *w1, int R,
  * into [0, r_max]; its constant weight cancels in the ratio, so eq. (BF) is
  * summed directly over the box of the clamp-extended image.  q_out (may be
  * NULL) receives the normaliser with unit-mass weights, Q / (2 r + 1)^2. */
+static void or_sv_at(const double *f, int H, int W, const int *radius, int r_max,
+                     const or_range *rg, int i, int j, double *out, double *q_out)
+{
+    int r = or_clamp(radius[(size_t)i * W + j], 0, r_max);
+    double fx = f[(size_t)i * W + j];
+    double p = 0.0, q = 0.0;
+    for (int a = -r; a <= r; a++) {
+        int zi = or_clamp(i + a, 0, H - 1);
+        for (int b = -r; b <= r; b++) {
+            int zj = or_clamp(j + b, 0, W - 1);
+            double v = f[(size_t)zi * W + zj];
+            double ph = or_phi(rg, v - fx);
+            p += ph * v;
+            q += ph;
+        }
+    }
+    *out = p / q;
+    if (q_out) *q_out = q / ((2.0 * r + 1.0) * (2.0 * r + 1.0));
+}
+
 void or_bf_brute_sv(const double *f, int H, int W, const int *radius, int r_max, int mode,
                     double sigma_r, int N, double *out, double *q_out)
 {
     or_range rg = or_make_range(mode, sigma_r, N);
 #pragma omp parallel for schedule(dynamic, 4)
-    for (int i = 0; i < H; i++) {
-        for (int j = 0; j < W; j++) {
-            int r = or_clamp(radius[(size_t)i * W + j], 0, r_max);
-            double fx = f[(size_t)i * W + j];
-            double p = 0.0, q = 0.0;
-            for (int a = -r; a <= r; a++) {
-                int zi = or_clamp(i + a, 0, H - 1);
-                for (int b = -r; b <= r; b++) {
-                    int zj = or_clamp(j + b, 0, W - 1);
-                    double v = f[(size_t)zi * W + zj];
-                    double ph = or_phi(&rg, v - fx);
-                    p += ph * v;
-                    q += ph;
-                }
-            }
-            out[(size_t)i * W + j] = p / q;
-            if (q_out) q_out[(size_t)i * W + j] = q / ((2.0 * r + 1.0) * (2.0 * r + 1.0));
-        }
-    }
+    for (int i = 0; i < H; i++)
+        for (int j = 0; j < W; j++)
+            or_sv_at(f, H, W, radius, r_max, &rg, i, j, out + (size_t)i * W + j,
+                     q_out ? q_out + (size_t)i * W + j : NULL);
+}
+
+/* The space-variant filter at a list of flat pixel indices only. */
+void or_bf_brute_sv_at(const double *f, int H, int W, const int *radius, int r_max, int mode,
+                       double sigma_r, int N, const long long *idx, long long n_idx,
+                       double *out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long t = 0; t < n_idx; t++)
+        or_sv_at(f, H, W, radius, r_max, &rg, (int)(idx[t] / W), (int)(idx[t] % W), out + t,
+                 NULL);
 }
 
 /* Brute-force filter at a list of flat pixel indices only. */

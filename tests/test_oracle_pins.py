@@ -520,6 +520,10 @@ def test_space_variant_matches_a_python_loop(oracle):
                     p += ph * v
                     q += ph
             assert out[i, j] == pytest.approx(p / q, rel=1e-12)
+    # the sampled form gives the same values at the same pixels
+    idx = np.array([0, 5, 17, H * W - 1])
+    np.testing.assert_array_equal(oracle.bf_brute_sv_at(f, rad, idx, int(rad.max()), sigma_r=sr),
+                                  out.ravel()[idx])
     # radii are clamped into [0, r_max]
     np.testing.assert_array_equal(oracle.bf_brute_sv(f, rad + 10, sigma_r=sr, r_max=3),
                                   oracle.bf_brute_sv(f, np.full(f.shape, 3), sigma_r=sr))
