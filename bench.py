@@ -158,6 +158,13 @@ def oracle_rate(step_seconds_budget: float, seed: int = 0):
     return mpx, cores, "; ".join(desc) + " (brute force of eq. (BF), extrapolated per pixel)"
 
 
+def oracle_accuracy(jobs):
+    """Runs the accuracy checks the GPU measurements queued: each job gets the
+    oracle module and returns its errors (max |GPU - oracle| in gray levels)."""
+    import oracle
+    return {name: fn(oracle) for name, fn in jobs}
+
+
 def oracle_table2_rate():
     """The paper's own timing workload (Table 2: 720 x 540, recursive Gaussian,
     sigma_s = 10 and 100) run by the oracle's FP64 O(1) formulation (Algorithm
@@ -363,20 +370,27 @@ def run_ours(args):
                    "on one stream)"}
 
     extras = {}
+    # accuracy checks: the GPU side keeps its outputs at the sampled pixels
+    # here; the oracle computes the references in the CPU-baseline leg
+    acc_jobs = []
     if rank == 0:
-        # ---- accuracy on sampled pixels (outside the timed region)
-        import oracle
         idx = synth.sample_indices(H, W, 1024, seed=3)
-        errs = {}
+        gots = []
         for i, p in enumerate(plans):
             one(i)
             torch.cuda.synchronize()
-            got = outs[i].cpu().numpy().ravel()[idx]
-            ref = oracle.bf_brute_at(img_np.astype(np.float64), idx, sigma_r=SIGMA_R, T=T_RANGE,
-                                     w1=oracle.spatial_w1("box", SIGMA_S[i]))
-            errs["sigma_s=%g" % SIGMA_S[i]] = float(np.abs(got - ref).max())
-        extras["max_abs_err_vs_oracle"] = errs
-        extras["max_abs_err_sample"] = "%d pixels (all borders + 1024 seeded)" % len(idx)
+            gots.append(outs[i].cpu().numpy().ravel()[idx])
+
+        def _c2_acc(oracle, idx=idx, gots=gots):
+            f64 = img_np.astype(np.float64)
+            res = {"sample": "%d pixels (all borders + 1024 seeded)" % len(idx)}
+            for i in range(len(gots)):
+                ref = oracle.bf_brute_at(f64, idx, sigma_r=SIGMA_R, T=T_RANGE,
+                                         w1=oracle.spatial_w1("box", SIGMA_S[i]))
+                res["sigma_s=%g" % SIGMA_S[i]] = float(np.abs(gots[i] - ref).max())
+            return res
+
+        acc_jobs.append(("c2_2048_box_max_abs_err", _c2_acc))
     if rank == 0 and not args.no_extras:
         # ---- unfused baseline on the same workload (fused vs per-term materialised)
         if ws is None:
@@ -402,13 +416,15 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         extras.update(measure_fwd_bwd(bf, torch, dev, stream))
         extras.update(measure_batch(bf, torch, dev, stream))
-        extras.update(measure_configs(bf, torch, dev, stream))
+        extras.update(measure_configs(bf, torch, dev, stream, acc_jobs))
+        extras.update(measure_space_variant(bf, torch, dev, stream, acc_jobs))
         extras.update(measure_table2(bf, torch, dev, stream))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_rate(float(os.environ.get("BF_CPU_SECONDS", "15")))
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu["accuracy_vs_oracle"] = oracle_accuracy(acc_jobs)
         if not args.no_extras:
             cpu["table2_fp64_o1_720x540_ms"] = oracle_table2_rate()
 
@@ -479,13 +495,12 @@ def measure_fwd_bwd(bf, torch, dev, stream):
             "fwd_instr_per_px": gauss_instr_per_px(nz, bool(np.any(w == 0)), 12)}
 
 
-def measure_configs(bf, torch, dev, stream):
-    """Configs 1 and 3: the 256^2 Gaussian forward (N = 30, full-image error
+def measure_configs(bf, torch, dev, stream, acc_jobs):
+    """Configs 1 and 3: the 256^2 Gaussian forward (N = 30; full-image error
     against the oracle) and the 4096^2 x 3 u8 HWC Gaussian forward at
-    sigma_r = 10 (N = 264) and 50 (N = 11), errors on seeded pixels against the
+    sigma_r = 10 (N = 264) and 50 (N = 11) (errors on seeded pixels against the
     raised-cosine oracle and against the Gaussian range kernel it
-    approximates."""
-    import oracle
+    approximates); the errors are queued on ``acc_jobs``."""
     import synth
     res = {}
     img1 = synth.rectangles(256, 256, n_rect=12, noise=10.0, seed=0)
@@ -494,9 +509,14 @@ def measure_configs(bf, torch, dev, stream):
     o1 = torch.empty_like(t1)
     bf.tune(p1, t1, reps=3)
     ms1 = _time(lambda: bf.forward(p1, t1, out=o1), torch, stream, 20)
-    ref1 = oracle.bf_brute(img1.astype(np.float64), sigma_s=3.0, sigma_r=30.0, kind="gauss")
-    res["c1_256_gauss_r9_n30"] = {"ms": ms1, "mpx_s": 256 * 256 / (ms1 * 1e-3) / 1e6,
-                                  "max_abs_err_full_image": float(np.abs(o1.cpu().numpy() - ref1).max())}
+    got1 = o1.cpu().numpy()
+    res["c1_256_gauss_r9_n30"] = {"ms": ms1, "mpx_s": 256 * 256 / (ms1 * 1e-3) / 1e6}
+
+    def _c1_acc(oracle):
+        ref1 = oracle.bf_brute(img1.astype(np.float64), sigma_s=3.0, sigma_r=30.0, kind="gauss")
+        return {"max_abs_err_full_image": float(np.abs(got1 - ref1).max())}
+
+    acc_jobs.append(("c1_256_gauss_r9_n30", _c1_acc))
     img3 = synth.rect_disk_u8(4096, 4096, 3, seed=0)
     t3 = torch.from_numpy(img3).to(dev)
     o3 = torch.empty(t3.shape, dtype=torch.float32, device=dev)
@@ -506,20 +526,58 @@ def measure_configs(bf, torch, dev, stream):
         bf.tune(p3, t3, reps=2)
         ms3 = _time(lambda: bf.forward(p3, t3, out=o3), torch, stream, 3)
         out = o3.cpu().numpy()
-        w1 = oracle.spatial_w1("gauss", 6.0)
-        err = err_g = 0.0
-        for c in range(3):
-            ch = img3[..., c].astype(np.float64)
-            got = out[..., c].ravel()[idx]
-            err = max(err, float(np.abs(got - oracle.bf_brute_at(ch, idx, sigma_r=sr, w1=w1,
-                                                                 N=p3.N)).max()))
-            err_g = max(err_g, float(np.abs(got - oracle.bf_brute_at(
-                ch, idx, sigma_r=sr, w1=w1, range_mode="gaussian")).max()))
-        res["c3_4096x3_u8_gauss_r18_sr%g_n%d" % (sr, p3.N)] = {
-            "ms": ms3, "mpx_s": 3 * 4096 * 4096 / (ms3 * 1e-3) / 1e6,
-            "max_abs_err_vs_oracle": err, "max_abs_err_vs_gaussian_range_kernel": err_g,
-            "error_sample": "%d px x 3 channels (borders + 512 seeded)" % len(idx)}
+        gots = [out[..., c].ravel()[idx] for c in range(3)]
+        key = "c3_4096x3_u8_gauss_r18_sr%g_n%d" % (sr, p3.N)
+        res[key] = {"ms": ms3, "mpx_s": 3 * 4096 * 4096 / (ms3 * 1e-3) / 1e6}
+
+        def _c3_acc(oracle, sr=sr, N=p3.N, gots=gots):
+            w1 = oracle.spatial_w1("gauss", 6.0)
+            err = err_g = 0.0
+            for c in range(3):
+                ch = img3[..., c].astype(np.float64)
+                err = max(err, float(np.abs(gots[c] - oracle.bf_brute_at(
+                    ch, idx, sigma_r=sr, w1=w1, N=N)).max()))
+                err_g = max(err_g, float(np.abs(gots[c] - oracle.bf_brute_at(
+                    ch, idx, sigma_r=sr, w1=w1, range_mode="gaussian")).max()))
+            return {"max_abs_err_vs_oracle": err, "max_abs_err_vs_gaussian_range_kernel": err_g,
+                    "error_sample": "%d px x 3 channels (borders + 512 seeded)" % len(idx)}
+
+        acc_jobs.append((key, _c3_acc))
     return {"configs": res}
+
+
+def measure_space_variant(bf, torch, dev, stream, acc_jobs):
+    """Space-variant extension (Section 4) on the 2048^2 workload image: a
+    smooth seeded radius map in [0, 8] (one box half-width per pixel),
+    sigma_r = 20 (N = 66); ms, Mpixel/s and the FP32 roofline fraction of the
+    algorithmic operations (per pixel and term: phase, f cos, f sin; four
+    summed-area tables of two running sums each and a three-operation box sum;
+    a six-operation combine); the error on seeded pixels is queued on
+    ``acc_jobs``."""
+    import synth
+    img = synth.smooth_field(H, W, noise=5.0, seed=0)
+    rad = synth.radius_map(H, W, 8, seed=1)
+    plan = bf.Plan(2.0, SIGMA_R, T_RANGE, kind="box")
+    t = torch.from_numpy(img).to(dev)
+    rt = torch.from_numpy(rad).to(dev)
+    o = torch.empty_like(t)
+    ms = _time(lambda: bf.forward_space_variant(plan, t, rt, r_max=8, out=o), torch, stream, 5)
+    ops = (29.0 * plan.n_terms + 4.0) * H * W
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    idx = synth.sample_indices(H, W, 1024, seed=7)
+    got = o.cpu().numpy().ravel()[idx]
+
+    def _sv_acc(oracle):
+        ref = oracle.bf_brute_sv_at(img.astype(np.float64), rad, idx, 8, sigma_r=SIGMA_R,
+                                    T=T_RANGE, N=plan.N)
+        return {"max_abs_err_vs_oracle": float(np.abs(got - ref).max()),
+                "error_sample": "%d pixels (all borders + 1024 seeded)" % len(idx)}
+
+    acc_jobs.append(("space_variant_2048_r0to8", _sv_acc))
+    return {"space_variant_2048_r0to8": {
+        "ms": ms, "mpx_s": H * W / (ms * 1e-3) / 1e6, "terms": plan.n_terms,
+        "achieved_tinstr_s": ops / (ms * 1e-3) / 1e12, "frac": ops / (ms * 1e-3) / peak}}
 
 
 # Table 2 of the paper: ms per 720 x 540 grayscale image with the recursive
@@ -589,7 +647,10 @@ def run_extras_only(which):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    fn = {"fwd_bwd": measure_fwd_bwd, "batch": measure_batch, "configs": measure_configs,
+    jobs = []  # accuracy checks need the oracle: not run on this profiling path
+    fn = {"fwd_bwd": measure_fwd_bwd, "batch": measure_batch,
+          "configs": lambda *a: measure_configs(*a, jobs),
+          "space_variant": lambda *a: measure_space_variant(*a, jobs),
           "table2": measure_table2}[which]
     print(json.dumps({"extras_only": which, **fn(bf, torch, dev, stream)}), flush=True)
     return 0
@@ -606,7 +667,8 @@ def main():
                     help="skip the unfused baseline and the other workloads")
     ap.add_argument("--sigma-s", default=None,
                     help="comma-separated subset of the workload's sigma_s values (profiling runs)")
-    ap.add_argument("--extras-only", choices=["fwd_bwd", "batch", "configs", "table2"],
+    ap.add_argument("--extras-only",
+                    choices=["fwd_bwd", "batch", "configs", "space_variant", "table2"],
                     default=None,
                     help="time only that extra workload and print its figures (profiling runs; "
                          "not the benchmark line)")

@@ -202,6 +202,32 @@ bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *ou
                      cudaStream_t stream);
 
 /*
+ * Space-variant extension (Section 4): the range kernel of `plan` with a
+ * spatial kernel that changes from pixel to pixel -- pixel x averages over its
+ * own (2 r(x) + 1) x (2 r(x) + 1) box of the clamp-extended image (equal
+ * weights, which cancel in the ratio):
+ *     out(x) = sum_{|y|_inf <= r(x)} phi(f(x-y) - f(x)) f(x-y)
+ *              / sum_{|y|_inf <= r(x)} phi(f(x-y) - f(x)).
+ * Computed through eq. (final-form) with per-term summed-area tables of the
+ * auxiliary images (64-bit fixed point, so every box sum is exact for the
+ * fixed-point planes), O(1) per pixel and term whatever r(x).  The plan's own
+ * spatial kernel is not used; its range kernel (raised cosine or cosine
+ * polynomial) is.
+ *   in               : device image, H x W, single channel, type dt, rows
+ *                      row_stride_elems (>= W) elements apart
+ *   radius           : device int32 H x W, row-major (row stride W): the
+ *                      half-widths r(x); values are clamped into [0, r_max]
+ *   r_max            : 0 <= r_max <= 16, the largest half-width used (it sets
+ *                      the halo each tile reads; smaller is faster)
+ *   out              : device float H x W, row stride W
+ * Asynchronous on `stream`.  Errors: BF_EINVAL (NULL pointers, sizes,
+ * r_max), BF_EUNSUPPORTED (image too large), BF_ECUDA (launch failure).
+ */
+bf_status bf_forward_space_variant(const bf_plan *plan, const void *in, bf_dtype dt,
+                                   const int *radius, int r_max, float *out, int H, int W,
+                                   long long row_stride_elems, cudaStream_t stream);
+
+/*
  * bf_forward for an image in HOST memory (not in the paper): in stream order,
  * copies host_in into the caller's device buffer dev_in, filters dev_in into
  * the caller's device buffer dev_out as bf_forward does, and copies dev_out

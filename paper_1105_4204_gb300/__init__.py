@@ -5,8 +5,8 @@ sm_103a by ``build.build()``); this package is its thin Python binding.
 """
 from .api import (BOX, GAUSS, Batch, BilateralFunction, Plan, backward, bilateral,  # noqa: F401
                   backward_stack, forward, forward_host, forward_stack, forward_unfused,
-                  fp32_pipe_rate, set_shape, tune)
+                  forward_space_variant, fp32_pipe_rate, set_shape, tune)
 
 __all__ = ["Plan", "forward", "forward_stack", "forward_host", "forward_unfused", "backward",
-           "backward_stack", "bilateral", "tune", "set_shape", "fp32_pipe_rate",
+           "backward_stack", "bilateral", "tune", "set_shape", "fp32_pipe_rate", "forward_space_variant",
            "BilateralFunction", "Batch", "GAUSS", "BOX"]

@@ -175,6 +175,27 @@ def set_shape(plan: Plan, img: torch.Tensor, shape: str):
     check(lib().bf_forward_set_shape(plan.handle, H, W, C, SHAPES[shape]))
 
 
+def forward_space_variant(plan: Plan, img: torch.Tensor, radius: torch.Tensor, r_max: int = 16,
+                          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Space-variant filter (Section 4): pixel x averages over its own box of
+    half-width radius[x] (int32 H x W on the device, clamped into [0, r_max]),
+    with the plan's range kernel.  Single channel; r_max <= 16 (smaller reads
+    less halo)."""
+    dt, H, W, C, rs = _image_args(img)
+    if C != 1 or img.dim() != 2:
+        raise ValueError("the space-variant filter takes a single-channel H x W image")
+    if radius.dtype != torch.int32 or tuple(radius.shape) != (H, W) or not radius.is_contiguous() \
+            or radius.device != img.device:
+        raise ValueError("radius must be a contiguous int32 H x W tensor on the image's device")
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    check(lib().bf_forward_space_variant(plan.handle, ctypes.c_void_p(img.data_ptr()), dt,
+                                         ctypes.c_void_p(radius.data_ptr()), int(r_max),
+                                         ctypes.c_void_p(out.data_ptr()), H, W, rs,
+                                         _stream_ptr(stream)))
+    return out
+
+
 def fp32_pipe_rate(paired: bool = False, stream=None) -> float:
     """Measured FP32 lane operations per second of the current device (an FMA
     counts as one; ``paired`` issues them as FFMA2).  Synchronises the

@@ -140,6 +140,26 @@ extern "C" bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt
     return forward_planes(plan, img, stream, "bf_forward");
 }
 
+extern "C" bf_status bf_forward_space_variant(const bf_plan *plan, const void *in, bf_dtype dt,
+                                              const int *radius, int r_max, float *out, int H,
+                                              int W, long long row_stride_elems,
+                                              cudaStream_t stream) {
+    const char *who = "bf_forward_space_variant";
+    if (!plan) return fail(BF_EINVAL, std::string(who) + ": plan is NULL");
+    if (!in || !out || !radius) return fail(BF_EINVAL, std::string(who) + ": a pointer is NULL");
+    if (H < 1 || W < 1) return fail(BF_EINVAL, std::string(who) + ": H and W must be >= 1");
+    if (dt != BF_F32 && dt != BF_U8) return fail(BF_EINVAL, std::string(who) + ": unknown dtype");
+    if (row_stride_elems < W) return fail(BF_EINVAL, std::string(who) + ": row_stride_elems < W");
+    if (r_max < 0 || r_max > sv_max_radius())
+        return fail(BF_EINVAL, std::string(who) + ": r_max must be in [0, " +
+                                   std::to_string(sv_max_radius()) + "]");
+    if ((long long)H * W > (1LL << 31) / 4)
+        return fail(BF_EUNSUPPORTED, std::string(who) + ": image too large");
+    return cuda_check(launch_space_variant(plan, in, (int)dt, row_stride_elems, radius, r_max,
+                                           out, H, W, stream),
+                      who);
+}
+
 extern "C" bf_status bf_forward_host(const bf_plan *plan, const void *host_in, bf_dtype dt,
                                      void *dev_in, float *dev_out, float *host_out, int H, int W,
                                      int C, long long row_stride_elems, cudaStream_t stream) {

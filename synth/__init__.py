@@ -16,7 +16,7 @@ import numpy as np
 
 __all__ = [
     "rectangles", "smooth_field", "rect_disk_u8", "batch_specs", "batch_images",
-    "upstream", "sample_indices",
+    "upstream", "sample_indices", "radius_map",
 ]
 
 
@@ -130,3 +130,20 @@ def sample_indices(H: int, W: int, n_interior: int, seed: int = 0,
     picks = rng.choice(H * W, size=n_interior, replace=False)
     idx.update(int(p) for p in picks)
     return np.array(sorted(idx), dtype=np.int64)
+
+
+def radius_map(H: int, W: int, r_max: int, seed: int = 0, smooth: bool = True) -> np.ndarray:
+    """int32 H x W map of box half-widths in [0, r_max] for the space-variant
+    filter: a seeded smooth field (a few random 2-D sinusoids) quantised to
+    the integers 0 .. r_max, or (``smooth=False``) independent uniform draws."""
+    rng = np.random.default_rng(seed)
+    if not smooth:
+        return rng.integers(0, r_max + 1, size=(H, W)).astype(np.int32)
+    yy = np.arange(H, dtype=np.float64)[:, None]
+    xx = np.arange(W, dtype=np.float64)[None, :]
+    v = np.zeros((H, W), dtype=np.float64)
+    for _ in range(4):
+        ky, kx = rng.uniform(-0.02, 0.02, size=2)
+        v += np.sin(ky * yy + kx * xx + rng.uniform(0, 2 * np.pi))
+    v = (v - v.min()) / max(v.max() - v.min(), 1e-9)
+    return np.rint(v * r_max).astype(np.int32)

@@ -277,3 +277,18 @@ def test_forward_host_rejects_bad_arguments_without_touching_a_gpu(bf):
     assert b"dev_in" in l.bf_last_error()
     assert l.bf_forward_host(p.handle, fake, 0, fake, fake, fake, 16, 16, 1, 8, null) == 1
     assert l.bf_forward_host(p.handle, fake, 0, fake, fake, fake, 16, 16, 5, 80, null) == 2
+
+
+def test_space_variant_rejects_bad_arguments_without_touching_a_gpu(bf):
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    p = bf.Plan(2.0, 20.0)
+    fake = ctypes.c_void_p(0x1000)
+    null = ctypes.c_void_p(0)
+    assert l.bf_forward_space_variant(p.handle, fake, 0, null, 4, fake, 16, 16, 16, null) == 1
+    assert l.bf_forward_space_variant(p.handle, fake, 0, fake, 17, fake, 16, 16, 16, null) == 1
+    assert b"r_max" in l.bf_last_error()
+    assert l.bf_forward_space_variant(p.handle, fake, 0, fake, -1, fake, 16, 16, 16, null) == 1
+    assert l.bf_forward_space_variant(p.handle, fake, 0, fake, 4, fake, 16, 16, 8, null) == 1
+    assert l.bf_forward_space_variant(p.handle, fake, 0, fake, 4, fake, 16384, 32769, 32769,
+                                      null) == 2
