@@ -6,25 +6,28 @@
 // section names; Crow's tables).
 //
 // One CTA owns a kSvT x kSvT output tile.  It reads the tile plus a halo of RM
-// (clamp-to-edge) once, then for every term:
-//   1. generates the auxiliary planes (cos, sin, f cos, f sin) over the
-//      extended tile and stores them as 64-bit fixed-point integers (value *
-//      2^26, rounded) in tables whose row 0 and column 0 stay zero;
-//   2. turns them into summed-area tables (running sums along rows, then
-//      along columns, a thread per line);
-//   3. reads each own pixel's box sums from four entries of each table and
-//      accumulates a_m (cos(w f(x)) S[cos] + sin(w f(x)) S[sin]) into Q and
-//      a_m (cos(w f(x)) S[f cos] + sin(w f(x)) S[f sin]) into P.
-// The tables are built two at a time (NTAB = 2: (cos, sin), then (f cos,
-// f sin), regenerating the sines): half the shared memory doubles the
-// resident blocks, which measured faster than building all four at once
-// (r_max = 8 on 2048^2: 3.31 vs 3.54 ms).
+// (clamp-to-edge) once, then for every term and for each of the two pairs
+// (cos, sin) -> Q and (f cos, f sin) -> P:
+//   1. generates the pair's planes over the extended tile and stores each
+//      value as the fixed-point integer q = round(v * 2^26), split as
+//      q = hi * 2^20 + lo (|hi| <= 2^14, |lo| <= 2^19), in two 32-bit tables
+//      per plane whose row 0 and column 0 stay zero;
+//   2. turns the four tables into summed-area tables (running sums along
+//      rows, then along columns, a thread per line) in wrapping 32-bit
+//      arithmetic;
+//   3. reads each own pixel's box sums from four entries of each table --
+//      exact, since a box of at most 33 x 33 keeps both halves' sums inside
+//      32 bits -- and accumulates a_m (cos(w f(x)) S[. cos] + sin(w f(x))
+//      S[. sin]) into Q or P.
 // Integer tables make every box sum exact for the fixed-point planes (no
 // cancellation between large prefix sums, which in FP32 would lose the small
 // boxes); the fixed-point step is 2^-26 (1.5e-8 of a unit plane value, below
-// the FP32 sine's own error), and the largest table entry, 255 * 2^26 *
-// (kSvT + 2 RM)^2 < 2^56, fits.  HBM sees f and the radius map read once and
-// out written once.
+// the FP32 sine's own error).  The split into 32-bit halves is done with FP32
+// additions (adding 1.5 * 2^23 to a float below 2^22 rounds it to the nearest
+// integer and leaves that integer in its low mantissa bits), because
+// conversions between FP32 and 64-bit integers run on the FP64 pipe, which
+// on this GPU is narrow: with 64-bit tables they were the kernel's limit.
+// HBM sees f and the radius map read once and out written once.
 #include <cstdint>
 
 #include "bf_internal.h"
@@ -50,24 +53,36 @@ struct SvParams {
     BfTerms terms;
 };
 
-template <int RM, int NTAB>
+// round(v * 2^26) = hi * 2^20 + lo for |v| < 2^8, exactly, by FP32 additions.
+__device__ __forceinline__ void fixed_split(float v, unsigned &hi, unsigned &lo) {
+    constexpr float kM = 12582912.f;  // 1.5 * 2^23
+    const float x = v * kSvScale;     // exact (a power of two)
+    const float th = __fadd_rn(x * 9.5367431640625e-07f, kM);  // round(x / 2^20) + kM
+    hi = (unsigned)(__float_as_int(th) - __float_as_int(kM));
+    // x - round(x / 2^20) 2^20 is representable: the FMA is exact
+    const float l = __fmaf_rn(-__fsub_rn(th, kM), 1048576.f, x);
+    lo = (unsigned)(__float_as_int(__fadd_rn(l, kM)) - __float_as_int(kM));
+}
+
+template <int RM>
 struct SvGeom {
     static constexpr int E = kSvT + 2 * RM;  // extended tile edge
     static constexpr int ES = E + 1;         // table edge (zero row / column first)
+    static constexpr int NT = 4;             // tables per pass: (hi, lo) of two planes
     static constexpr size_t SMEM =
-        sizeof(long long) * NTAB * ES * ES + sizeof(float) * E * E;
-    static_assert(NTAB == 2 || NTAB == 4, "tables per pass");
-    static_assert(NTAB * E <= kSvThreads, "a thread per table line");
+        sizeof(unsigned) * NT * ES * ES + sizeof(float) * E * E;
+    static_assert(NT * E <= kSvThreads, "a thread per table line");
 };
 
-template <int RM, int NTAB>
+template <int RM>
 __global__ void __launch_bounds__(kSvThreads) bf_sv_fwd(const __grid_constant__ SvParams p) {
-    using G = SvGeom<RM, NTAB>;
-    constexpr int E = G::E, ES = G::ES;
+    using G = SvGeom<RM>;
+    constexpr int E = G::E, ES = G::ES, NT = G::NT;
     constexpr int TS = ES * ES;  // entries per table
-    extern __shared__ long long sv_smem[];
-    long long *Tb = sv_smem;                                     // NTAB tables
-    float *Fs = reinterpret_cast<float *>(Tb + NTAB * TS);       // E x E extended f tile
+    extern __shared__ unsigned sv_smem[];
+    // tables: 0 hi / 1 lo of the pair's first plane, 2 hi / 3 lo of its second
+    unsigned *Tb = sv_smem;
+    float *Fs = reinterpret_cast<float *>(Tb + NT * TS);  // E x E extended f tile
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kSvT, y0 = blockIdx.y * kSvT;
@@ -83,9 +98,9 @@ __global__ void __launch_bounds__(kSvThreads) bf_sv_fwd(const __grid_constant__ 
     }
     for (int k = tid; k < ES; k += kSvThreads) {  // the zero row and column of every table
 #pragma unroll
-        for (int t = 0; t < NTAB; ++t) {
-            Tb[t * TS + k] = 0;
-            Tb[t * TS + k * ES] = 0;
+        for (int t = 0; t < NT; ++t) {
+            Tb[t * TS + k] = 0u;
+            Tb[t * TS + k * ES] = 0u;
         }
     }
 
@@ -122,9 +137,8 @@ __global__ void __launch_bounds__(kSvThreads) bf_sv_fwd(const __grid_constant__ 
             __sincosf(kTwoPi * rr, &sx[k], &cx[k]);
         }
 #pragma unroll 1
-        for (int pass = 0; pass < 4 / NTAB; ++pass) {
-            // 1. planes (pass * NTAB ...) of (cos, sin, f cos, f sin), fixed
-            //    point, at table entry (i + 1, j + 1)
+        for (int pass = 0; pass < 2; ++pass) {  // 0: (cos, sin) -> Q; 1: (f cos, f sin) -> P
+            // 1. the pair's planes, fixed point, at table entry (i + 1, j + 1)
             for (int idx = tid; idx < E * E; idx += kSvThreads) {
                 const int i = idx / E, j = idx - (idx / E) * E;
                 const float fv = Fs[idx];
@@ -132,31 +146,28 @@ __global__ void __launch_bounds__(kSvThreads) bf_sv_fwd(const __grid_constant__ 
                 rr = rr - rintf(rr);
                 float sn, cs;
                 __sincosf(kTwoPi * rr, &sn, &cs);
-                long long *e0 = Tb + (i + 1) * ES + j + 1;
-                if (NTAB == 4 || pass == 0) {
-                    e0[0] = __float2ll_rn(cs * kSvScale);
-                    e0[TS] = __float2ll_rn(sn * kSvScale);
+                if (pass == 1) {
+                    cs = cs * fv;
+                    sn = sn * fv;
                 }
-                if (NTAB == 4 || pass == 1) {
-                    constexpr int o = NTAB == 4 ? 2 * TS : 0;
-                    e0[o] = __float2ll_rn((cs * fv) * kSvScale);
-                    e0[o + TS] = __float2ll_rn((sn * fv) * kSvScale);
-                }
+                unsigned *e0 = Tb + (i + 1) * ES + j + 1;
+                fixed_split(cs, e0[0], e0[TS]);
+                fixed_split(sn, e0[2 * TS], e0[3 * TS]);
             }
             __syncthreads();
             // 2. summed-area tables: rows, then columns (a thread per line)
-            if (tid < NTAB * E) {
-                long long *row = Tb + (tid / E) * TS + (tid % E + 1) * ES;
-                long long run = 0;
+            if (tid < NT * E) {
+                unsigned *row = Tb + (tid / E) * TS + (tid % E + 1) * ES;
+                unsigned run = 0u;
                 for (int j = 1; j < ES; ++j) {
                     run += row[j];
                     row[j] = run;
                 }
             }
             __syncthreads();
-            if (tid < NTAB * E) {
-                long long *col = Tb + (tid / E) * TS + tid % E + 1;
-                long long run = 0;
+            if (tid < NT * E) {
+                unsigned *col = Tb + (tid / E) * TS + tid % E + 1;
+                unsigned run = 0u;
                 for (int i = 1; i < ES; ++i) {
                     run += col[i * ES];
                     col[i * ES] = run;
@@ -170,23 +181,19 @@ __global__ void __launch_bounds__(kSvThreads) bf_sv_fwd(const __grid_constant__ 
                 const int r = rad[k];
                 const int a0 = RM + pi - r, a1 = RM + pi + r + 1;
                 const int b0 = RM + pj - r, b1 = RM + pj + r + 1;
-                float bs[NTAB];
+                float bs[2];
 #pragma unroll
-                for (int t = 0; t < NTAB; ++t) {
-                    const long long *T = Tb + t * TS;
-                    const long long sum = T[a1 * ES + b1] - T[a0 * ES + b1] - T[a1 * ES + b0] +
-                                          T[a0 * ES + b0];
-                    bs[t] = __ll2float_rn(sum) * kSvInvScale;
+                for (int q = 0; q < 2; ++q) {
+                    const unsigned *Th = Tb + (2 * q) * TS, *Tl = Th + TS;
+                    const int sh = (int)(Th[a1 * ES + b1] - Th[a0 * ES + b1] - Th[a1 * ES + b0] +
+                                         Th[a0 * ES + b0]);
+                    const int sl = (int)(Tl[a1 * ES + b1] - Tl[a0 * ES + b1] - Tl[a1 * ES + b0] +
+                                         Tl[a0 * ES + b0]);
+                    bs[q] = fmaf(__int2float_rn(sh), 1048576.f, __int2float_rn(sl)) * kSvInvScale;
                 }
-                const float vq = am * fmaf(cx[k], bs[0], sx[k] * bs[1]);
-                if (NTAB == 4) {
-                    Q[k] += vq;
-                    P[k] += am * fmaf(cx[k], bs[2], sx[k] * bs[3]);
-                } else if (pass == 0) {
-                    Q[k] += vq;
-                } else {
-                    P[k] += vq;
-                }
+                const float v = am * fmaf(cx[k], bs[0], sx[k] * bs[1]);
+                if (pass == 0) Q[k] += v;
+                else P[k] += v;
             }
             __syncthreads();  // the tables are rewritten next
         }
@@ -198,21 +205,21 @@ __global__ void __launch_bounds__(kSvThreads) bf_sv_fwd(const __grid_constant__ 
     }
 }
 
-template <int RM, int NTAB>
+template <int RM>
 cudaError_t launch_sv(const SvParams &prm, cudaStream_t s) {
-    using G = SvGeom<RM, NTAB>;
+    using G = SvGeom<RM>;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(bf_sv_fwd<RM, NTAB>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+        e = cudaFuncSetAttribute(bf_sv_fwd<RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)G::SMEM);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     dim3 grid((prm.W + kSvT - 1) / kSvT, (prm.H + kSvT - 1) / kSvT);
-    bf_sv_fwd<RM, NTAB><<<grid, kSvThreads, G::SMEM, s>>>(prm);
+    bf_sv_fwd<RM><<<grid, kSvThreads, G::SMEM, s>>>(prm);
     return cudaGetLastError();
 }
 
@@ -233,9 +240,9 @@ cudaError_t launch_space_variant(const bf_plan *pl, const void *in, int dtype,
     prm.H = H;
     prm.W = W;
     fill_terms(pl, &prm.terms);
-    if (r_max <= 4) return launch_sv<4, 2>(prm, s);
-    if (r_max <= 8) return launch_sv<8, 2>(prm, s);
-    return launch_sv<16, 2>(prm, s);
+    if (r_max <= 4) return launch_sv<4>(prm, s);
+    if (r_max <= 8) return launch_sv<8>(prm, s);
+    return launch_sv<16>(prm, s);
 }
 
 }  // namespace bf
