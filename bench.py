@@ -42,6 +42,13 @@ T_RANGE = 255.0
 WORKLOAD = ("2048x2048 f32 smooth field (20 sinusoids + regions + noise 5, seed 0), "
             "3-pass box sigma_s in {2, 8, 32} (r = 2, 8, 32), sigma_r = 20 (N = 66), T = 255, "
             "clamp-to-edge; 3 forwards per step")
+# DRAM bytes per call (dram__bytes_read.sum + dram__bytes_write.sum over the
+# call's kernels, one ncu capture of this workload each; the captures and
+# commands are in profiles/): sigma_s = 2 and 8, one fused tile kernel that
+# reads f once (its out writes leave L2 after the kernel); sigma_s = 32,
+# lr_transpose + lr_vert + lr_horz + lr_final, dominated by the 4 x 34
+# filtered planes written and read back.
+DRAM_BYTES_PER_CALL = {2.0: 16.84e6, 8.0: 16.84e6, 32.0: 5.664e9}
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -319,13 +326,17 @@ def run_ours(args):
         instr = box_instr_per_px(nz, bool(np.any(w == 0))) * H * W
         ach = instr / (call_ms[i] * 1e-3)
         rl.append({"sigma_s": SIGMA_S[i], "r": p.radius // 3,
+                   "dram_bytes_ncu": DRAM_BYTES_PER_CALL.get(SIGMA_S[i]),
+                   "algorithmic_bytes": 8.0 * H * W,
                    "kernel": "bf_tile_fwd" if p.radius // 3 <= 8
                    else "streaming sweeps (lr_transpose, lr_vert, lr_horz, lr_final)",
                    "ms": float(call_ms[i]), "achieved_tinstr_s": ach / 1e12,
                    "frac": ach / peak_instr})
     roofline = {"bound": "alu", "achieved": rl[dom]["achieved_tinstr_s"],
                 "peak": peak_instr / 1e12, "unit": "T FP32-pipe instr/s",
-                "frac": rl[dom]["frac"], "traffic": None,
+                "frac": rl[dom]["frac"], "traffic": rl[dom]["dram_bytes_ncu"],
+                "traffic_note": "DRAM bytes per call of the dominant call's kernels from ncu "
+                                "(profiles/); algorithmic bytes are 8 per pixel (f in, out out)",
                 "kernel": rl[dom]["kernel"], "per_call": rl,
                 "peak_note": "SMs x 128 FP32 lanes x max SM clock %.0f MHz (%s)" % (
                     peaks.get("sm_max_mhz", SM_MAX_MHZ), peak_kind),
