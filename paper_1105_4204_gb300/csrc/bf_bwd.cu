@@ -64,10 +64,8 @@ cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, c
     for (int k = 0; k < prm.terms.n_terms; ++k) prm.omega[k] = (float)pl->omega[k];
     for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) prm.taps.w[k] = 0.f;
     for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) prm.tail[k] = 0.f;
-    int halo;
     if (pl->kind == BF_SPATIAL_GAUSS_TRUNC) {
         const int Ri = gauss_bwd_radius(pl->R);
-        halo = Ri;
         for (int k = 0; k < 2 * pl->R + 1; ++k) prm.taps.w[k + Ri - pl->R] = pl->w1f[k];
         // T(d) = sum_{e >= d} w1(e), d = 0 .. R
         double t = 0.0;
@@ -80,7 +78,6 @@ cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, c
     } else {
         // box: unnormalised integer-count taps, normalisation applied at the end
         const int r = pl->r_box;
-        halo = 3 * r;
         const double L = 2.0 * r + 1.0;
         const double norm = L * L * L;
         double t = 0.0;
@@ -91,7 +88,6 @@ cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, c
         prm.scale = pl->q_scale;
         prm.total = (float)norm;
     }
-    (void)halo;
     pair_taps(&prm.taps);
     cudaError_t e;
     if (pl->kind == BF_SPATIAL_GAUSS_TRUNC) {
