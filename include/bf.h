@@ -109,9 +109,10 @@ typedef struct bf_plan bf_plan;
  *   T        : dynamic range bound of the image values, > 0 (255 for 8-bit)
  *   kind     : spatial kernel
  *   opts     : NULL for defaults
- * Errors: BF_EINVAL for non-positive or non-finite sigma/T or a NULL out;
- *         BF_EUNSUPPORTED for N > 1024, a support radius above the kernels'
- *         limits, or box_passes other than 3.
+ * Errors: BF_EINVAL for non-positive or non-finite sigma/T, a NULL out, a
+ *         negative option or an unknown degree_rule; BF_EUNSUPPORTED for
+ *         N > 1024, a support radius above the kernels' limits, or
+ *         box_passes other than 3.
  */
 bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_r, double T,
                          bf_spatial_kind kind, const bf_plan_opts *opts);
@@ -123,7 +124,8 @@ bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_r, double T
  * of which the raised cosine of bf_plan_create is one instance.  Everything
  * else -- spatial kernel, tile and streaming kernels, stacks, batches, the
  * backward pass for dL/df -- is shared with raised-cosine plans.
- *   sigma_s, kind, opts : as in bf_plan_create (opts->N_override must be 0)
+ *   sigma_s, kind, opts : as in bf_plan_create (opts->N_override and
+ *                         opts->degree_rule must be 0)
  *   gamma               : base angular frequency in radians per gray level, > 0
  *   a                   : host array of n_coef real coefficients (copied)
  *   n_coef              : 1 <= n_coef <= 1025
@@ -134,7 +136,8 @@ bf_status bf_plan_create(bf_plan **out, double sigma_s, double sigma_r, double T
  * FP32.  bf_backward and its variants reject grad_sigma_r for such a plan
  * (BF_EINVAL): it has no sigma_r.
  * Errors: BF_EINVAL for NULL pointers, gamma or sigma_s not finite and > 0,
- *         non-finite coefficients, all coefficients 0, or N_override set;
+ *         non-finite coefficients, all coefficients 0, or N_override or
+ *         degree_rule set;
  *         BF_EUNSUPPORTED for n_coef > 1025 or a support beyond the kernels.
  */
 bf_status bf_plan_create_cosine(bf_plan **out, double sigma_s, double gamma, const double *a,
