@@ -127,6 +127,9 @@ def _load():
         lib.or_bf_brute_sv.restype = None
         lib.or_bf_brute_sv.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
+        lib.or_bf_brute_sv_cos.restype = None
+        lib.or_bf_brute_sv_cos.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
+                                           ctypes.c_double, _dp, ctypes.c_int, _dp]
         lib.or_bf_brute_sv_at.restype = None
         lib.or_bf_brute_sv_at.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, _llp,
@@ -259,6 +262,22 @@ def bf_brute_sv(f, radius, sigma_r=30.0, T=255.0, r_max=None, N=None,
     lib.or_bf_brute_sv(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max),
                        _range_mode(range_mode), float(sigma_r), int(N), _ptr(o), _ptr(q))
     return (o, q) if return_q else o
+
+
+def bf_brute_sv_cos(f, radius, gamma, coefs, r_max=None):
+    """Space-variant brute force with a general cosine kernel (Section 2.2),
+    phi(s) = sum_n coefs[n] cos(n gamma s)."""
+    lib = _load()
+    x = _f64(f)
+    H, W = x.shape
+    rad = np.ascontiguousarray(np.asarray(radius, dtype=np.int32))
+    a = np.ascontiguousarray(np.asarray(coefs, dtype=np.float64).ravel())
+    if r_max is None:
+        r_max = int(rad.max()) if rad.size else 0
+    o = np.empty((H, W), dtype=np.float64)
+    lib.or_bf_brute_sv_cos(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max), float(gamma),
+                           _ptr(a), len(a), _ptr(o))
+    return o
 
 
 def bf_brute_sv_at(f, radius, idx, r_max, sigma_r=30.0, T=255.0, N=None,

@@ -295,6 +295,18 @@ void or_bf_brute_sv(const double *f, int H, int W, const int *radius, int r_max,
                      q_out ? q_out + (size_t)i * W + j : NULL);
 }
 
+/* The space-variant filter with a general cosine kernel (Section 2.2),
+ * phi(s) = sum_n a[n] cos(n gamma s), evaluated term by term. */
+void or_bf_brute_sv_cos(const double *f, int H, int W, const int *radius, int r_max,
+                        double gamma, const double *a, int n_coef, double *out)
+{
+    or_range rg = or_make_cos_range(gamma, a, n_coef);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < H; i++)
+        for (int j = 0; j < W; j++)
+            or_sv_at(f, H, W, radius, r_max, &rg, i, j, out + (size_t)i * W + j, NULL);
+}
+
 /* The space-variant filter at a list of flat pixel indices only. */
 void or_bf_brute_sv_at(const double *f, int H, int W, const int *radius, int r_max, int mode,
                        double sigma_r, int N, const long long *idx, long long n_idx,

@@ -527,3 +527,22 @@ def test_space_variant_matches_a_python_loop(oracle):
     # radii are clamped into [0, r_max]
     np.testing.assert_array_equal(oracle.bf_brute_sv(f, rad + 10, sigma_r=sr, r_max=3),
                                   oracle.bf_brute_sv(f, np.full(f.shape, 3), sigma_r=sr))
+
+
+def test_space_variant_cosine_kernel_agrees_with_the_power_form(oracle):
+    # the raised cosine written as its cosine polynomial gives the power-form
+    # space-variant filter; a constant radius gives the one-box cosine filter
+    f = _small_image(14, 17, seed=12)
+    rad = np.random.default_rng(6).integers(0, 4, size=f.shape)
+    sr = 40.0
+    N = oracle.n_rule(sr)
+    gamma = 1.0 / (sr * math.sqrt(N))
+    coefs = np.zeros(N + 1)
+    for n in range(N + 1):  # cos^N x = 2^-N sum_n C(N,n) cos((2n - N) x)
+        k = abs(2 * n - N)
+        coefs[k] += math.comb(N, n) / 2.0 ** N
+    np.testing.assert_allclose(oracle.bf_brute_sv_cos(f, rad, gamma, coefs),
+                               oracle.bf_brute_sv(f, rad, sigma_r=sr), rtol=1e-11)
+    w1 = oracle.spatial_w1("box", 1.0, radius=2, passes=1)
+    np.testing.assert_allclose(oracle.bf_brute_sv_cos(f, np.full(f.shape, 2), gamma, coefs),
+                               oracle.bf_brute_cos(f, gamma, coefs, w1=w1), rtol=1e-11)
