@@ -102,3 +102,19 @@ def test_full_size_sampled_and_deterministic(bf, oracle):
     err = np.abs(out.ravel()[idx] - ref).max()
     print("space-variant 2048^2 max abs err %.3e over %d px" % (err, len(idx)))
     assert err <= TOL
+
+
+@pytest.mark.parametrize("coefs", [
+    np.array([1.0] + [2.0 * (1.0 - n / 7.0) for n in range(1, 7)]) / 7.0,  # Fejer, N = 6
+    np.array([1.0, 0.8, 0.5, 0.3, 0.1]),
+])
+def test_general_cosine_kernel(bf, oracle, coefs):
+    # Section 2.2's general kernel through the space-variant path
+    import math
+    gamma = math.pi / 510
+    img = synth.rectangles(58, 91, n_rect=6, noise=10.0, seed=13)
+    rad = synth.radius_map(58, 91, 12, seed=14, smooth=False)
+    plan = bf.Plan.cosine(2.0, gamma, coefs, kind="box")
+    out = _sv(bf, img, rad, plan, 12)
+    ref = oracle.bf_brute_sv_cos(img, rad, gamma, coefs, r_max=12)
+    assert np.abs(out - ref).max() <= TOL
