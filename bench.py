@@ -324,9 +324,16 @@ def run_ours(args):
         nz = int(np.sum(w > 0))
         instr = box_instr_per_px(nz, bool(np.any(w == 0))) * H * W
         ach = instr / (call_ms[i] * 1e-3)
+        dram = DRAM_BYTES_PER_CALL.get(SIGMA_S[i])
+        sec = call_ms[i] * 1e-3
         rl.append({"sigma_s": SIGMA_S[i], "r": p.radius // 3,
-                   "dram_bytes_ncu": DRAM_BYTES_PER_CALL.get(SIGMA_S[i]),
+                   "dram_bytes_ncu": dram,
                    "algorithmic_bytes": 8.0 * H * W,
+                   "hbm": {"algorithmic_gbs": 8.0 * H * W / sec / 1e9,
+                           "dram_gbs": dram / sec / 1e9 if dram else None,
+                           "peak_gbs": peaks.get("hbm_gbs", 6800.0),
+                           "dram_frac": (dram / sec / 1e9 / peaks.get("hbm_gbs", 6800.0)
+                                         if dram else None)},
                    "kernel": "bf_tile_fwd" if p.radius // 3 <= 8
                    else "streaming sweeps (lr_transpose, lr_vert, lr_horz, lr_final)",
                    "ms": float(call_ms[i]), "achieved_tinstr_s": ach / 1e12,
