@@ -580,14 +580,19 @@ __global__ void __launch_bounds__(kVCols * kVB) rg_vert(const __grid_constant__ 
         s1[q] = x0[q];
         s2[q] = s3[q] = make_float2(0.f, 0.f);
     }
-    float cur[kChunk], nxt[kChunk];
+    // f of the chunk being filtered and of the next two (loads issued two
+    // chunks ahead: with few terms the sweep has few warps to hide latency)
+    float cur[kChunk], nxt[kChunk], nx2[kChunk];
 #pragma unroll
-    for (int d = 0; d < kChunk; ++d) cur[d] = fval(d);
+    for (int d = 0; d < kChunk; ++d) {
+        cur[d] = fval(d);
+        nxt[d] = fval(kChunk + d);
+    }
     float2 st[2][kChunk];
     // causal, rows 0 .. E-1 (the last chunk's rows past E keep the state)
     for (int e0 = 0; e0 < E; e0 += kChunk) {
 #pragma unroll
-        for (int d = 0; d < kChunk; ++d) nxt[d] = fval(e0 + kChunk + d);
+        for (int d = 0; d < kChunk; ++d) nx2[d] = fval(e0 + 2 * kChunk + d);
 #pragma unroll
         for (int d = 0; d < kChunk; ++d) {
             if (e0 + d < E) {
@@ -610,7 +615,10 @@ __global__ void __launch_bounds__(kVCols * kVB) rg_vert(const __grid_constant__ 
             }
         }
 #pragma unroll
-        for (int d = 0; d < kChunk; ++d) cur[d] = nxt[d];
+        for (int d = 0; d < kChunk; ++d) {
+            cur[d] = nxt[d];
+            nxt[d] = nx2[d];
+        }
     }
     // anticausal, rows E-1 .. 0, from the steady state of w(E-1), in place
     float2 t1[2], t2[2], t3[2];
@@ -634,11 +642,14 @@ __global__ void __launch_bounds__(kVCols * kVB) rg_vert(const __grid_constant__ 
             }
         }
     };
-    float2 wv[2][kChunk], nv[2][kChunk];
+    float2 wv[2][kChunk], nv[2][kChunk], nv2[2][kChunk];
     const int e_top = (E - 1) / kChunk * kChunk;
     load_chunk(e_top, wv);
+    if (e_top >= kChunk) load_chunk(e_top - kChunk, nv);
     for (int e0 = e_top; e0 >= 0; e0 -= kChunk) {
-        if (e0 >= kChunk) load_chunk(e0 - kChunk, nv);  // next chunk, issued ahead
+        // the chunk after next, issued ahead; it is read before this chunk's
+        // results are written, and lies in other rows
+        if (e0 >= 2 * kChunk) load_chunk(e0 - 2 * kChunk, nv2);
 #pragma unroll
         for (int d = kChunk - 1; d >= 0; --d) {
             if (e0 + d < E) {
@@ -660,7 +671,10 @@ __global__ void __launch_bounds__(kVCols * kVB) rg_vert(const __grid_constant__ 
 #pragma unroll
         for (int q = 0; q < 2; ++q)
 #pragma unroll
-            for (int d = 0; d < kChunk; ++d) wv[q][d] = nv[q][d];
+            for (int d = 0; d < kChunk; ++d) {
+                wv[q][d] = nv[q][d];
+                nv[q][d] = nv2[q][d];
+            }
     }
 }
 
@@ -694,14 +708,19 @@ __global__ void __launch_bounds__(64 * kHT) rg_horz(const __grid_constant__ RgPa
     const float2 last = V[(size_t)(W - 1) * kYB];
     const float2 cB = make_float2(p.cB, p.cB), cD1 = make_float2(p.cD1, p.cD1);
     const float2 cD2 = make_float2(p.cD2, p.cD2);
-    float2 cur[kChunkH], nxt[kChunkH];
+    // the chunk being filtered and the next two (loads issued two chunks
+    // ahead; columns ahead of the in-place writes)
+    float2 cur[kChunkH], nxt[kChunkH], nx2[kChunkH];
 #pragma unroll
-    for (int d = 0; d < kChunkH; ++d) cur[d] = d < W ? V[(size_t)d * kYB] : last;
+    for (int d = 0; d < kChunkH; ++d) {
+        cur[d] = d < W ? V[(size_t)d * kYB] : last;
+        nxt[d] = kChunkH + d < W ? V[(size_t)(kChunkH + d) * kYB] : last;
+    }
     for (int e0 = 0; e0 < E; e0 += kChunkH) {
 #pragma unroll
         for (int d = 0; d < kChunkH; ++d) {
-            const int e = e0 + kChunkH + d;
-            nxt[d] = e < W ? V[(size_t)e * kYB] : last;
+            const int e = e0 + 2 * kChunkH + d;
+            nx2[d] = e < W ? V[(size_t)e * kYB] : last;
         }
 #pragma unroll
         for (int d = 0; d < kChunkH; ++d) {
@@ -711,7 +730,10 @@ __global__ void __launch_bounds__(64 * kHT) rg_horz(const __grid_constant__ RgPa
             }
         }
 #pragma unroll
-        for (int d = 0; d < kChunkH; ++d) cur[d] = nxt[d];
+        for (int d = 0; d < kChunkH; ++d) {
+            cur[d] = nxt[d];
+            nxt[d] = nx2[d];
+        }
     }
     // anticausal, columns E-1 .. 0, combining at the image's columns
     float2 t1 = s1, t2 = make_float2(0.f, 0.f), t3 = t2;
@@ -724,22 +746,29 @@ __global__ void __launch_bounds__(64 * kHT) rg_horz(const __grid_constant__ RgPa
             cf[d] = __ldg(F + (size_t)min(e, W - 1) * kYB);
         }
     };
-    float2 wv[kChunkH], nwv[kChunkH];
-    float cf[kChunkH], ncf[kChunkH];
+    float2 wv[kChunkH], nwv[kChunkH], nw2[kChunkH];
+    float cf[kChunkH], ncf[kChunkH], nc2[kChunkH];
     const int e_top = (E - 1) / kChunkH * kChunkH;
     load_back(e_top, wv, cf);
+    if (e_top >= kChunkH) load_back(e_top - kChunkH, nwv, ncf);
+    // the chunk being filtered and the next two (loads issued two chunks ahead)
+    auto advance = [&]() {
+#pragma unroll
+        for (int d = 0; d < kChunkH; ++d) {
+            wv[d] = nwv[d];
+            cf[d] = ncf[d];
+            nwv[d] = nw2[d];
+            ncf[d] = nc2[d];
+        }
+    };
     for (int e0 = e_top; e0 >= 0; e0 -= kChunkH) {
-        if (e0 >= kChunkH) load_back(e0 - kChunkH, nwv, ncf);  // next chunk, issued ahead
+        if (e0 >= 2 * kChunkH) load_back(e0 - 2 * kChunkH, nw2, nc2);
 #pragma unroll
         for (int d = kChunkH - 1; d >= 0; --d) {
             if (e0 + d < E) wv[d] = rg_step1(cB, cD1, cD2, wv[d], t1, t2, t3);
         }
         if (e0 >= W) {  // extension only: no outputs (uniform)
-#pragma unroll
-            for (int d = 0; d < kChunkH; ++d) {
-                wv[d] = nwv[d];
-                cf[d] = ncf[d];
-            }
+            advance();
             continue;
         }
 #pragma unroll
@@ -769,11 +798,7 @@ __global__ void __launch_bounds__(64 * kHT) rg_horz(const __grid_constant__ RgPa
             }
         }
         buf ^= 1;
-#pragma unroll
-        for (int d = 0; d < kChunkH; ++d) {
-            wv[d] = nwv[d];
-            cf[d] = ncf[d];
-        }
+        advance();
     }
 }
 
