@@ -546,3 +546,19 @@ def test_space_variant_cosine_kernel_agrees_with_the_power_form(oracle):
     w1 = oracle.spatial_w1("box", 1.0, radius=2, passes=1)
     np.testing.assert_allclose(oracle.bf_brute_sv_cos(f, np.full(f.shape, 2), gamma, coefs),
                                oracle.bf_brute_cos(f, gamma, coefs, w1=w1), rtol=1e-11)
+
+
+def test_sampled_and_scalar_forms_agree_with_the_whole_image(oracle):
+    # the sampled cosine-kernel brute force and the scalar loss are the whole-image
+    # filter read at pixels / summed against u
+    f = _small_image(12, 15, seed=15)
+    gamma = math.pi / 510
+    coefs = np.array([1.0, 0.8, 0.5, 0.3, 0.1])
+    whole = oracle.bf_brute_cos(f, gamma, coefs, sigma_s=1.5)
+    idx = np.array([0, 7, 33, 12 * 15 - 1])
+    np.testing.assert_array_equal(oracle.bf_brute_cos_at(f, idx, gamma, coefs, sigma_s=1.5),
+                                  whole.ravel()[idx])
+    u = np.random.default_rng(3).standard_normal(f.shape)
+    out = oracle.bf_brute(f, sigma_s=2.0, sigma_r=25.0, kind="gauss")
+    assert oracle.loss(f, u, sigma_s=2.0, sigma_r=25.0) == pytest.approx(float((u * out).sum()),
+                                                                        rel=1e-12)
