@@ -1,7 +1,7 @@
 """The oracle's pins catch plausible mistakes.  Each case plants one mistake
 in a copy of the oracle's C source (a dropped range factor, a wrong clamp
 bound, a wrong frequency or sign, floor for ceil, an off-by-one box, a flipped
-gradient term), builds it with gcc on the CPU and checks that at least one of
+gradient term, a wrong coefficient of the recursive filter), builds it with gcc on the CPU and checks that at least one of
 the pin checks below fails on it -- while all of them pass on the oracle as
 committed."""
 import importlib.util
@@ -50,6 +50,10 @@ MUTANTS = {
                                    "{\n    size_t n = (size_t)H * W;\n"
                                    "    double gamma = OR_PI / (2.0 * T);\n"
                                    "    double rho = 1.05 * gamma * sigma_r;"),
+    "cosine kernel frequency shifted": ("v += r->a[n] * cos((double)n * r->gamma * s);",
+                                        "v += r->a[n] * cos((double)(n + 1) * r->gamma * s);"),
+    "recursive design coefficient": ("double b2 = -(1.4281 * q * q + 1.26661 * q * q * q);",
+                                     "double b2 = -(1.4281 * q * q + 1.26661 * q * q);"),
 }
 
 
@@ -108,6 +112,21 @@ def _checks(o):
     sv = o.bf_brute_sv(np.array([[0.0, 100.0, 50.0]]), [[2, 1, 0]], sigma_r=200.0)
     if not np.allclose(sv[0], [gs["sv1d_0"], gs["sv1d_1"], gs["sv1d_2"]], atol=1e-7):
         failed.append("space-variant examples")
+    gc = _golden("cosine_kernel_examples.txt")
+    outc = o.bf_brute_cos(np.array([[0.0, 100.0], [100.0, 0.0]]), math.pi / 200, [0.5, 0.5],
+                          w1=w1)
+    if not np.allclose(outc, [[gc["2d_00"], gc["2d_01"]], [gc["2d_10"], gc["2d_11"]]],
+                       atol=1e-7) or abs(gc["2d_00"] - 200 / 7) > 5e-8:
+        failed.append("cosine kernel examples")
+    sigma, n = 3.0, 133
+    x = np.zeros((1, n))
+    x[0, n // 2] = 1.0
+    y = o.rg_filter(x, sigma)[0]
+    k = np.arange(n) - n // 2
+    gauss = np.exp(-k * k / (2 * sigma * sigma))
+    gauss /= gauss.sum()
+    if abs(y.sum() - 1.0) > 1e-5 or np.abs(y - gauss).max() > 0.05 * gauss.max():
+        failed.append("recursive Gaussian impulse response")
     return failed
 
 
