@@ -364,6 +364,9 @@ bf_status bf_backward_stack(const bf_plan *plan, const float *f, const float *ou
  *          grad_sigma_r NULL no scratch is used and there is no limit.
  *   The first call on a device asks the runtime for the array's device
  *   address and caches it; make that first call before any stream capture.
+ *   cudaDeviceReset on that device invalidates the cached address (the
+ *   module is loaded again, possibly elsewhere): do not call this entry
+ *   point on a device after resetting it in the same process.
  *   All calls share the array.  Each call writes every partial it reads
  *   before reading it, so nothing has to be cleared between calls, but calls
  *   whose work overlaps on the GPU (other streams, other host threads) race

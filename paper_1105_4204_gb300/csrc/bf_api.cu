@@ -155,6 +155,9 @@ extern "C" bf_status bf_forward_space_variant(const bf_plan *plan, const void *i
                                    std::to_string(sv_max_radius()) + "]");
     if ((long long)H * W > (1LL << 31) / 4)
         return fail(BF_EUNSUPPORTED, std::string(who) + ": image too large");
+    if (H > BF_MAX_ROWS)
+        return fail(BF_EUNSUPPORTED, std::string(who) + ": image taller than " +
+                                         std::to_string(BF_MAX_ROWS) + " rows");
     return cuda_check(launch_space_variant(plan, in, (int)dt, row_stride_elems, radius, r_max,
                                            out, H, W, stream),
                       who);
@@ -194,6 +197,9 @@ extern "C" bf_status bf_forward_host(const bf_plan *plan, const void *host_in, b
 static bf_status forward_planes(const bf_plan *plan, const BfImage &img, cudaStream_t stream,
                                 const char *who) {
     const int H = img.H, W = img.W;
+    if (H > BF_MAX_ROWS)
+        return fail(BF_EUNSUPPORTED, std::string(who) + ": image taller than " +
+                                         std::to_string(BF_MAX_ROWS) + " rows");
     if (tile_supported(plan))
         return cuda_check(launch_tile_forward(plan, img, stream), who);
     if (plan->kind == BF_SPATIAL_BOX_ITER) {
@@ -326,6 +332,9 @@ extern "C" bf_status bf_backward_stack(const bf_plan *plan, const float *f, cons
         return fail(BF_EINVAL, "bf_backward_stack: H, W and count must be >= 1");
     if ((long long)H * W > (1LL << 31) / 4 || count > 65535)
         return fail(BF_EUNSUPPORTED, "bf_backward_stack: image or stack too large");
+    if (H > BF_MAX_ROWS)
+        return fail(BF_EUNSUPPORTED, "bf_backward_stack: image taller than " +
+                                         std::to_string(BF_MAX_ROWS) + " rows");
     if (!bwd_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward_stack: no kernel for this spatial support "
                                      "(Gaussian R <= 24 or box r <= 8)");
@@ -356,6 +365,9 @@ extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const floa
     if (H < 1 || W < 1) return fail(BF_EINVAL, "bf_backward: H and W must be >= 1");
     if ((long long)H * W > (1LL << 31) / 4)
         return fail(BF_EUNSUPPORTED, "bf_backward: image too large");
+    if (H > BF_MAX_ROWS)
+        return fail(BF_EUNSUPPORTED, "bf_backward: image taller than " +
+                                         std::to_string(BF_MAX_ROWS) + " rows");
     if (!bwd_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward: no kernel for this spatial support "
                                      "(Gaussian R <= 24 or box r <= 8)");

@@ -13,6 +13,9 @@
 #define BF_MAX_TERMS 520
 // Largest 1-D support half-width of a truncated Gaussian handled by taps.
 #define BF_MAX_TAPS_R 32
+// Tallest image: the tile kernels put the row tiles (32 rows or more) on
+// gridDim.y, which is at most 65535.
+#define BF_MAX_ROWS (65535 * 32)
 
 struct bf_plan {
     double sigma_s = 0, sigma_r = 0, T = 0;

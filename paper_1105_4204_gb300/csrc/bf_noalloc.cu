@@ -51,6 +51,9 @@ extern "C" bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, co
     if (H < 1 || W < 1) return fail(BF_EINVAL, "bf_backward_noalloc: H and W must be >= 1");
     if ((long long)H * W > (1LL << 31) / 4)
         return fail(BF_EUNSUPPORTED, "bf_backward_noalloc: image too large");
+    if (H > BF_MAX_ROWS)
+        return fail(BF_EUNSUPPORTED, "bf_backward_noalloc: image taller than " +
+                                         std::to_string(BF_MAX_ROWS) + " rows");
     if (!bwd_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward_noalloc: no kernel for this spatial support "
                                      "(Gaussian R <= 24 or box r <= 8)");

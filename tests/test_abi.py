@@ -239,6 +239,34 @@ def test_size_limits_are_checked_on_the_host(bf):
     assert l.bf_backward(p.handle, fake, fake, fake, fake, fake, null, H, W, null, 0, null) == 2
 
 
+def test_tall_images_are_refused_on_the_host(bf):
+    # 2^22 x 128 is within the pixel limit but has more 32-row tiles than a
+    # grid's y dimension holds: refused with a message, before any launch
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    l.bf_backward_noalloc.restype = ctypes.c_int
+    l.bf_backward_noalloc.argtypes = [ctypes.c_void_p] * 7 + [ctypes.c_int, ctypes.c_int,
+                                                              ctypes.c_void_p]
+    fake = ctypes.c_void_p(0x1000)
+    null = ctypes.c_void_p(0)
+    H, W = 1 << 22, 128
+    for kind, ss in (("gauss", 3.0), ("box", 2.0)):
+        p = bf.Plan(ss, 20.0, kind=kind)
+        assert l.bf_forward(p.handle, fake, 0, fake, H, W, 1, W, null, null) == 2
+        assert b"taller than" in l.bf_last_error()
+        assert l.bf_backward(p.handle, fake, fake, fake, fake, fake, null, H, W, null, 0,
+                             null) == 2
+        assert b"taller than" in l.bf_last_error()
+        assert l.bf_backward_stack(p.handle, fake, fake, fake, fake, fake, null, H, W, 1, null,
+                                   0, null) == 2
+        assert b"taller than" in l.bf_last_error()
+        assert l.bf_backward_noalloc(p.handle, fake, fake, fake, fake, fake, null, H, W,
+                                     null) == 2
+        assert b"taller than" in l.bf_last_error()
+    # the tallest accepted height is stated in the message
+    assert str(65535 * 32).encode() in l.bf_last_error()
+
+
 def test_recursive_gaussian_plan(bf, oracle):
     # radius reports the extension P = ceil(6 sigma_s); achieved sigma is the cascade's
     # (closed form from the coefficients), equal to the oracle's measured impulse response

@@ -54,6 +54,10 @@ MUTANTS = {
                                         "v += r->a[n] * cos((double)(n + 1) * r->gamma * s);"),
     "recursive design coefficient": ("double b2 = -(1.4281 * q * q + 1.26661 * q * q * q);",
                                      "double b2 = -(1.4281 * q * q + 1.26661 * q * q);"),
+    "recursive design digits transposed": ("double b1 = 2.44413 * q",
+                                           "double b1 = 2.44431 * q"),
+    "recursive design digit of the small-sigma branch": (": 3.97156 - 4.14554 * sqrt",
+                                                         ": 3.97156 - 4.14545 * sqrt"),
 }
 
 
@@ -127,6 +131,14 @@ def _checks(o):
     gauss /= gauss.sum()
     if abs(y.sum() - 1.0) > 1e-5 or np.abs(y - gauss).max() > 0.05 * gauss.max():
         failed.append("recursive Gaussian impulse response")
+    for line in open(os.path.join(GOLDEN, "young_van_vliet_design.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        s, _q, b0, b1, b2, b3, B = [float(x) for x in line.split()]
+        c, _ = o.rg_coefs(s)
+        if not np.allclose(c, [B, b1 / b0, b2 / b0, b3 / b0], rtol=1e-9, atol=1e-15):
+            failed.append("recursive Gaussian published design")
+            break
     return failed
 
 

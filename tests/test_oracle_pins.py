@@ -400,6 +400,26 @@ def test_recursive_gaussian_approximates_the_gaussian(oracle, sigma, bound):
     assert int(np.argmax(y)) == len(y) // 2
 
 
+def _yvv_golden():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "young_van_vliet_design.txt")):
+        if line.strip() and not line.startswith("#"):
+            rows.append([float(x) for x in line.split()])
+    return rows
+
+
+def test_recursive_gaussian_design_matches_the_published_coefficients(oracle):
+    # the oracle's (B, b1/b0, b2/b0, b3/b0) at seven sigma on both branches of
+    # the published q(sigma), against the design worked out from Young and van
+    # Vliet's equations in tests/golden: one wrong digit of a published constant
+    # moves some ratio by far more than 1e-9
+    for s, q, b0, b1, b2, b3, B in _yvv_golden():
+        c, P = oracle.rg_coefs(s)
+        assert P == math.ceil(6 * s)
+        for got, want in zip(c, (B, b1 / b0, b2 / b0, b3 / b0)):
+            assert got == pytest.approx(want, rel=1e-9, abs=1e-15), (s, got, want)
+
+
 def test_recursive_gaussian_variance_closed_form(oracle):
     # the cascade's variance from the cumulants of the causal recursion
     # (2 (S''/B + (S'/B)^2), S' = sum k a_k, S'' = sum k^2 a_k) equals the measured one

@@ -1,7 +1,8 @@
 """bf_backward_noalloc: the backward entry point for callers that cannot
 allocate device memory (real-time loops, fixed memory pools, plug-in hosts
-that own every allocation).  It must give what bf_backward gives with a
-caller workspace, call after call, although every call reuses one fixed
+that own every allocation).  It runs the same kernel and the same
+fixed-order reduction as bf_backward with a caller workspace, so its results
+must be the same bits, call after call, although every call reuses one fixed
 device array for its partial sums.  This file is named to be collected last,
 so that a failure here comes after every other test has run."""
 import ctypes
@@ -12,8 +13,6 @@ import pytest
 import synth
 
 pytestmark = pytest.mark.gpu
-
-REL = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -32,37 +31,75 @@ def env():
     return torch, bf, fn, l
 
 
-def _noalloc(torch, fn, plan, f, out, q, u):
+def _noalloc(torch, fn, plan, f, out, q, u, need_sigma=True):
     g = torch.empty_like(f)
-    gs = torch.empty((), dtype=torch.float64, device=f.device)
+    gs = torch.full((), float("nan"), dtype=torch.float64, device=f.device)
     st = fn(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()),
             ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(u.data_ptr()),
-            ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(gs.data_ptr()), f.shape[0], f.shape[1],
+            ctypes.c_void_p(g.data_ptr()),
+            ctypes.c_void_p(gs.data_ptr() if need_sigma else 0), f.shape[0], f.shape[1],
             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 0
     torch.cuda.synchronize()
     return g, gs
 
 
+def _inputs(torch, bf, plan, H, W, seed):
+    f = torch.from_numpy(synth.rectangles(H, W, seed=seed)).cuda()
+    u = torch.from_numpy(synth.upstream((H, W), seed=seed + 1)).cuda()
+    out, q = bf.forward(plan, f, return_q=True)
+    return f, out, q, u
+
+
 @pytest.mark.parametrize("kind,ss,sr,H,W", [("gauss", 4.0, 25.0, 512, 512),
                                               ("box", 2.0, 20.0, 300, 170)])
-def test_noalloc_matches_workspace_backward_twice(env, kind, ss, sr, H, W):
+def test_noalloc_matches_workspace_backward_bit_for_bit(env, kind, ss, sr, H, W):
     torch, bf, fn, _ = env
-    img = synth.rectangles(H, W, seed=11)
-    u_np = synth.upstream((H, W), seed=12)
-    f = torch.from_numpy(img).cuda()
-    u = torch.from_numpy(u_np).cuda()
     plan = bf.Plan(ss, sr, kind=kind)
-    out, q = bf.forward(plan, f, return_q=True)
+    f, out, q, u = _inputs(torch, bf, plan, H, W, seed=11)
     g_ref, gs_ref = bf.backward(plan, f, out, q, u)  # caller-provided workspace
     torch.cuda.synchronize()
-    g_ref = g_ref.cpu().numpy()
-    gs_ref = float(gs_ref)
-    scale = np.abs(g_ref).max()
-    for _ in range(2):  # the second call reuses the array the first one filled
+    # a call on other data, at least as large, fills the shared array with
+    # other partials first; the next call must overwrite every one it reads
+    f2, out2, q2, u2 = _inputs(torch, bf, plan, H + 64, W + 64, seed=21)
+    g2_ref, gs2_ref = bf.backward(plan, f2, out2, q2, u2)
+    for call in range(3):
+        if call == 1:
+            g2, gs2 = _noalloc(torch, fn, plan, f2, out2, q2, u2)
+            assert torch.equal(g2, g2_ref)
+            assert torch.equal(gs2, gs2_ref)
+            assert float(gs2) != float(gs_ref)
+            continue
         g, gs = _noalloc(torch, fn, plan, f, out, q, u)
-        assert np.abs(g.cpu().numpy() - g_ref).max() <= REL * scale
-        assert abs(float(gs) - gs_ref) <= REL * abs(gs_ref)
+        assert torch.equal(g, g_ref)
+        assert torch.equal(gs, gs_ref)
+
+
+def test_noalloc_image_gradient_alone(env):
+    # grad_sigma_r = NULL: no partials, the no-dsigma_r kernel; same bits as
+    # bf_backward without grad_sigma_r
+    torch, bf, fn, _ = env
+    plan = bf.Plan(3.0, 30.0, kind="gauss")
+    f, out, q, u = _inputs(torch, bf, plan, 200, 333, seed=31)
+    g_ref, _ = bf.backward(plan, f, out, q, u, need_sigma=False)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        g, _ = _noalloc(torch, fn, plan, f, out, q, u, need_sigma=False)
+        assert torch.equal(g, g_ref)
+
+
+def test_noalloc_without_sigma_has_no_size_limit(env):
+    # ceil(8192/64) * ceil(4128/32) = 16512 blocks: more partials than the
+    # fixed array holds, accepted when no dL/dsigma_r is asked for
+    torch, bf, fn, _ = env
+    plan = bf.Plan(2.0, 20.0, kind="box")
+    H, W = 4128, 8192
+    f, out, q, u = _inputs(torch, bf, plan, H, W, seed=41)
+    g_ref, _ = bf.backward(plan, f, out, q, u, need_sigma=False)
+    torch.cuda.synchronize()
+    g, _ = _noalloc(torch, fn, plan, f, out, q, u, need_sigma=False)
+    assert torch.equal(g, g_ref)
+    assert bool(torch.isfinite(g).all())
 
 
 def test_noalloc_rejects_images_beyond_the_fixed_array(env):
