@@ -268,28 +268,42 @@ bf_status bf_forward_stack(const bf_plan *plan, const void *in, bf_dtype dt, flo
 
 /*
  * Tile-shape autotuner for bf_forward (not in the paper).  Runs each tile
- * shape the fused kernel has for this plan's spatial support `reps` times on
- * the given buffers (out is overwritten), and keeps the fastest for later
- * bf_forward calls with the same kind, radius, degree, H, W and C
+ * configuration the fused kernel has for this plan's spatial support `reps`
+ * times on the given buffers (out is overwritten), and keeps the fastest for
+ * later bf_forward calls with the same kind, radius, degree, H, W and C
  * (process-wide, thread-safe).  Synchronises `stream`.  *shape receives the
  * choice (-1 when the support runs on the streaming kernels, which have no
- * shape to choose), *ms its time per call; either may be NULL.  Shape ids:
+ * shape to choose), *ms its time per call; either may be NULL.  A
+ * configuration is shape | split << 8.  Shape ids:
  *   0  32 x 64 tiles (every support)
  *   1  32 x 96 tiles, wider row segments (box r <= 4, Gaussian R <= 9)
  *   2  64 x 64 tiles, one 512-thread block per SM (box 3 <= r <= 8,
  *      Gaussian R >= 9)
  *   3  64 x 64 tiles, 32-pixel row segments, one 256-thread block per SM
  *      (box 7 <= r <= 8)
+ * split (1, 2, 4 or 8; 0 reads as 1; the 32-row shapes 0 and 1 only): images
+ * with fewer tiles than the GPU has SMs cut the terms into `split`
+ * consecutive groups, one block per tile and group, so that the grid fills
+ * the GPU; the groups of a tile run as one thread-block cluster whose first
+ * block adds the others' numerators and normalisers (read from their shared
+ * memory) in group order and divides.  Nothing is allocated.  Without a tuned
+ * configuration bf_forward picks the split that brings the blocks nearest two
+ * per SM.  Different configurations sum the terms in different orders, so
+ * their results agree to FP32 rounding, not bit for bit; one configuration
+ * gives the same bits run to run.
  */
 bf_status bf_forward_tune(const bf_plan *plan, const void *in, bf_dtype dt, float *out, int H,
                           int W, int C, long long row_stride_elems, int reps,
                           cudaStream_t stream, int *shape, float *ms);
 
 /*
- * Pins the tile shape (id as above) that later bf_forward calls use for this
- * plan's kind, radius and degree at size H x W x C, as bf_forward_tune would
- * after timing.  Host only.  Errors: BF_EINVAL for a shape the plan's support
- * does not have (or a support without tile shapes) or bad sizes.
+ * Pins the tile configuration (shape | split << 8, as above) that later
+ * bf_forward calls use for this plan's kind, radius and degree at size
+ * H x W x C (C: the channels, or the images of a bf_forward_stack), as
+ * bf_forward_tune would after timing.  Host only.  Errors:
+ * BF_EINVAL for a shape the plan's support does not have (or a support
+ * without tile shapes), a split that is not a power of two up to 8 or exceeds
+ * the number of terms, or bad sizes.
  */
 bf_status bf_forward_set_shape(const bf_plan *plan, int H, int W, int C, int shape);
 

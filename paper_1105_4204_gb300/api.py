@@ -159,20 +159,22 @@ def tune(plan: Plan, img: torch.Tensor, reps: int = 3, stream=None):
     check(lib().bf_forward_tune(plan.handle, ctypes.c_void_p(img.data_ptr()), dt,
                                 ctypes.c_void_p(out.data_ptr()), H, W, C, rs, int(reps),
                                 _stream_ptr(stream), ctypes.byref(shape), ctypes.byref(ms)))
-    return {"shape": {-1: "streaming", 0: "32x64", 1: "32x96", 2: "64x64",
-                      3: "64x64-seg32"}[shape.value],
-            "ms": ms.value}
+    v = shape.value
+    names = {-1: "streaming", 0: "32x64", 1: "32x96", 2: "64x64", 3: "64x64-seg32"}
+    return {"shape": names[v if v < 0 else v & 0xFF],
+            "split": 1 if v < 0 else max(1, v >> 8), "ms": ms.value}
 
 
 SHAPES = {"32x64": 0, "32x96": 1, "64x64": 2, "64x64-seg32": 3}
 
 
-def set_shape(plan: Plan, img: torch.Tensor, shape: str):
+def set_shape(plan: Plan, img: torch.Tensor, shape: str, split: int = 1):
     """Pin the fused kernel's tile shape ("32x64", "32x96", "64x64" or
-    "64x64-seg32") for this plan at img's size, as ``tune`` would after
+    "64x64-seg32") and term split (1, 2, 4 or 8 groups of terms, one block
+    each per tile) for this plan at img's size, as ``tune`` would after
     timing."""
     dt, H, W, C, rs = _image_args(img)
-    check(lib().bf_forward_set_shape(plan.handle, H, W, C, SHAPES[shape]))
+    check(lib().bf_forward_set_shape(plan.handle, H, W, C, SHAPES[shape] | (int(split) << 8)))
 
 
 def forward_space_variant(plan: Plan, img: torch.Tensor, radius: torch.Tensor, r_max: int = 16,

@@ -29,13 +29,18 @@ int gauss_tile_radius(int R);
 int gauss_tile_shape_ids(int R, int *ids);
 int box_tile_max_r();
 int box_tile_shape_ids(int r, int *ids);
-cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape);
-cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape);
+cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape,
+                              int split);
+cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape,
+                            int split);
 
-// Tile shapes picked by bf_forward_tune, per (kind, radius, N, H, W, planes).
+// Tile configurations picked by bf_forward_tune, per (kind, radius, N, H, W,
+// planes): the tile shape id plus, for images with fewer tiles than the GPU
+// has SMs, the number of term groups (shape | split << 8).
 using TuneKey = std::tuple<int, int, int, int, int, int>;
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tuned;
+constexpr int kMaxSplit = 8;
 
 static TuneKey tune_key(const bf_plan *p, const BfImage &img) {
     return TuneKey(p->kind, p->R, p->N, img.H, img.W, img.C);
@@ -47,10 +52,53 @@ static int tile_shapes(const bf_plan *p, int *ids) {
                                              : box_tile_shape_ids(p->r_box, ids);
 }
 
-static cudaError_t launch_tile_shape(const bf_plan *p, const BfImage &img, cudaStream_t s,
-                                     int shape) {
-    if (p->kind == BF_SPATIAL_GAUSS_TRUNC) return launch_tile_gauss(p, img, s, shape);
-    return launch_tile_box(p, img, s, shape);
+static cudaError_t launch_tile_config(const bf_plan *p, const BfImage &img, cudaStream_t s,
+                                      int shape, int split) {
+    if (p->kind == BF_SPATIAL_GAUSS_TRUNC) return launch_tile_gauss(p, img, s, shape, split);
+    return launch_tile_box(p, img, s, shape, split);
+}
+
+// Output tile of a shape id (rows, columns): 0 = 32 x 64, 1 = 32 x 96,
+// 2 and 3 = 64 x 64.
+static void tile_dims(int shape, int *th, int *tw) {
+    *th = shape >= 2 ? 64 : 32;
+    *tw = shape == 1 ? 96 : 64;
+}
+
+static long long tile_count(const BfImage &img, int shape) {
+    int th, tw;
+    tile_dims(shape, &th, &tw);
+    return (long long)((img.W + tw - 1) / tw) * ((img.H + th - 1) / th) * img.C;
+}
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
+}
+
+// Whether `split` term groups suit an image of this many tiles: a power of two
+// up to kMaxSplit, no more groups than terms, at most four blocks per SM in
+// all, within the grid's z limit, and the 32-row tiles only (a cluster of
+// the 64-row tiles' one-block-per-SM blocks would hold eight SMs).
+static bool split_ok(const bf_plan *p, const BfImage &img, int shape, int split, int n_sm) {
+    if (split == 1) return true;
+    const long long tiles = tile_count(img, shape);
+    return shape < 2 && split <= kMaxSplit && split <= (int)p->a32.size() &&
+           tiles * split <= 4LL * n_sm && (long long)img.C * split <= 65535;
+}
+
+// Default term split when nothing was tuned: as many groups (a power of two)
+// as bring the blocks to about two per SM.
+static int default_split(const bf_plan *p, const BfImage &img, int shape) {
+    const int n_sm = sm_count();
+    const long long tiles = tile_count(img, shape);
+    int split = 1;
+    while (split * 2 <= kMaxSplit && tiles * split * 2 <= 2LL * n_sm &&
+           split_ok(p, img, shape, split * 2, n_sm))
+        split *= 2;
+    return split;
 }
 
 
@@ -90,13 +138,18 @@ bool tile_supported(const bf_plan *p) {
 }
 
 cudaError_t launch_tile_forward(const bf_plan *p, const BfImage &img, cudaStream_t s) {
-    int shape = 0;
+    int cfg = -1;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(tune_key(p, img));
-        if (it != g_tuned.end()) shape = it->second;
+        if (it != g_tuned.end()) cfg = it->second;
     }
-    return launch_tile_shape(p, img, s, shape);
+    const int shape = cfg < 0 ? 0 : (cfg & 0xff);
+    const int split = cfg < 0 ? default_split(p, img, shape) : std::max(1, cfg >> 8);
+    cudaError_t e = launch_tile_config(p, img, s, shape, split);
+    if (split > 1 && e == cudaErrorInvalidClusterSize)
+        e = launch_tile_config(p, img, s, shape, 1);  // the cluster does not fit: no split
+    return e;
 }
 
 }  // namespace bf
@@ -392,15 +445,25 @@ extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const floa
 
 extern "C" bf_status bf_forward_set_shape(const bf_plan *plan, int H, int W, int C, int shape) {
     if (!plan) return fail(BF_EINVAL, "bf_forward_set_shape: NULL plan");
-    if (H < 1 || W < 1 || C < 1 || C > 4) return fail(BF_EINVAL, "bf_forward_set_shape: bad size");
+    if (H < 1 || W < 1 || C < 1 || C > 65535)
+        return fail(BF_EINVAL, "bf_forward_set_shape: bad size (C counts the channels, or the images of a stack)");
     if (!tile_supported(plan))
         return fail(BF_EINVAL, "bf_forward_set_shape: this support runs on the streaming kernels");
     int ids[4];
     const int n = tile_shapes(plan, ids);
     bool ok = false;
-    for (int i = 0; i < n; ++i) ok = ok || ids[i] == shape;
-    if (!ok) return fail(BF_EINVAL, "bf_forward_set_shape: shape " + std::to_string(shape) +
-                                         " is not available for this support");
+    const int sid = shape & 0xff, split = std::max(1, shape >> 8);
+    for (int i = 0; i < n; ++i) ok = ok || ids[i] == sid;
+    if (split > 1 && sid >= 2)
+        return fail(BF_EINVAL, "bf_forward_set_shape: the term split runs on the 32-row shapes "
+                               "(0 and 1) only");
+    if (!ok || shape < 0) return fail(BF_EINVAL, "bf_forward_set_shape: shape " +
+                                                     std::to_string(sid) +
+                                                     " is not available for this support");
+    if ((split & (split - 1)) != 0 || split > kMaxSplit || split > (int)plan->a32.size() ||
+        (long long)C * split > 65535)
+        return fail(BF_EINVAL, "bf_forward_set_shape: term split " + std::to_string(split) +
+                                   " must be a power of two <= 8 and <= the number of terms");
     BfImage img{};
     img.H = H;
     img.W = W;
@@ -440,25 +503,31 @@ extern "C" bf_status bf_forward_tune(const bf_plan *plan, const void *in, bf_dty
     }
     int ids[4];
     const int n = tile_shapes(plan, ids);
+    const int n_sm = sm_count();
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) return cuda_check(e, "bf_forward_tune");
     float best = 1e30f;
     int best_shape = 0;
+    // every shape, each with every term split that suits its tile count
     for (int si = 0; si < n && e == cudaSuccess; ++si) {
-        const int sh = ids[si];
-        e = launch_tile_shape(plan, img, stream, sh);  // warm-up
-        if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
-        for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch_tile_shape(plan, img, stream, sh);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        ms /= reps;
-        if (e == cudaSuccess && ms < best) {
-            best = ms;
-            best_shape = sh;
+        for (int split = 1; split <= kMaxSplit && e == cudaSuccess; split *= 2) {
+            const int sh = ids[si];
+            if (!split_ok(plan, img, sh, split, n_sm)) continue;
+            e = launch_tile_config(plan, img, stream, sh, split);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+            for (int k = 0; k < reps && e == cudaSuccess; ++k)
+                e = launch_tile_config(plan, img, stream, sh, split);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                best_shape = sh | (split > 1 ? split << 8 : 0);
+            }
         }
     }
     cudaEventDestroy(e0);

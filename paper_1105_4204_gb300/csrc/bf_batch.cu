@@ -87,6 +87,7 @@ __device__ __forceinline__ void run_tile(const BatchParams &p, const ImgDesc &d,
     jb.w2 = nullptr;
     jb.x0 = tx * S::TW;
     jb.y0 = ty * S::TH;
+    jb.split = 1;
     tile_body<1, R, S::TH, S::TW, S::TWT>(jb, smem);
 }
 

@@ -85,6 +85,7 @@ void pair_taps(BfTaps *t);
 // Fused tile kernel for the truncated Gaussian / small-radius box.
 bool tile_supported(const bf_plan *p);
 cudaError_t launch_tile_forward(const bf_plan *p, const BfImage &img, cudaStream_t s);
+
 // Streaming sweeps for the 3-pass box with r > 8 (one image, its channels in
 // turn) through a scratch buffer of large_workspace(p, H, W) bytes.
 size_t large_workspace(const bf_plan *p, int H, int W);

@@ -29,11 +29,14 @@
 //           the common scale (2 RAD + 1)^-6 cancels in P / Q.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cstdint>
 
 #include "bf_internal.h"
 
 namespace bf {
+
+namespace cg = cooperative_groups;
 
 constexpr float kTwoPi = 6.28318530717958647692f;
 
@@ -319,6 +322,12 @@ struct TileParams {
     BfImage img;
     BfTerms terms;
     BfTaps taps;
+    // Term split (small images): the terms are cut into `split` consecutive
+    // groups, one block per tile and group, the groups of a tile launched as
+    // one thread-block cluster; the cluster's first block sums the groups' P
+    // and Q from the others' shared memory in group order and divides.
+    // split = 1: all terms in one block, no cluster.
+    int split;
 };
 
 // Everything one tile needs: the image, its term table and taps, the tile
@@ -336,6 +345,9 @@ struct TileJob {
     int n_terms;
     const float2 *w2;  // Gaussian taps, each duplicated into a pair
     int x0, y0;
+    // term groups of the tile (1: all terms in this block; > 1: this block
+    // is one of a cluster of `split`, its rank the group)
+    int split;
 };
 
 template <int KIND, int RAD, int TH, int TW, int TWT>
@@ -435,12 +447,52 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
 
     // ---- out = P / Q
     __syncthreads();
-    float *Xq = VP;
+    float *Xq = VP;  // Q of the tile's pixels (row stride G::SV)
+    float *Xp = VQ;  // P, kept in shared memory only by term-split blocks
     if (pa == 1) {
 #pragma unroll
         for (int k = 0; k < TWT; ++k) Xq[pi * G::SV + ps * TWT + k] = acc[k];
+    } else if (jb.split > 1) {
+#pragma unroll
+        for (int k = 0; k < TWT; ++k) Xp[pi * G::SV + ps * TWT + k] = acc[k];
     }
     __syncthreads();
+    if (jb.split > 1) {
+        // the tile's term groups form one cluster: block g of the cluster
+        // finishes the g-th slice of the tile's pixels, adding the groups' P
+        // and Q (read from every block's shared memory) in group order
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        const int S = jb.split;
+        const int g = (int)cl.block_rank();
+        const int per = (TH * TW + S - 1) / S;
+        for (int i = g * per + tid; i < min((g + 1) * per, TH * TW); i += G::NT) {
+            const int row = i / TW, col = i - (i / TW) * TW;
+            const int si = row * G::SV + col;
+            float pr[8], qr[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (r < S) {
+                    pr[r] = cl.map_shared_rank(Xp, r)[si];
+                    qr[r] = cl.map_shared_rank(Xq, r)[si];
+                }
+            float pv = pr[0], qv = qr[0];
+#pragma unroll
+            for (int r = 1; r < 8; ++r)
+                if (r < S) {
+                    pv += pr[r];
+                    qv += qr[r];
+                }
+            const int gy = y0 + row, gx = x0 + col;
+            if (gy < H && gx < W) {
+                const long long o = ((long long)gy * W + gx) * jb.out_px;
+                jb.out[o] = pv / qv;
+                if (jb.q_out) jb.q_out[o] = qv * jb.q_scale;
+            }
+        }
+        cl.sync();  // every block keeps its shared memory until the others have read it
+        return;
+    }
     if (pa == 0) {
         const int gy = y0 + pi;
         if (gy < H) {
@@ -473,7 +525,8 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT,
     bf_tile_fwd(const __grid_constant__ TileParams p) {
     extern __shared__ float4 smem4[];
     TileJob jb;
-    const int z = blockIdx.z;
+    const int z = blockIdx.z / p.split;   // plane
+    const int sg = blockIdx.z % p.split;  // term group
     const int esz = p.img.dtype == 0 ? 4 : 1;
     jb.in = reinterpret_cast<const char *>(p.img.in) + (long long)z * p.img.in_z * esz;
     jb.out = p.img.out + (long long)z * p.img.out_z;
@@ -485,12 +538,15 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT,
     jb.out_px = p.img.out_px;
     jb.dtype = p.img.dtype;
     jb.q_scale = p.img.q_scale;
-    jb.a = p.terms.a;
-    jb.t = p.terms.t;
-    jb.n_terms = p.terms.n_terms;
+    const int nt = p.terms.n_terms;
+    const int m0 = sg * nt / p.split, m1 = (sg + 1) * nt / p.split;
+    jb.a = p.terms.a + m0;
+    jb.t = p.terms.t + m0;
+    jb.n_terms = m1 - m0;
     jb.w2 = p.taps.w2;
     jb.x0 = blockIdx.x * TW;
     jb.y0 = blockIdx.y * TH;
+    jb.split = p.split;
     tile_body<KIND, RAD, TH, TW, TWT>(jb, reinterpret_cast<float *>(smem4));
 }
 
@@ -509,7 +565,23 @@ cudaError_t launch_tile(const TileParams &prm, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    dim3 grid((prm.img.W + TW - 1) / TW, (prm.img.H + TH - 1) / TH, prm.img.C);
+    dim3 grid((prm.img.W + TW - 1) / TW, (prm.img.H + TH - 1) / TH, prm.img.C * prm.split);
+    if (prm.split > 1) {
+        // a tile's term groups (consecutive z) as one cluster
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(G::NT);
+        cfg.dynamicSmemBytes = G::SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = prm.split;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, prm);
+    }
     kern<<<grid, G::NT, G::SMEM, s>>>(prm);
     return cudaGetLastError();
 }

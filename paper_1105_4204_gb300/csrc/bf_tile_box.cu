@@ -23,9 +23,11 @@ int box_tile_shape_ids(int r, int *ids) {
 
 cudaError_t launch_tile_box_long_segments(int r, const TileParams &prm, cudaStream_t s);
 
-cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t s, int shape) {
+cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img0, cudaStream_t s, int shape,
+                            int split) {
     TileParams prm;
     prm.img = img0;
+    prm.split = split;
     fill_terms(pl, &prm.terms);
     for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) prm.taps.w[k] = 0.f;
     pair_taps(&prm.taps);

@@ -27,10 +27,12 @@ int gauss_tile_shape_ids(int R, int *ids) {
     return n;
 }
 
-cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape) {
+cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_t s, int shape,
+                              int split) {
     const int Ri = gauss_tile_radius(pl->R);
     TileParams prm;
     prm.img = img;
+    prm.split = split;
     fill_terms(pl, &prm.terms);
     for (int k = 0; k < 2 * BF_MAX_TAPS_R + 1; ++k) prm.taps.w[k] = 0.f;
     for (int k = 0; k < 2 * pl->R + 1; ++k) prm.taps.w[k + Ri - pl->R] = pl->w1f[k];
@@ -68,3 +70,4 @@ cudaError_t launch_tile_gauss(const bf_plan *pl, const BfImage &img, cudaStream_
 }
 
 }  // namespace bf
+

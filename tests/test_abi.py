@@ -184,6 +184,23 @@ def test_set_shape_accepts_only_the_supports_shapes(bf):
     assert b"streaming" in l.bf_last_error()
 
 
+def test_set_shape_term_split(bf):
+    # configuration = shape | split << 8; split a power of two up to 8 and no
+    # more groups than terms
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    g = bf.Plan(3.0, 30.0, kind="gauss")                           # 16 terms
+    for split in (0, 1, 2, 4, 8):
+        assert l.bf_forward_set_shape(g.handle, 64, 64, 1, split << 8) == 0
+    for split in (3, 16):
+        assert l.bf_forward_set_shape(g.handle, 64, 64, 1, split << 8) == 1
+        assert b"split" in l.bf_last_error()
+    one = bf.Plan(3.0, 200.0, kind="gauss")                        # N = 1: one term
+    assert one.n_terms == 1
+    assert l.bf_forward_set_shape(one.handle, 64, 64, 1, 2 << 8) == 1
+    assert l.bf_forward_set_shape(g.handle, 64, 64, 1, (2 << 8) | 7) == 1
+
+
 def test_cosine_plan_terms_reproduce_the_polynomial(bf):
     # Section 2.2: phi(s) = sum_n a_n cos(n gamma s); the plan's folded term table must give
     # the same function (terms of zero FP32 weight dropped, constant last)

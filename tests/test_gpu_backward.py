@@ -146,8 +146,14 @@ def test_stack_calls_match_per_image_calls(bf):
     import torch
     imgs = torch.from_numpy(np.stack([synth.rectangles(70, 130, seed=s) for s in range(5)])).cuda()
     u = torch.from_numpy(synth.upstream(tuple(imgs.shape), seed=4)).cuda()
+    lib = __import__("paper_1105_4204_gb300._lib", fromlist=["lib"]).lib()
     for kind, ss, sr in [("gauss", 4.0, 25.0), ("box", 3.0, 30.0), ("box", 12.0, 20.0)]:
         plan = bf.Plan(ss, sr, kind=kind)
+        if plan.radius // 3 <= 8 or kind == "gauss":
+            # one configuration for the stack and the single images (32 x 64
+            # tiles, all terms per block): the same summation order
+            for c in (1, imgs.shape[0]):
+                assert lib.bf_forward_set_shape(plan.handle, 70, 130, c, 1 << 8) == 0
         out, q = bf.forward_stack(plan, imgs, return_q=True)
         for b in range(imgs.shape[0]):
             ob, qb = bf.forward(plan, imgs[b], return_q=True)

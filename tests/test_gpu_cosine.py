@@ -118,6 +118,8 @@ def test_batch_with_cosine_plans(bf, oracle):
     b.forward()
     assert b.check() == 0
     for i, p in enumerate(plans):
+        if p.radius // 3 <= 8:  # the batch's configuration: 32 x 64 tiles, all terms per block
+            bf.set_shape(p, ins[i], "32x64", split=1)
         single = bf.forward(p, ins[i]).cpu().numpy()
         got = outs[i].cpu().numpy()
         assert np.array_equal(got, single)

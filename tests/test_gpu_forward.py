@@ -133,6 +133,57 @@ def test_every_tile_shape(bf, oracle, kind, rad, shape):
     assert err <= TOL
 
 
+@pytest.mark.parametrize("split", [1, 2, 4, 8])
+@pytest.mark.parametrize("kind,ss,sr", [("gauss", 3.0, 30.0), ("box", 2.0, 20.0),
+                                        ("box", 8.0, 15.0)])
+def test_term_split(bf, oracle, kind, ss, sr, split):
+    # small images cut the terms into groups, one block per tile and group,
+    # summed in group order by a last kernel: every split matches the oracle,
+    # its Q too, for one channel, three interleaved u8 channels and a stack
+    import torch
+    img = synth.rectangles(96, 150, n_rect=8, noise=10.0, seed=int(ss * 10) + split)
+    plan = bf.Plan(ss, sr, kind=kind)
+    t = torch.from_numpy(img).cuda()
+    bf.set_shape(plan, t, "32x64", split=split)
+    out, q = bf.forward(plan, t, return_q=True)
+    ref, qref = _oracle_full(oracle, img, plan, return_q=True)
+    assert np.abs(out.cpu().numpy() - ref).max() <= TOL
+    np.testing.assert_allclose(q.cpu().numpy(), qref, rtol=2e-4, atol=1e-6)
+    u8 = synth.rect_disk_u8(40, 70, C=3, n_shapes=6, seed=split)
+    t3 = torch.from_numpy(u8).cuda()
+    bf.set_shape(plan, t3, "32x64", split=split)
+    out3 = bf.forward(plan, t3).cpu().numpy()
+    ref3 = oracle.bf_brute(u8.astype(np.float64), sigma_r=sr, w1=plan_w1(oracle, plan), N=plan.N)
+    assert np.abs(out3 - ref3).max() <= TOL
+    stack = np.stack([synth.rectangles(33, 47, seed=k) for k in range(3)])
+    ts = torch.from_numpy(stack).cuda()
+    lib = __import__("paper_1105_4204_gb300._lib", fromlist=["lib"]).lib()
+    assert lib.bf_forward_set_shape(plan.handle, 33, 47, 3, split << 8) == 0
+    outs = bf.forward_stack(plan, ts).cpu().numpy()
+    for k in range(3):
+        refk = oracle.bf_brute(stack[k].astype(np.float64), sigma_r=sr, w1=plan_w1(oracle, plan),
+                               N=plan.N)
+        assert np.abs(outs[k] - refk).max() <= TOL
+
+
+def test_small_image_default_split_fills_the_gpu(bf, oracle):
+    # the 256 x 256 image of the first configuration has 32 tiles of 32 x 64:
+    # untuned, bf_forward cuts its 16 terms into groups; results agree with a
+    # pinned split of 1 within rounding and are the same bits run to run
+    import torch
+    img = synth.rectangles(256, 256, n_rect=12, noise=10.0, seed=0)
+    plan = bf.Plan(3.0, 30.0, 255.0, kind="gauss")
+    t = torch.from_numpy(img).cuda()
+    a = bf.forward(plan, t).cpu().numpy()
+    b = bf.forward(plan, t).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    bf.set_shape(plan, t, "32x64", split=1)
+    c = bf.forward(plan, t).cpu().numpy()
+    assert np.abs(a - c).max() <= 1e-3
+    info = bf.tune(plan, t, reps=2)
+    assert info["split"] in (1, 2, 4, 8)
+
+
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 7, 11, 30, 66, 118, 264])
 def test_degrees(bf, oracle, N):
     # sigma_r chosen so that N meets the validity bound of Section 2.5,
