@@ -42,15 +42,44 @@ WORKLOAD = ("2048x2048 f32 smooth field (20 sinusoids + regions + noise 5, seed 
             "3-pass box sigma_s in {2, 8, 32} (r = 2, 8, 32), sigma_r = 20 (N = 66), T = 255, "
             "clamp-to-edge; 3 forwards per step")
 # DRAM bytes per call (dram__bytes_read.sum + dram__bytes_write.sum over the
-# call's kernels, one ncu capture of this workload each; the captures and
-# commands are in profiles/): sigma_s = 2 and 8, one fused tile kernel that
-# reads f once (its out writes leave L2 after the kernel); sigma_s = 32,
-# lr_transpose + lr_vert + lr_horz + lr_final, dominated by the 4 x 34
-# filtered planes written and read back.
+# call's kernels, one ncu capture of this workload; the command is in
+# profiles/): sigma_s = 2 and 8, one fused tile kernel that reads f once (its
+# out writes leave L2 after the kernel); sigma_s = 32, lr_transpose + lr_vert
+# + lr_horz + lr_final, dominated by the 4 x 34 filtered planes written and
+# read back.  The figures belong to the kernel sources they were captured on:
+# DRAM_SOURCES_SHA256 is kernel_sources_sha256() of that build, and the bench
+# line reports no traffic (and says why) when the sources differ.
 DRAM_BYTES_PER_CALL = {2.0: 16.84e6, 8.0: 16.84e6, 32.0: 5.664e9}
+DRAM_SOURCES_SHA256 = None
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+
+
+def kernel_sources_sha256() -> str:
+    """SHA-256 over the library's CUDA/C++ sources and headers (file names and
+    contents, in name order): identifies the build an ncu capture was made on."""
+    import hashlib
+    import glob
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1105_4204_gb300", "csrc", "*")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def dram_traffic(sigma_s: float):
+    """(bytes, note): the ncu DRAM bytes of one call, or None when the kernel
+    sources changed since the capture."""
+    cur = kernel_sources_sha256()
+    if DRAM_SOURCES_SHA256 is None or cur != DRAM_SOURCES_SHA256:
+        return None, ("no ncu capture of the current kernel sources (sha256 %s...); "
+                      "traffic not reported" % cur[:12])
+    return DRAM_BYTES_PER_CALL.get(sigma_s), "ncu capture of these kernel sources (sha256 %s...)" % cur[:12]
 
 
 def _load_peaks():
@@ -73,6 +102,36 @@ def box_instr_per_px(n_nonzero: int, has_center: bool) -> float:
 def gauss_instr_per_px(n_nonzero: int, has_center: bool, R: int) -> float:
     fs = 2.0 * (2 * R + 1)
     return (9.0 + 4.0 * fs) * n_nonzero + ((fs + 3.0) if has_center else 0.0) + 4.0
+
+
+def gauss_bwd_instr_per_px(n_nonzero: int, has_center: bool, R: int) -> float:
+    """Algorithmic FP32-pipe instructions per pixel of the adjoint for the
+    truncated Gaussian: per nonzero frequency 9 to generate the ten planes
+    (phase; f c, f s, f^2 c, f^2 s; alpha c, alpha s, alpha o c, alpha o s),
+    10 planes x 2(2R+1) taps, and 26 to form the per-pixel factors and combine;
+    the constant term one plane (alpha through W^T) and 3."""
+    fs = 2.0 * (2 * R + 1)
+    return (35.0 + 10.0 * fs) * n_nonzero + ((fs + 3.0) if has_center else 0.0)
+
+
+def alu_roofline(ops: float, ms: float, peak_ops: float, what: str) -> dict:
+    """Roofline object of one measured call: algorithmic FP32 operations per
+    second against the FP32-pipe peak."""
+    ach = ops / (ms * 1e-3)
+    return {"bound": "alu", "achieved": ach / 1e12, "peak": peak_ops / 1e12,
+            "unit": "T FP32-pipe instr/s", "frac": ach / peak_ops, "ms": ms,
+            "ops": ops, "count": what}
+
+
+def _peak_ops(torch, dev) -> float:
+    peaks, _ = _load_peaks()
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sm * FP32_LANES_PER_SM * peaks.get("sm_max_mhz", SM_MAX_MHZ) * 1e6
+
+
+def _plan_counts(plan):
+    a, w = plan.terms()
+    return int(np.sum(w > 0)), bool(np.any(w == 0))
 
 
 class ClockSampler:
@@ -324,10 +383,10 @@ def run_ours(args):
         nz = int(np.sum(w > 0))
         instr = box_instr_per_px(nz, bool(np.any(w == 0))) * H * W
         ach = instr / (call_ms[i] * 1e-3)
-        dram = DRAM_BYTES_PER_CALL.get(SIGMA_S[i])
+        dram, dram_note = dram_traffic(SIGMA_S[i])
         sec = call_ms[i] * 1e-3
         rl.append({"sigma_s": SIGMA_S[i], "r": p.radius // 3,
-                   "dram_bytes_ncu": dram,
+                   "dram_bytes_ncu": dram, "dram_note": dram_note,
                    "algorithmic_bytes": 8.0 * H * W,
                    "hbm": {"algorithmic_gbs": 8.0 * H * W / sec / 1e9,
                            "dram_gbs": dram / sec / 1e9 if dram else None,
@@ -342,7 +401,8 @@ def run_ours(args):
                 "peak": peak_instr / 1e12, "unit": "T FP32-pipe instr/s",
                 "frac": rl[dom]["frac"], "traffic": rl[dom]["dram_bytes_ncu"],
                 "traffic_note": "DRAM bytes per call of the dominant call's kernels from ncu "
-                                "(profiles/); algorithmic bytes are 8 per pixel (f in, out out)",
+                                "(profiles/); algorithmic bytes are 8 per pixel (f in, out out); "
+                                + rl[dom]["dram_note"],
                 "kernel": rl[dom]["kernel"], "per_call": rl,
                 "peak_note": "SMs x 128 FP32 lanes x max SM clock %.0f MHz (%s)" % (
                     peaks.get("sm_max_mhz", SM_MAX_MHZ), peak_kind),
@@ -504,12 +564,19 @@ def measure_fwd_bwd(bf, torch, dev, stream):
     t_fb = _time(fwd_bwd, torch, stream, 5)
     t_fbd = _time(fwd_bwd_df_only, torch, stream, 5)
     px = B * HH * WW
-    a, w = plan.terms()
-    nz = int(np.sum(w > 0))
+    nz, center = _plan_counts(plan)
+    peak = _peak_ops(torch, dev)
+    f_ops = gauss_instr_per_px(nz, center, 12) * px
+    b_ops = gauss_bwd_instr_per_px(nz, center, 12) * px
     return {"fwd_bwd_config": "16 x 512^2, gauss sigma_s=4 (R=12), sigma_r=25 (N=43)",
             "fwd_mpx_s": px / (t_f * 1e-3) / 1e6, "fwd_bwd_mpx_s": px / (t_fb * 1e-3) / 1e6,
             "fwd_ms": t_f, "fwd_bwd_ms": t_fb, "fwd_bwd_image_gradient_only_ms": t_fbd,
-            "fwd_instr_per_px": gauss_instr_per_px(nz, bool(np.any(w == 0)), 12)}
+            "fwd_instr_per_px": gauss_instr_per_px(nz, center, 12),
+            "bwd_instr_per_px": gauss_bwd_instr_per_px(nz, center, 12),
+            "roofline_fwd": alu_roofline(f_ops, t_f, peak, "gauss_instr_per_px x pixels"),
+            "roofline_bwd": alu_roofline(b_ops, t_fb - t_f, peak,
+                                         "gauss_bwd_instr_per_px x pixels; backward time = "
+                                         "fwd+bwd minus fwd")}
 
 
 def measure_configs(bf, torch, dev, stream, acc_jobs):
@@ -527,7 +594,12 @@ def measure_configs(bf, torch, dev, stream, acc_jobs):
     bf.tune(p1, t1, reps=3)
     ms1 = _time(lambda: bf.forward(p1, t1, out=o1), torch, stream, 20)
     got1 = o1.cpu().numpy()
-    res["c1_256_gauss_r9_n30"] = {"ms": ms1, "mpx_s": 256 * 256 / (ms1 * 1e-3) / 1e6}
+    peak = _peak_ops(torch, dev)
+    nz1, c1 = _plan_counts(p1)
+    res["c1_256_gauss_r9_n30"] = {
+        "ms": ms1, "mpx_s": 256 * 256 / (ms1 * 1e-3) / 1e6, "tuned": bf.tune(p1, t1, reps=3),
+        "roofline": alu_roofline(gauss_instr_per_px(nz1, c1, 9) * 256 * 256, ms1, peak,
+                                 "gauss_instr_per_px x pixels")}
 
     def _c1_acc(oracle):
         ref1 = oracle.bf_brute(img1.astype(np.float64), sigma_s=3.0, sigma_r=30.0, kind="gauss")
@@ -545,7 +617,11 @@ def measure_configs(bf, torch, dev, stream, acc_jobs):
         out = o3.cpu().numpy()
         gots = [out[..., c].ravel()[idx] for c in range(3)]
         key = "c3_4096x3_u8_gauss_r18_sr%g_n%d" % (sr, p3.N)
-        res[key] = {"ms": ms3, "mpx_s": 3 * 4096 * 4096 / (ms3 * 1e-3) / 1e6}
+        nz3, c3 = _plan_counts(p3)
+        res[key] = {"ms": ms3, "mpx_s": 3 * 4096 * 4096 / (ms3 * 1e-3) / 1e6,
+                    "roofline": alu_roofline(gauss_instr_per_px(nz3, c3, 18) * 3 * 4096 * 4096,
+                                             ms3, peak, "gauss_instr_per_px x pixels x 3 "
+                                             "channels (terms of zero FP32 weight not counted)")}
 
         def _c3_acc(oracle, sr=sr, N=p3.N, gots=gots):
             w1 = oracle.spatial_w1("gauss", 6.0)
@@ -598,7 +674,9 @@ def measure_space_variant(bf, torch, dev, stream, acc_jobs):
         acc_jobs.append((key, _sv_acc))
         res[key] = {"ms": ms, "mpx_s": H * W / (ms * 1e-3) / 1e6, "terms": plan.n_terms,
                     "achieved_tinstr_s": ops / (ms * 1e-3) / 1e12,
-                    "frac": ops / (ms * 1e-3) / peak}
+                    "frac": ops / (ms * 1e-3) / peak,
+                    "roofline": alu_roofline(ops, ms, _peak_ops(torch, dev),
+                                             "29 per pixel and term + 4 per pixel")}
     return res
 
 
@@ -652,12 +730,19 @@ def measure_batch(bf, torch, dev, stream):
 
     t_loop = _time(loop, torch, stream, 3)
     px = sum(h * w for (h, w, _, _) in specs)
+    ops = 0.0
+    for p, (h, w, _, _) in zip(plans, specs):
+        nz, center = _plan_counts(p)
+        ops += box_instr_per_px(nz, center) * h * w
+    peak = _peak_ops(torch, dev)
     return {"batch_config": "64 images, box sigma_s~U[2,16], sigma_r~U[15,60], N in [%d, %d]" % (
                 min(p.N for p in plans), max(p.N for p in plans)),
             "batch_mpx_s": px / (t_batch * 1e-3) / 1e6,
             "batch_images_s": len(plans) / (t_batch * 1e-3),
             "batch_loop_mpx_s": px / (t_loop * 1e-3) / 1e6,
-            "batch_ms": t_batch, "batch_loop_ms": t_loop, "batch_tuned": tuned}
+            "batch_ms": t_batch, "batch_loop_ms": t_loop, "batch_tuned": tuned,
+            "roofline_batch": alu_roofline(ops, t_batch, peak,
+                                           "box_instr_per_px x pixels, summed over the images")}
 
 
 def run_extras_only(which):

@@ -40,3 +40,26 @@ def test_reference_arm_line():
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_traffic_is_tied_to_the_kernel_sources(monkeypatch):
+    # the ncu DRAM figures are reported only for the build they were captured on
+    import bench
+    h = bench.kernel_sources_sha256()
+    assert h == bench.kernel_sources_sha256() and len(h) == 64
+    monkeypatch.setattr(bench, "DRAM_SOURCES_SHA256", h)
+    b, note = bench.dram_traffic(32.0)
+    assert b == bench.DRAM_BYTES_PER_CALL[32.0] and h[:12] in note
+    monkeypatch.setattr(bench, "DRAM_SOURCES_SHA256", "0" * 64)
+    b, note = bench.dram_traffic(32.0)
+    assert b is None and "not reported" in note
+
+
+def test_backward_operation_count_and_roofline_object():
+    # the adjoint's count for the differentiable workload (Gaussian R = 12,
+    # N = 43: 22 nonzero frequencies, no constant term) is ten planes through
+    # 2(2R+1) taps plus generation and combine per frequency
+    import bench
+    assert bench.gauss_bwd_instr_per_px(22, False, 12) == 22 * (35 + 10 * 50)
+    r = bench.alu_roofline(4.0e12, 100.0, 40.0e12, "x")
+    assert r["bound"] == "alu" and abs(r["achieved"] - 40.0) < 1e-9 and abs(r["frac"] - 1.0) < 1e-12
