@@ -40,7 +40,7 @@ cudaError_t launch_tile_box(const bf_plan *pl, const BfImage &img, cudaStream_t 
 using TuneKey = std::tuple<int, int, int, int, int, int>;
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tuned;
-constexpr int kMaxSplit = 8;
+constexpr int kMaxSplit = 16;
 
 static TuneKey tune_key(const bf_plan *p, const BfImage &img) {
     return TuneKey(p->kind, p->R, p->N, img.H, img.W, img.C);
@@ -463,7 +463,7 @@ extern "C" bf_status bf_forward_set_shape(const bf_plan *plan, int H, int W, int
     if ((split & (split - 1)) != 0 || split > kMaxSplit || split > (int)plan->a32.size() ||
         (long long)C * split > 65535)
         return fail(BF_EINVAL, "bf_forward_set_shape: term split " + std::to_string(split) +
-                                   " must be a power of two <= 8 and <= the number of terms");
+                                   " must be a power of two <= 16 and <= the number of terms");
     BfImage img{};
     img.H = H;
     img.W = W;

@@ -38,6 +38,10 @@ namespace bf {
 
 namespace cg = cooperative_groups;
 
+// Most term groups of a tile (blocks of one cluster; above 8 a non-portable
+// cluster size).
+constexpr int kMaxTermSplit = 16;
+
 constexpr float kTwoPi = 6.28318530717958647692f;
 
 // sin(2 pi r) for r in turns: the argument is first reduced to [-1/2, 1/2]
@@ -469,16 +473,16 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
         for (int i = g * per + tid; i < min((g + 1) * per, TH * TW); i += G::NT) {
             const int row = i / TW, col = i - (i / TW) * TW;
             const int si = row * G::SV + col;
-            float pr[8], qr[8];
+            float pr[kMaxTermSplit], qr[kMaxTermSplit];
 #pragma unroll
-            for (int r = 0; r < 8; ++r)
+            for (int r = 0; r < kMaxTermSplit; ++r)
                 if (r < S) {
                     pr[r] = cl.map_shared_rank(Xp, r)[si];
                     qr[r] = cl.map_shared_rank(Xq, r)[si];
                 }
             float pv = pr[0], qv = qr[0];
 #pragma unroll
-            for (int r = 1; r < 8; ++r)
+            for (int r = 1; r < kMaxTermSplit; ++r)
                 if (r < S) {
                     pv += pr[r];
                     qv += qr[r];
@@ -568,6 +572,12 @@ cudaError_t launch_tile(const TileParams &prm, cudaStream_t s) {
     dim3 grid((prm.img.W + TW - 1) / TW, (prm.img.H + TH - 1) / TH, prm.img.C * prm.split);
     if (prm.split > 1) {
         // a tile's term groups (consecutive z) as one cluster
+        static bool big_cluster[64] = {};
+        if (prm.split > 8 && dev >= 0 && dev < 64 && !big_cluster[dev]) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+            big_cluster[dev] = true;
+        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = grid;
         cfg.blockDim = dim3(G::NT);

@@ -190,9 +190,9 @@ def test_set_shape_term_split(bf):
     from paper_1105_4204_gb300 import _lib
     l = _lib.lib()
     g = bf.Plan(3.0, 30.0, kind="gauss")                           # 16 terms
-    for split in (0, 1, 2, 4, 8):
+    for split in (0, 1, 2, 4, 8, 16):
         assert l.bf_forward_set_shape(g.handle, 64, 64, 1, split << 8) == 0
-    for split in (3, 16):
+    for split in (3, 32):
         assert l.bf_forward_set_shape(g.handle, 64, 64, 1, split << 8) == 1
         assert b"split" in l.bf_last_error()
     one = bf.Plan(3.0, 200.0, kind="gauss")                        # N = 1: one term
