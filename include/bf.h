@@ -281,14 +281,17 @@ bf_status bf_forward_stack(const bf_plan *plan, const void *in, bf_dtype dt, flo
  *      Gaussian R >= 9)
  *   3  64 x 64 tiles, 32-pixel row segments, one 256-thread block per SM
  *      (box 7 <= r <= 8)
- * split (1, 2, 4 or 8; 0 reads as 1; the 32-row shapes 0 and 1 only): images
+ * split (1, 2, 4, 8 or 16; 0 reads as 1): images
  * with fewer tiles than the GPU has SMs cut the terms into `split`
  * consecutive groups, one block per tile and group, so that the grid fills
- * the GPU; the groups of a tile run as one thread-block cluster whose first
- * block adds the others' numerators and normalisers (read from their shared
- * memory) in group order and divides.  Nothing is allocated.  Without a tuned
- * configuration bf_forward picks the split that brings the blocks nearest two
- * per SM.  Different configurations sum the terms in different orders, so
+ * the GPU; the groups of a tile run as one thread-block cluster whose blocks
+ * each finish a slice of the tile, adding the groups' numerators and
+ * normalisers (read from every block's shared memory) in group order.
+ * Nothing is allocated.  The tuner and the default consider splits of the
+ * 32-row shapes 0 and 1 (a cluster of the 64-row shapes' one-block-per-SM
+ * blocks holds as many SMs); bf_forward_set_shape accepts any shape.
+ * Without a tuned configuration bf_forward picks the split that brings the
+ * blocks nearest two per SM.  Different configurations sum the terms in different orders, so
  * their results agree to FP32 rounding, not bit for bit; one configuration
  * gives the same bits run to run.
  */
@@ -395,10 +398,16 @@ bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, const float *
  * Batched forward: many f32 single-channel images of uneven sizes, each with
  * its own plan (own sigma_s, sigma_r and hence N), replayed from one CUDA
  * graph.  Images whose box half-width fits a tile (r <= 8) share ONE
- * persistent launch that pulls tiles from a device work queue, largest cost
- * first; images with 8 < r <= 64 run the streaming sweeps of bf_forward in
- * the same graph, in up to four concurrent chains (images spread over the
- * chains largest cost first), concurrently with the persistent launch.
+ * persistent launch that pulls work items (a tile, or a tile's group of
+ * terms) from a device work queue, largest cost first; each radius bucket
+ * r = 1 .. 8 has its own configuration (tile shape and term split, see
+ * bf_batch_set_config), and the term groups of split images are summed in
+ * group order by one more kernel.  Images with 8 < r <= 64 run the streaming
+ * sweeps of bf_forward in the same graph, in up to four concurrent chains
+ * (images spread over the chains largest cost first), concurrently with the
+ * persistent launch.  Each image's result is bit-identical to bf_forward's
+ * in the same configuration (bf_forward_set_shape with the bucket's shape
+ * and split).
  *
  * bf_batch_create  : plans[count], H[count], W[count] are host arrays; the
  *                    batch copies what it needs (the plans may be destroyed
@@ -427,12 +436,32 @@ bf_status bf_batch_check(bf_batch *batch, cudaStream_t stream, int *device_error
 void bf_batch_destroy(bf_batch *batch);
 
 /*
- * Launch-configuration autotuner for a bound batch (not in the paper): times
- * `reps` replays for each candidate -- persistent grid of 1x or 2x the
- * resident blocks, tile queue in largest-cost-first or image order -- keeps
- * the fastest in the batch's graph and reports it (any output may be NULL).
- * Synchronises `stream`.  The tile shape itself is fixed (32 x 64); the
- * streaming images are timed with the rest but not tuned here.
+ * Configuration of radius bucket r (1 <= r <= 8) of a batch (not in the
+ * paper): the tile shape of its images (ids as bf_forward_tune's, all with
+ * 256 threads per tile: 0 = 32 x 64 tiles, 8 pixels per thread; 1 = 32 x 96,
+ * 12 pixels per thread, r <= 4; 3 = 64 x 64, 16 pixels per thread,
+ * r = 7, 8) and the number of groups its terms are cut into (1, 2 or 4, each
+ * group of a tile a separate work item; split images keep their groups'
+ * numerators and normalisers in a batch-owned buffer of 2 * split * H * W
+ * floats).  bf_batch_config reads it (host only); bf_batch_set_config sets
+ * it, synchronises `stream`, re-uploads the batch's tables and captures its
+ * graph again.  Defaults: shape 0, split 1.  Errors: BF_EINVAL for r outside
+ * 1 .. 8, a shape the bucket does not have, a split other than 1, 2, 4.
+ */
+bf_status bf_batch_config(const bf_batch *batch, int r, int *shape, int *split);
+bf_status bf_batch_set_config(bf_batch *batch, int r, int shape, int split,
+                              cudaStream_t stream);
+
+/*
+ * Autotuner for a bound batch (not in the paper): for each radius bucket of
+ * tiled images in turn (largest share of the tile work first), every tile
+ * shape the bucket has and every term split (1, 2, 4), the other buckets as
+ * they stand; then the persistent grid (1x or 2x the resident blocks) and the
+ * queue order (largest cost first or image order).  Each candidate is timed
+ * as `reps` replays of the whole batch; the fastest configuration is kept in
+ * the batch's graph (bf_batch_config reads the buckets' choices) and the
+ * grid, order and time reported (any output may be NULL).  Synchronises
+ * `stream`.  The streaming images (r > 8) are timed with the rest.
  */
 bf_status bf_batch_tune(bf_batch *batch, cudaStream_t stream, int reps, int *grid,
                         int *order, float *ms);

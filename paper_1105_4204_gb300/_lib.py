@@ -74,6 +74,8 @@ def _declare(lib):
         "bf_batch_destroy": (None, [c_void_p]),
         "bf_batch_tune": (c_int, [c_void_p, c_void_p, c_int, _ip, _ip,
                                   ctypes.POINTER(ctypes.c_float)]),
+        "bf_batch_config": (c_int, [c_void_p, c_int, _ip, _ip]),
+        "bf_batch_set_config": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p]),
         "bf_release_scratch": (None, []),
         "bf_last_error": (c_char_p, []),
         "bf_version": (c_int, []),

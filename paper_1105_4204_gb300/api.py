@@ -407,11 +407,30 @@ class Batch:
         return err.value
 
     def tune(self, reps: int = 3, stream=None):
+        """Pick each radius bucket's tile shape and term split, then the
+        persistent grid and queue order, by timing the whole batch."""
         g, o, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
         check(self._lib.bf_batch_tune(self._h, _stream_ptr(stream), int(reps), ctypes.byref(g),
                                       ctypes.byref(o), ctypes.byref(ms)))
         return {"grid": g.value, "order": "largest-cost-first" if o.value == 0 else "image",
-                "ms": ms.value}
+                "ms": ms.value, "buckets": self.config()}
+
+    def config(self):
+        """{r: (shape name, split)} of the radius buckets r = 1 .. 8."""
+        names = {0: "32x64", 1: "32x96", 3: "64x64-seg32"}
+        out = {}
+        for r in range(1, 9):
+            sh, sp = ctypes.c_int(), ctypes.c_int()
+            check(self._lib.bf_batch_config(self._h, r, ctypes.byref(sh), ctypes.byref(sp)))
+            out[r] = (names[sh.value], sp.value)
+        return out
+
+    def set_config(self, r: int, shape: str, split: int = 1, stream=None):
+        """Pin radius bucket r's tile shape ("32x64", "32x96" for r <= 4,
+        "64x64-seg32" for r = 7, 8) and term split (1, 2 or 4)."""
+        ids = {"32x64": 0, "32x96": 1, "64x64-seg32": 3}
+        check(self._lib.bf_batch_set_config(self._h, int(r), ids[shape], int(split),
+                                            _stream_ptr(stream)))
 
     def __del__(self):
         h = getattr(self, "_h", None)

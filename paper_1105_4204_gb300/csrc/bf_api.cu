@@ -454,9 +454,6 @@ extern "C" bf_status bf_forward_set_shape(const bf_plan *plan, int H, int W, int
     bool ok = false;
     const int sid = shape & 0xff, split = std::max(1, shape >> 8);
     for (int i = 0; i < n; ++i) ok = ok || ids[i] == sid;
-    if (split > 1 && sid >= 2)
-        return fail(BF_EINVAL, "bf_forward_set_shape: the term split runs on the 32-row shapes "
-                               "(0 and 1) only");
     if (!ok || shape < 0) return fail(BF_EINVAL, "bf_forward_set_shape: shape " +
                                                      std::to_string(sid) +
                                                      " is not available for this support");

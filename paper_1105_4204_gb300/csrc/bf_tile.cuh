@@ -352,6 +352,11 @@ struct TileJob {
     // term groups of the tile (1: all terms in this block; > 1: this block
     // is one of a cluster of `split`, its rank the group)
     int split;
+    // or, when not NULL: this block's terms are one group of a tile whose
+    // groups run as separate work items; its P goes to slot (at the output's
+    // offsets; Q slot_n further) for a later sum over the groups
+    float *slot;
+    long long slot_n;
 };
 
 template <int KIND, int RAD, int TH, int TW, int TWT>
@@ -453,6 +458,16 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
     __syncthreads();
     float *Xq = VP;  // Q of the tile's pixels (row stride G::SV)
     float *Xp = VQ;  // P, kept in shared memory only by term-split blocks
+    if (jb.slot) {  // uniform: one term group's partial sums
+        const int gy = y0 + pi;
+        float *dstq = jb.slot + (pa == 1 ? jb.slot_n : 0);
+#pragma unroll
+        for (int k = 0; k < TWT; ++k) {
+            const int gx = x0 + ps * TWT + k;
+            if (gy < H && gx < W) dstq[((long long)gy * W + gx) * jb.out_px] = acc[k];
+        }
+        return;
+    }
     if (pa == 1) {
 #pragma unroll
         for (int k = 0; k < TWT; ++k) Xq[pi * G::SV + ps * TWT + k] = acc[k];
@@ -551,6 +566,8 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT,
     jb.x0 = blockIdx.x * TW;
     jb.y0 = blockIdx.y * TH;
     jb.split = p.split;
+    jb.slot = nullptr;
+    jb.slot_n = 0;
     tile_body<KIND, RAD, TH, TW, TWT>(jb, reinterpret_cast<float *>(smem4));
 }
 

@@ -22,12 +22,15 @@ def bf():
     return pkg
 
 
-def _single(bf, plan, img):
-    """bf_forward of one image in the configuration the batch runs: tiles of
-    32 x 64 with all terms in one block (bf_forward would cut the terms of a
-    small image into groups, which sums them in another order)."""
-    if plan.radius // 3 <= 8:
-        bf.set_shape(plan, img, "32x64", split=1)
+def _single(bf, plan, img, batch=None):
+    """bf_forward of one image in the configuration the batch runs for its
+    radius bucket (tile shape and term split; by default 32 x 64 tiles with all
+    terms in one block -- bf_forward alone would cut the terms of a small
+    image into groups, which sums them in another order)."""
+    r = plan.radius // 3
+    if r <= 8:
+        shape, split = batch.config()[r] if batch is not None else ("32x64", 1)
+        bf.set_shape(plan, img, shape, split=split)
     return bf.forward(plan, img)
 
 
@@ -90,9 +93,14 @@ def test_replay_tune_and_rebind(bf):
     specs = synth.batch_specs(10, seed=3, w_range=(64, 256), h_range=(64, 256))
     imgs, plans, ins, outs, b = _setup(bf, specs, seed=3)
     b.forward()
-    first = [o.clone() for o in outs]
+    before = [o.clone() for o in outs]
     info = b.tune(reps=2)
     assert info["grid"] >= 1 and info["ms"] > 0
+    b.forward()
+    first = [o.clone() for o in outs]
+    # the tuned configuration may sum the terms in groups: equal to rounding
+    for a, c in zip(before, first):
+        torch.testing.assert_close(a, c, rtol=0, atol=1e-3)
     for o in outs:
         o.zero_()
     b.forward()
@@ -131,3 +139,48 @@ def test_batch_of_streaming_images_only(bf, oracle):
         ref = oracle.bf_brute_at(imgs[i].astype(np.float64), idx, sigma_r=sr,
                                  w1=oracle.spatial_w1("box", ss), N=plans[i].N)
         assert np.abs(got.ravel()[idx] - ref).max() <= TOL
+
+
+@pytest.mark.parametrize("split", [1, 2, 4])
+def test_every_bucket_configuration_matches_single_image(bf, oracle, split):
+    # every radius bucket in every tile shape it has, with its terms in 1, 2
+    # or 4 groups per tile: each image bit for bit as bf_forward in the same
+    # configuration, and within the bar against the oracle
+    import torch
+    specs = [(70 + 9 * r, 150 - 7 * r, float(r), 20.0 + 3 * r) for r in range(1, 9)]
+    imgs, plans, ins, outs, b = _setup(bf, specs, seed=40 + split)
+    assert [p.radius // 3 for p in plans] == list(range(1, 9))
+    shapes = {r: ["32x64"] + (["32x96"] if r <= 4 else []) + (["64x64-seg32"] if r >= 7 else [])
+              for r in range(1, 9)}
+    for k in range(3):
+        for r in range(1, 9):
+            b.set_config(r, shapes[r][min(k, len(shapes[r]) - 1)], split)
+        b.forward()
+        assert b.check() == 0
+        cfg = b.config()
+        for i, (h, w, ss, sr) in enumerate(specs):
+            got = outs[i].cpu().numpy()
+            np.testing.assert_array_equal(got, _single(bf, plans[i], ins[i], b).cpu().numpy())
+            idx = synth.sample_indices(h, w, 60, seed=i + k)
+            ref = oracle.bf_brute_at(imgs[i].astype(np.float64), idx, sigma_r=sr,
+                                     w1=oracle.spatial_w1("box", ss), N=plans[i].N)
+            assert np.abs(got.ravel()[idx] - ref).max() <= TOL, (i, cfg[i + 1])
+
+
+def test_tuner_picks_a_configuration_per_bucket(bf):
+    import torch
+    specs = synth.batch_specs(20, seed=5, w_range=(100, 700), h_range=(100, 500))
+    imgs, plans, ins, outs, b = _setup(bf, specs, seed=5)
+    info = b.tune(reps=1)
+    assert set(info["buckets"]) == set(range(1, 9))
+    for r, (shape, split) in info["buckets"].items():
+        assert shape in ("32x64", "32x96", "64x64-seg32") and split in (1, 2, 4)
+    b.forward()
+    assert b.check() == 0
+    for i in range(len(plans)):
+        np.testing.assert_array_equal(outs[i].cpu().numpy(),
+                                      _single(bf, plans[i], ins[i], b).cpu().numpy())
+    with pytest.raises(Exception):
+        b.set_config(5, "32x96", 1)   # 32 x 96 tiles serve r <= 4
+    with pytest.raises(Exception):
+        b.set_config(3, "32x64", 3)   # splits 1, 2, 4
