@@ -212,10 +212,14 @@ bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *ou
  *     out(x) = sum_{|y|_inf <= r(x)} phi(f(x-y) - f(x)) f(x-y)
  *              / sum_{|y|_inf <= r(x)} phi(f(x-y) - f(x)).
  * Computed through eq. (final-form) with per-term summed-area tables of the
- * auxiliary images (64-bit fixed point, so every box sum is exact for the
- * fixed-point planes), O(1) per pixel and term whatever r(x).  The plan's own
- * spatial kernel is not used; its range kernel (raised cosine or cosine
- * polynomial) is.
+ * four auxiliary images of the tile, O(1) per pixel and term whatever r(x).
+ * The tables hold 32-bit fixed-point values whose step is set by r_max and,
+ * for the f-weighted planes, by the value range of the tile, so that every
+ * box sum comes out exact for the fixed-point planes; the step's rounding
+ * error is of the order of the FP32 sine's.  Results therefore depend, to
+ * rounding, on r_max (and on the tile each pixel falls in), not only on r(x).
+ * The plan's own spatial kernel is not used; its range kernel (raised cosine
+ * or cosine polynomial) is.  Input values must be finite.
  *   in               : device image, H x W, single channel, type dt, rows
  *                      row_stride_elems (>= W) elements apart
  *   radius           : device int32 H x W, row-major (row stride W): the

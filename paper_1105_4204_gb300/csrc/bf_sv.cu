@@ -5,28 +5,39 @@
 // images, which summed-area tables give in O(1) per pixel (the box filter the
 // section names; Crow's tables).
 //
-// One CTA owns a kSvT x kSvT output tile.  It reads the tile plus a halo of RM
-// (clamp-to-edge) once, then for every term and for each of the two pairs
-// (cos, sin) -> Q and (f cos, f sin) -> P:
-//   1. generates the pair's planes over the extended tile and stores each
-//      value as the fixed-point integer q = round(v * 2^26), split as
-//      q = hi * 2^20 + lo (|hi| <= 2^14, |lo| <= 2^19), in two 32-bit tables
-//      per plane whose row 0 and column 0 stay zero;
-//   2. turns the four tables into summed-area tables (running sums along
-//      rows, then along columns, a thread per line) in wrapping 32-bit
-//      arithmetic;
-//   3. reads each own pixel's box sums from four entries of each table --
-//      exact, since a box of at most 33 x 33 keeps both halves' sums inside
-//      32 bits -- and accumulates a_m (cos(w f(x)) S[. cos] + sin(w f(x))
-//      S[. sin]) into Q or P.
-// Integer tables make every box sum exact for the fixed-point planes (no
-// cancellation between large prefix sums, which in FP32 would lose the small
-// boxes); the fixed-point step is 2^-26 (1.5e-8 of a unit plane value, below
-// the FP32 sine's own error).  The split into 32-bit halves is done with FP32
-// additions (adding 1.5 * 2^23 to a float below 2^22 rounds it to the nearest
-// integer and leaves that integer in its low mantissa bits), because
-// conversions between FP32 and 64-bit integers run on the FP64 pipe, which
-// on this GPU is narrow: with 64-bit tables they were the kernel's limit.
+// One CTA owns a T x T output tile.  It reads the tile plus a halo of RM
+// (clamp-to-edge) once and centres it: f~ = f - c, c the middle of the
+// extended tile's range, h = max |f~| (the range kernel depends only on
+// differences, so any per-tile offset gives the same filter; it halves the
+// magnitude of the f-weighted planes).  Then, for every term m:
+//   1. a thread per (plane, row) generates one row of one of the four planes
+//        cos(w f~), sin(w f~), f~ cos(w f~), f~ sin(w f~)
+//      over the extended tile (the sine as the cosine a quarter turn back),
+//      converts each value to the fixed-point integer round(v 2^k) and keeps
+//      its running sum along the row in a register, writing each table entry
+//      once;
+//   2. a thread per (plane, column) adds the rows up: four summed-area tables
+//      in wrapping 32-bit arithmetic, row 0 and column 0 zero;
+//   3. each own pixel reads its box sum of every plane from four entries of
+//      its table and accumulates a_m (cos(w f~(x)) S[. cos] + sin(w f~(x))
+//      S[. sin]) into Q (the plain planes) or P (the f~-weighted ones).
+// out(x) = c + P / Q, with the fixed-point scales taken out as one power of
+// two.
+//
+// Exactness.  Every plane value is |v| <= 1 (cos, sin) or |v| <= h (f~ cos,
+// f~ sin).  The step 2^-k is chosen per plane pair so that |round(v 2^k)| <
+// 2^21 and a box of (2 RM + 1)^2 values sums to less than 2^31 in magnitude:
+// every box sum then comes out exact from the wrapping 32-bit tables, however
+// large the prefix sums grow (no cancellation between large prefix sums, which
+// in FP32 would lose the small boxes).  k is fixed by RM for the plain planes
+// (2^-21 for boxes up to 17 x 17, 2^-20 up to 33 x 33) and set per tile from
+// h for the weighted ones (2^-13 for a 33 x 33 box and h = 127.5); the
+// rounding error per entry is then of the order of the FP32 sine's own.
+// Rounding to the integer is one FMA against 1.5 * 2^23: the sum lands in
+// [2^23, 2^24), where the FP32 spacing is 1, so the integer sits in the low
+// mantissa bits.  The tables keep those bit patterns as they are; their
+// constant part, 1.5 * 2^23's bit pattern per entry, is taken out of each box
+// sum as (box area) x that pattern.
 // HBM sees f and the radius map read once and out written once.
 #include <cstdint>
 
@@ -37,10 +48,9 @@ namespace bf {
 
 namespace {
 
-constexpr int kSvT = 32;         // output tile edge
-constexpr int kSvThreads = 256;  // 4 own pixels per thread
-constexpr float kSvScale = 67108864.f;            // 2^26
-constexpr float kSvInvScale = 1.f / 67108864.f;   // 2^-26 (exact)
+constexpr float kSvMagic = 12582912.f;      // 1.5 * 2^23
+constexpr unsigned kSvMagicBits = 0x4B400000u;  // its bit pattern
+constexpr int kSvMaxQ = 21;                 // |round(v 2^k)| <= 2^21 < 2^22
 
 struct SvParams {
     const void *in;
@@ -53,173 +63,230 @@ struct SvParams {
     BfTerms terms;
 };
 
-// round(v * 2^26) = hi * 2^20 + lo for |v| < 2^8, exactly, by FP32 additions.
-__device__ __forceinline__ void fixed_split(float v, unsigned &hi, unsigned &lo) {
-    constexpr float kM = 12582912.f;  // 1.5 * 2^23
-    const float x = v * kSvScale;     // exact (a power of two)
-    const float th = __fadd_rn(x * 9.5367431640625e-07f, kM);  // round(x / 2^20) + kM
-    hi = (unsigned)(__float_as_int(th) - __float_as_int(kM));
-    // x - round(x / 2^20) 2^20 is representable: the FMA is exact
-    const float l = __fmaf_rn(-__fsub_rn(th, kM), 1048576.f, x);
-    lo = (unsigned)(__float_as_int(__fadd_rn(l, kM)) - __float_as_int(kM));
+// Largest k <= 21 with 2^k * nbox below 2^31 (with a 0.1 % margin): the
+// fixed-point exponent of the plain planes, |v| <= 1.
+constexpr int sv_plain_exponent(int nbox) {
+    int k = kSvMaxQ;
+    while (k > 0 && (double)(1LL << k) * nbox >= 0.999 * 2147483648.0) --k;
+    return k;
 }
 
-template <int RM>
+// Smallest n' >= n with n' = rem (mod 32): the table stride that puts the
+// planes of a shared warp into disjoint banks (see the line layout below).
+constexpr int sv_table_stride(int n, int rem) {
+    if (rem == 0) return n;
+    while (n % 32 != rem) ++n;
+    return n;
+}
+
+template <int RM, int T, int NTHR>
 struct SvGeom {
-    static constexpr int E = kSvT + 2 * RM;  // extended tile edge
-    static constexpr int ES = E + 1;         // table edge (zero row / column first)
-    static constexpr int NT = 4;             // tables per pass: (hi, lo) of two planes
-    static constexpr size_t SMEM =
-        sizeof(unsigned) * NT * ES * ES + sizeof(float) * E * E;
-    static_assert(NT * E <= kSvThreads, "a thread per table line");
+    static constexpr int E = T + 2 * RM;  // extended tile edge
+    static constexpr int ES = E + 1;      // table edge (a zero row and column first)
+    static constexpr int FS = E + 1;      // f~ tile row stride: odd, so that a thread
+                                          // per row reads without bank conflicts
+    // Table lines (a row in step 1, a column in step 2) go to threads in
+    // blocks of 32 lines of one plane; the remaining E % 32 lines of the four
+    // planes share warps, with the same line numbers in every plane (one
+    // broadcast read of f~) and tables RMD banks apart.
+    static constexpr int F = E / 32 * 32;  // lines per plane in whole warps
+    static constexpr int RMD = E - F;      // remaining lines per plane
+    static constexpr int TS = sv_table_stride(ES * ES, RMD);  // entries per table
+    static constexpr int NBOX = (2 * RM + 1) * (2 * RM + 1);  // largest box
+    static constexpr int KQ = sv_plain_exponent(NBOX);
+    static constexpr int OWN = T * T / NTHR;  // own pixels per thread
+    static constexpr size_t SMEM = sizeof(unsigned) * 4 * TS + sizeof(float) * E * FS;
+    static_assert(4 * E <= NTHR, "a thread per table row and per table column");
+    static_assert(NTHR % T == 0 && NTHR % 32 == 0 && T % 32 == 0, "own-pixel layout");
+    static_assert(RMD == 0 || 32 % RMD == 0, "whole planes of remaining lines per warp");
 };
 
-template <int RM>
-__global__ void __launch_bounds__(kSvThreads) bf_sv_fwd(const __grid_constant__ SvParams p) {
-    using G = SvGeom<RM>;
-    constexpr int E = G::E, ES = G::ES, NT = G::NT;
-    constexpr int TS = ES * ES;  // entries per table
+// 2^k for -126 <= k <= 127, exactly.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+template <int RM, int T, int NTHR>
+__global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvParams p) {
+    using G = SvGeom<RM, T, NTHR>;
+    constexpr int E = G::E, ES = G::ES, FS = G::FS, TS = G::TS, OWN = G::OWN;
+    constexpr int NW = NTHR / 32;
     extern __shared__ unsigned sv_smem[];
-    // tables: 0 hi / 1 lo of the pair's first plane, 2 hi / 3 lo of its second
+    // tables 0 cos, 1 sin, 2 f~ cos, 3 f~ sin, then the E x E f~ tile
     unsigned *Tb = sv_smem;
-    float *Fs = reinterpret_cast<float *>(Tb + NT * TS);  // E x E extended f tile
+    float *Fs = reinterpret_cast<float *>(Tb + 4 * TS);
+    __shared__ float red[2][NW];
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kSvT, y0 = blockIdx.y * kSvT;
+    const int x0 = blockIdx.x * T, y0 = blockIdx.y * T;
     const int H = p.H, W = p.W;
 
-    for (int idx = tid; idx < E * E; idx += kSvThreads) {
+    // ---- the extended tile, its range and its centre ----
+    float mn = __int_as_float(0x7f800000), mx = -mn;
+    for (int idx = tid; idx < E * E; idx += NTHR) {
         const int i = idx / E, j = idx - (idx / E) * E;
         const int gy = min(max(y0 - RM + i, 0), H - 1);
         const int gx = min(max(x0 - RM + j, 0), W - 1);
         const long long off = (long long)gy * p.in_stride + gx;
-        Fs[idx] = p.dtype == 0 ? __ldg(reinterpret_cast<const float *>(p.in) + off)
-                               : (float)__ldg(reinterpret_cast<const uint8_t *>(p.in) + off);
+        const float v = p.dtype == 0 ? __ldg(reinterpret_cast<const float *>(p.in) + off)
+                                     : (float)__ldg(reinterpret_cast<const uint8_t *>(p.in) + off);
+        Fs[i * FS + j] = v;
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
     }
-    for (int k = tid; k < ES; k += kSvThreads) {  // the zero row and column of every table
+    for (int k = tid; k < ES; k += NTHR) {  // the zero row and column of every table
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
+        for (int t = 0; t < 4; ++t) {
             Tb[t * TS + k] = 0u;
             Tb[t * TS + k * ES] = 0u;
         }
     }
-
-    // own pixels: k-th of this thread at tile row (tid / 32) + 8 k, column tid % 32
-    constexpr int kOwn = kSvT * kSvT / kSvThreads;
-    int rad[kOwn];
-    float fown[kOwn];
-    bool ok[kOwn];
 #pragma unroll
-    for (int k = 0; k < kOwn; ++k) {
-        const int pi = tid / kSvT + k * (kSvThreads / kSvT), pj = tid % kSvT;
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = mn;
+        red[1][tid >> 5] = mx;
+    }
+    __syncthreads();
+    mn = red[0][0];
+    mx = red[1][0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) {
+        mn = fminf(mn, red[0][w]);
+        mx = fmaxf(mx, red[1][w]);
+    }
+    const float c = mn + 0.5f * (mx - mn);
+    // fl(f - c) is monotone in f, so these two bound every centred value
+    const float h = fmaxf(mx - c, c - mn);
+    // weighted planes: largest 2^kp with h 2^kp <= min(2^21, 0.999 * 2^31 / NBOX)
+    constexpr float kCap = (float)(0.999 * 2147483648.0 / G::NBOX) < (float)(1 << kSvMaxQ)
+                               ? (float)(0.999 * 2147483648.0 / G::NBOX)
+                               : (float)(1 << kSvMaxQ);
+    const float lim = kCap / fmaxf(h, 1e-30f);
+    const int kp = min(max((__float_as_int(lim) >> 23) - 127, -60), 60);  // floor(log2(lim))
+    const float sP = pow2f(kp), sQ = pow2f(G::KQ);
+    for (int idx = tid; idx < E * E; idx += NTHR) {
+        const int i = idx / E, j = idx - (idx / E) * E;
+        Fs[i * FS + j] -= c;
+    }
+
+    // own pixels: k-th of this thread at tile row tid / T + (NTHR / T) k, column tid % T
+    int rad[OWN];
+    float fo[OWN];
+#pragma unroll
+    for (int k = 0; k < OWN; ++k) {
+        const int pi = tid / T + k * (NTHR / T), pj = tid % T;
         const int gy = y0 + pi, gx = x0 + pj;
-        ok[k] = gy < H && gx < W;
-        const int r = ok[k] ? __ldg(p.radius + (long long)gy * W + gx) : 0;
+        const int r = (gy < H && gx < W) ? __ldg(p.radius + (long long)gy * W + gx) : 0;
         rad[k] = min(max(r, 0), p.r_max);
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kOwn; ++k) {
-        const int pi = tid / kSvT + k * (kSvThreads / kSvT), pj = tid % kSvT;
-        fown[k] = Fs[(RM + pi) * E + RM + pj];
+    for (int k = 0; k < OWN; ++k) {
+        const int pi = tid / T + k * (NTHR / T), pj = tid % T;
+        fo[k] = Fs[(RM + pi) * FS + RM + pj];
     }
 
-    float P[kOwn], Q[kOwn], cx[kOwn], sx[kOwn];
+    float P[OWN], Q[OWN];
 #pragma unroll
-    for (int k = 0; k < kOwn; ++k) P[k] = Q[k] = 0.f;
+    for (int k = 0; k < OWN; ++k) P[k] = Q[k] = 0.f;
+
+    // this thread's table line in steps 1 and 2: plane q, row (step 1) or column (step 2) l
+    const bool line = tid < 4 * E;
+    int q, l;
+    if (tid < 4 * G::F) {
+        q = tid / G::F;
+        l = tid - q * G::F;
+    } else {
+        const int i = tid - 4 * G::F;
+        q = G::RMD > 0 ? i / max(G::RMD, 1) : 0;
+        l = G::F + i - q * G::RMD;
+    }
+    const float quarter = (q & 1) ? 0.25f : 0.f;  // sin(x) = cos(x - quarter turn)
+    const bool weighted = q >= 2;
 
     for (int m = 0; m < p.terms.n_terms; ++m) {
         const float am = p.terms.a[m], tm = p.terms.t[m];
-#pragma unroll
-        for (int k = 0; k < kOwn; ++k) {
-            float rr = tm * fown[k];
-            rr = rr - rintf(rr);
-            __sincosf(kTwoPi * rr, &sx[k], &cx[k]);
-        }
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {  // 0: (cos, sin) -> Q; 1: (f cos, f sin) -> P
-            // 1. the pair's planes, fixed point, at table entry (i + 1, j + 1)
-            for (int idx = tid; idx < E * E; idx += kSvThreads) {
-                const int i = idx / E, j = idx - (idx / E) * E;
-                const float fv = Fs[idx];
-                float rr = tm * fv;
+        // 1. one plane row: fixed point, running sum along the row
+        if (line) {
+            const float *frow = Fs + l * FS;
+            unsigned *row = Tb + q * TS + (l + 1) * ES + 1;
+            unsigned run = 0u;
+#pragma unroll 4
+            for (int j = 0; j < E; ++j) {
+                const float fv = frow[j];
+                float rr = __fmaf_rn(tm, fv, -quarter);
                 rr = rr - rintf(rr);
-                float sn, cs;
-                __sincosf(kTwoPi * rr, &sn, &cs);
-                if (pass == 1) {
-                    cs = cs * fv;
-                    sn = sn * fv;
-                }
-                unsigned *e0 = Tb + (i + 1) * ES + j + 1;
-                fixed_split(cs, e0[0], e0[TS]);
-                fixed_split(sn, e0[2 * TS], e0[3 * TS]);
+                const float v = __cosf(kTwoPi * rr);
+                const float s = weighted ? fv * sP : sQ;
+                run += __float_as_uint(__fmaf_rn(v, s, kSvMagic));
+                row[j] = run;
             }
-            __syncthreads();
-            // 2. summed-area tables: rows, then columns (a thread per line)
-            if (tid < NT * E) {
-                unsigned *row = Tb + (tid / E) * TS + (tid % E + 1) * ES;
-                unsigned run = 0u;
-                for (int j = 1; j < ES; ++j) {
-                    run += row[j];
-                    row[j] = run;
-                }
-            }
-            __syncthreads();
-            if (tid < NT * E) {
-                unsigned *col = Tb + (tid / E) * TS + tid % E + 1;
-                unsigned run = 0u;
-                for (int i = 1; i < ES; ++i) {
-                    run += col[i * ES];
-                    col[i * ES] = run;
-                }
-            }
-            __syncthreads();
-            // 3. box sums at the own pixels
-#pragma unroll
-            for (int k = 0; k < kOwn; ++k) {
-                const int pi = tid / kSvT + k * (kSvThreads / kSvT), pj = tid % kSvT;
-                const int r = rad[k];
-                const int a0 = RM + pi - r, a1 = RM + pi + r + 1;
-                const int b0 = RM + pj - r, b1 = RM + pj + r + 1;
-                float bs[2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const unsigned *Th = Tb + (2 * q) * TS, *Tl = Th + TS;
-                    const int sh = (int)(Th[a1 * ES + b1] - Th[a0 * ES + b1] - Th[a1 * ES + b0] +
-                                         Th[a0 * ES + b0]);
-                    const int sl = (int)(Tl[a1 * ES + b1] - Tl[a0 * ES + b1] - Tl[a1 * ES + b0] +
-                                         Tl[a0 * ES + b0]);
-                    bs[q] = fmaf(__int2float_rn(sh), 1048576.f, __int2float_rn(sl)) * kSvInvScale;
-                }
-                const float v = am * fmaf(cx[k], bs[0], sx[k] * bs[1]);
-                if (pass == 0) Q[k] += v;
-                else P[k] += v;
-            }
-            __syncthreads();  // the tables are rewritten next
         }
-    }
+        __syncthreads();
+        // 2. the columns: summed-area tables
+        if (line) {
+            unsigned *col = Tb + q * TS + ES + l + 1;
+            unsigned run = 0u;
+#pragma unroll 4
+            for (int i = 0; i < E; ++i) {
+                run += col[i * ES];
+                col[i * ES] = run;
+            }
+        }
+        __syncthreads();
+        // 3. box sums at the own pixels
 #pragma unroll
-    for (int k = 0; k < kOwn; ++k) {
-        const int pi = tid / kSvT + k * (kSvThreads / kSvT), pj = tid % kSvT;
-        if (ok[k]) p.out[(long long)(y0 + pi) * W + x0 + pj] = P[k] / Q[k];
+        for (int k = 0; k < OWN; ++k) {
+            const int pi = tid / T + k * (NTHR / T), pj = tid % T;
+            // the own pixel's cos and sin, computed as its table entries are
+            float rc = tm * fo[k];
+            rc = rc - rintf(rc);
+            float rs = __fmaf_rn(tm, fo[k], -0.25f);
+            rs = rs - rintf(rs);
+            const float cx = __cosf(kTwoPi * rc), sx = __cosf(kTwoPi * rs);
+            const int r = rad[k];
+            const int a0 = (RM + pi - r) * ES, a1 = (RM + pi + r + 1) * ES;
+            const int b0 = RM + pj - r, b1 = RM + pj + r + 1;
+            const unsigned bias = (unsigned)((2 * r + 1) * (2 * r + 1)) * kSvMagicBits;
+            float S[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const unsigned *Tt = Tb + t * TS;
+                const unsigned s = Tt[a1 + b1] - Tt[a0 + b1] - Tt[a1 + b0] + Tt[a0 + b0] - bias;
+                S[t] = __int2float_rn((int)s);
+            }
+            Q[k] = __fmaf_rn(am, __fmaf_rn(cx, S[0], sx * S[1]), Q[k]);
+            P[k] = __fmaf_rn(am, __fmaf_rn(cx, S[2], sx * S[3]), P[k]);
+        }
+        __syncthreads();  // the tables are rewritten next
+    }
+    // P is in units of 2^-kp, Q in units of 2^-KQ
+    const float back = pow2f(G::KQ - kp);
+#pragma unroll
+    for (int k = 0; k < OWN; ++k) {
+        const int pi = tid / T + k * (NTHR / T), pj = tid % T;
+        const int gy = y0 + pi, gx = x0 + pj;
+        if (gy < H && gx < W) p.out[(long long)gy * W + gx] = c + P[k] / Q[k] * back;
     }
 }
 
-template <int RM>
+template <int RM, int T, int NTHR>
 cudaError_t launch_sv(const SvParams &prm, cudaStream_t s) {
-    using G = SvGeom<RM>;
+    using G = SvGeom<RM, T, NTHR>;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(bf_sv_fwd<RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)G::SMEM);
+        e = cudaFuncSetAttribute(bf_sv_fwd<RM, T, NTHR>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    dim3 grid((prm.W + kSvT - 1) / kSvT, (prm.H + kSvT - 1) / kSvT);
-    bf_sv_fwd<RM><<<grid, kSvThreads, G::SMEM, s>>>(prm);
+    dim3 grid((prm.W + T - 1) / T, (prm.H + T - 1) / T);
+    bf_sv_fwd<RM, T, NTHR><<<grid, NTHR, G::SMEM, s>>>(prm);
     return cudaGetLastError();
 }
 
@@ -240,9 +307,9 @@ cudaError_t launch_space_variant(const bf_plan *pl, const void *in, int dtype,
     prm.H = H;
     prm.W = W;
     fill_terms(pl, &prm.terms);
-    if (r_max <= 4) return launch_sv<4>(prm, s);
-    if (r_max <= 8) return launch_sv<8>(prm, s);
-    return launch_sv<16>(prm, s);
+    if (r_max <= 4) return launch_sv<4, 32, 256>(prm, s);
+    if (r_max <= 8) return launch_sv<8, 32, 256>(prm, s);
+    return launch_sv<16, 64, 512>(prm, s);
 }
 
 }  // namespace bf

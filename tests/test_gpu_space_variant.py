@@ -84,8 +84,9 @@ def test_radii_are_clamped_and_u8_matches_f32(bf):
     wild[1::3] -= 40
     np.testing.assert_array_equal(_sv(bf, img, wild, plan, 6),
                                   _sv(bf, img, np.clip(wild, 0, 6), plan, 6))
-    # the same result with a larger table: only the halo grows
-    np.testing.assert_array_equal(a, _sv(bf, img, rad, plan, 16))
+    # the same filter with a larger table: the halo, the tile and the
+    # fixed-point steps change, so the results agree to rounding
+    assert np.abs(a - _sv(bf, img, rad, plan, 16)).max() <= 1e-3
 
 
 def test_full_size_sampled_and_deterministic(bf, oracle):
