@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
             const float *frow = Fs + l * FS;
             unsigned *row = Tb + q * TS + (l + 1) * ES + 1;
             unsigned run = 0u;
-#pragma unroll 4
+#pragma unroll 8
             for (int j = 0; j < E; ++j) {
                 const float fv = frow[j];
                 float rr = __fmaf_rn(tm, fv, -quarter);
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
         if (line) {
             unsigned *col = Tb + q * TS + ES + l + 1;
             unsigned run = 0u;
-#pragma unroll 4
+#pragma unroll 8
             for (int i = 0; i < E; ++i) {
                 run += col[i * ES];
                 col[i * ES] = run;
