@@ -109,7 +109,10 @@ def test_biased_wrapping_tables_give_exact_box_sums():
     # make every prefix sum wrap and every box sum reach its largest value
     for k, rmax, kind in [(21, 8, "uniform"), (21, 8, "max"), (20, 16, "uniform"),
                           (20, 16, "min"), (13, 16, "uniform")]:
-        lim = np.float32(CAP / 2.0 ** k)
+        # the largest rounded magnitude at this box size: 2^k for the plain
+        # planes (|v| <= 1), the cap for the weighted ones
+        bound = min(float(CAP), 0.999 * 2.0 ** 31 / _nbox(rmax))
+        lim = np.float32(bound / 2.0 ** k)
         if kind == "uniform":
             v = rng.uniform(-lim, lim, (E, E)).astype(np.float32)
         else:
