@@ -460,12 +460,14 @@ bf_status bf_batch_set_config(bf_batch *batch, int r, int shape, int split,
  * Autotuner for a bound batch (not in the paper): for each radius bucket of
  * tiled images in turn (largest share of the tile work first), every tile
  * shape the bucket has and every term split (1, 2, 4), the other buckets as
- * they stand; then the persistent grid (1x or 2x the resident blocks) and the
- * queue order (largest cost first or image order).  Each candidate is timed
- * as `reps` replays of the whole batch; the fastest configuration is kept in
- * the batch's graph (bf_batch_config reads the buckets' choices) and the
- * grid, order and time reported (any output may be NULL).  Synchronises
- * `stream`.  The streaming images (r > 8) are timed with the rest.
+ * they stand, each timed as the fastest of 2 reps + 1 launches of the tiled
+ * images alone; then the persistent grid (1x or 2x the resident blocks) and
+ * the queue order (largest cost first or image order), each timed as the
+ * fastest of `reps` replays of the whole batch, streaming images (r > 8)
+ * included.  A candidate replaces the configuration in hand only when more
+ * than 1 % faster.  The result is kept in the batch's graph (bf_batch_config
+ * reads the buckets' choices) and the grid, order and whole-batch time
+ * reported (any output may be NULL).  Synchronises `stream`.
  */
 bf_status bf_batch_tune(bf_batch *batch, cudaStream_t stream, int reps, int *grid,
                         int *order, float *ms);

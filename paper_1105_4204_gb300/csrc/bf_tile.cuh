@@ -359,7 +359,10 @@ struct TileJob {
     long long slot_n;
 };
 
-template <int KIND, int RAD, int TH, int TW, int TWT>
+// CLUSTER: the block is one term group of a cluster (TileJob::split > 1) and
+// the epilogue reduces the cluster's groups; a separate instantiation, so
+// that blocks holding all terms compile without that code.
+template <int KIND, int RAD, int TH, int TW, int TWT, bool CLUSTER = false>
 __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
     using G = TileGeom<KIND, RAD, TH, TW, TWT>;
     constexpr int HALO = G::HALO, EH = G::EH, EW = G::EW;
@@ -471,12 +474,12 @@ __device__ __forceinline__ void tile_body(const TileJob &jb, float *smem) {
     if (pa == 1) {
 #pragma unroll
         for (int k = 0; k < TWT; ++k) Xq[pi * G::SV + ps * TWT + k] = acc[k];
-    } else if (jb.split > 1) {
+    } else if (CLUSTER) {
 #pragma unroll
         for (int k = 0; k < TWT; ++k) Xp[pi * G::SV + ps * TWT + k] = acc[k];
     }
     __syncthreads();
-    if (jb.split > 1) {
+    if constexpr (CLUSTER) {
         // the tile's term groups form one cluster: block g of the cluster
         // finishes the g-th slice of the tile's pixels, adding the groups' P
         // and Q (read from every block's shared memory) in group order
@@ -538,7 +541,7 @@ struct TileMinBlocks {
     static constexpr int value = TH > 32 ? 1 : (KIND == 1 && RAD <= 2 && TW == 64) ? 3 : 2;
 };
 
-template <int KIND, int RAD, int TH, int TW, int TWT>
+template <int KIND, int RAD, int TH, int TW, int TWT, bool CLUSTER>
 __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT,
                                   TileMinBlocks<KIND, RAD, TH, TW>::value)
     bf_tile_fwd(const __grid_constant__ TileParams p) {
@@ -568,47 +571,72 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT,
     jb.split = p.split;
     jb.slot = nullptr;
     jb.slot_n = 0;
-    tile_body<KIND, RAD, TH, TW, TWT>(jb, reinterpret_cast<float *>(smem4));
+    tile_body<KIND, RAD, TH, TW, TWT, CLUSTER>(jb, reinterpret_cast<float *>(smem4));
 }
 
-// Host-side launcher for one instantiation.
-template <int KIND, int RAD, int TH, int TW, int TWT>
-cudaError_t launch_tile(const TileParams &prm, cudaStream_t s) {
-    using G = TileGeom<KIND, RAD, TH, TW, TWT>;
-    auto kern = bf_tile_fwd<KIND, RAD, TH, TW, TWT>;
-    // the dynamic shared-memory opt-in is per device
-    static bool attr_set[64] = {};
+// The dynamic shared-memory opt-in of one kernel, once per device.
+template <typename K>
+cudaError_t tile_smem_attr(K kern, size_t smem, bool *done) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        if (dev >= 0 && dev < 64) done[dev] = true;
     }
-    dim3 grid((prm.img.W + TW - 1) / TW, (prm.img.H + TH - 1) / TH, prm.img.C * prm.split);
-    if (prm.split > 1) {
-        // a tile's term groups (consecutive z) as one cluster
-        static bool big_cluster[64] = {};
-        if (prm.split > 8 && dev >= 0 && dev < 64 && !big_cluster[dev]) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            if (e != cudaSuccess) return e;
-            big_cluster[dev] = true;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = grid;
-        cfg.blockDim = dim3(G::NT);
-        cfg.dynamicSmemBytes = G::SMEM;
-        cfg.stream = s;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 1;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = prm.split;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, kern, prm);
+    return cudaSuccess;
+}
+
+// Launcher of the term-split (cluster) instantiation: prm.split > 1 groups of
+// a tile's terms as one thread-block cluster.  Defined, and instantiated for
+// every tile shape, in bf_tile_split.cu.
+template <int KIND, int RAD, int TH, int TW, int TWT>
+cudaError_t launch_tile_cluster(const TileParams &prm, cudaStream_t s);
+
+template <int KIND, int RAD, int TH, int TW, int TWT>
+cudaError_t launch_tile_cluster_impl(const TileParams &prm, cudaStream_t s) {
+    using G = TileGeom<KIND, RAD, TH, TW, TWT>;
+    auto kern = bf_tile_fwd<KIND, RAD, TH, TW, TWT, true>;
+    static bool attr_set[64] = {}, big_cluster[64] = {};
+    cudaError_t e = tile_smem_attr(kern, G::SMEM, attr_set);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (prm.split > 8 && dev >= 0 && dev < 64 && !big_cluster[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        big_cluster[dev] = true;
     }
+    // a tile's term groups (consecutive z) as one cluster
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((prm.img.W + TW - 1) / TW, (prm.img.H + TH - 1) / TH,
+                       prm.img.C * prm.split);
+    cfg.blockDim = dim3(G::NT);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = prm.split;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, prm);
+}
+
+// Host-side launcher for one instantiation (all terms per block, or the
+// term-split cluster launch when prm.split > 1).
+template <int KIND, int RAD, int TH, int TW, int TWT>
+cudaError_t launch_tile(const TileParams &prm, cudaStream_t s) {
+    using G = TileGeom<KIND, RAD, TH, TW, TWT>;
+    if (prm.split > 1) return launch_tile_cluster<KIND, RAD, TH, TW, TWT>(prm, s);
+    auto kern = bf_tile_fwd<KIND, RAD, TH, TW, TWT, false>;
+    static bool attr_set[64] = {};
+    cudaError_t e = tile_smem_attr(kern, G::SMEM, attr_set);
+    if (e != cudaSuccess) return e;
+    dim3 grid((prm.img.W + TW - 1) / TW, (prm.img.H + TH - 1) / TH, prm.img.C);
     kern<<<grid, G::NT, G::SMEM, s>>>(prm);
     return cudaGetLastError();
 }
