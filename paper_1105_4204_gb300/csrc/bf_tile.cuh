@@ -547,8 +547,9 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT,
     bf_tile_fwd(const __grid_constant__ TileParams p) {
     extern __shared__ float4 smem4[];
     TileJob jb;
-    const int z = blockIdx.z / p.split;   // plane
-    const int sg = blockIdx.z % p.split;  // term group
+    // plane and term group (all terms, group 0, without a cluster)
+    const int z = CLUSTER ? blockIdx.z / p.split : blockIdx.z;
+    const int sg = CLUSTER ? blockIdx.z % p.split : 0;
     const int esz = p.img.dtype == 0 ? 4 : 1;
     jb.in = reinterpret_cast<const char *>(p.img.in) + (long long)z * p.img.in_z * esz;
     jb.out = p.img.out + (long long)z * p.img.out_z;
@@ -561,14 +562,20 @@ __global__ void __launch_bounds__(TileGeom<KIND, RAD, TH, TW, TWT>::NT,
     jb.dtype = p.img.dtype;
     jb.q_scale = p.img.q_scale;
     const int nt = p.terms.n_terms;
-    const int m0 = sg * nt / p.split, m1 = (sg + 1) * nt / p.split;
-    jb.a = p.terms.a + m0;
-    jb.t = p.terms.t + m0;
-    jb.n_terms = m1 - m0;
+    if constexpr (CLUSTER) {
+        const int m0 = sg * nt / p.split, m1 = (sg + 1) * nt / p.split;
+        jb.a = p.terms.a + m0;
+        jb.t = p.terms.t + m0;
+        jb.n_terms = m1 - m0;
+    } else {
+        jb.a = p.terms.a;
+        jb.t = p.terms.t;
+        jb.n_terms = nt;
+    }
     jb.w2 = p.taps.w2;
     jb.x0 = blockIdx.x * TW;
     jb.y0 = blockIdx.y * TH;
-    jb.split = p.split;
+    jb.split = CLUSTER ? p.split : 1;
     jb.slot = nullptr;
     jb.slot_n = 0;
     tile_body<KIND, RAD, TH, TW, TWT, CLUSTER>(jb, reinterpret_cast<float *>(smem4));
