@@ -347,6 +347,22 @@ bf_status bf_forward_unfused(const bf_plan *plan, const float *in, float *out, i
  *                   (needed only when grad_sigma_r is not NULL)
  * The planes are recomputed from f; nothing from the forward pass other than
  * out and q is stored.
+ * Kernels: the fused adjoint tile kernel serves the truncated Gaussian
+ * (R <= 24) and the box with r <= 8.  The box with 8 < r <= 64 runs the same
+ * chain rule term by term through planes in device memory: about
+ * 48 * H * W bytes of the library's scratch (the one bf_forward's
+ * large-radius path uses, shared with it, allocated on first need and kept
+ * until bf_release_scratch(); the first such call on a device must not
+ * happen during stream capture).  That path is bandwidth-bound, not fused.
+ * The recursive Gaussian has no adjoint (BF_EUNSUPPORTED).
+ * Accuracy: dL/df within 1e-3 of the exact gradient (relative to its largest
+ * element).  dL/dsigma_r carries the FP32 expansion's error in the kernel's
+ * sigma_r-derivative weighted by grad_out / Q.  It stays within 1e-3 where Q
+ * is not small, and within 1e-2 on images far smaller than the support
+ * (tested down to 1 x 17 at r = 12).
+ * Errors: BF_EINVAL (pointers, sizes, workspace, grad_sigma_r with a
+ * cosine-polynomial plan), BF_EUNSUPPORTED (no adjoint for the support,
+ * image too large), BF_ENOMEM (scratch), BF_ECUDA (launch failure).
  */
 size_t bf_backward_workspace(const bf_plan *plan, int H, int W);
 bf_status bf_backward(const bf_plan *plan, const float *f, const float *out,
@@ -356,8 +372,9 @@ bf_status bf_backward(const bf_plan *plan, const float *f, const float *out,
 
 /*
  * bf_backward over a contiguous stack of `count` H x W images (layout as in
- * bf_forward_stack) in one launch; grad_sigma_r receives the sum over the
- * stack of dL/dsigma_r (the images share sigma_r).  workspace needs
+ * bf_forward_stack) in one launch (the box with r > 8: the stack's images
+ * share each launch, in chunks of up to 2 GiB of scratch); grad_sigma_r
+ * receives the sum over the stack of dL/dsigma_r (the images share sigma_r).  workspace needs
  * bf_backward_stack_workspace(plan, H, W, count) bytes, 8-byte aligned, when
  * grad_sigma_r is not NULL.
  */
@@ -392,6 +409,8 @@ bf_status bf_backward_stack(const bf_plan *plan, const float *f, const float *ou
  *   before reading it, so nothing has to be cleared between calls, but calls
  *   whose work overlaps on the GPU (other streams, other host threads) race
  *   on the array: serialise them.
+ *   Supports: the fused adjoint's (Gaussian R <= 24, box r <= 8); the box
+ *   with r > 8 needs device scratch and returns BF_EUNSUPPORTED here.
  *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  */
 bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, const float *out,

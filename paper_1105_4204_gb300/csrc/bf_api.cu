@@ -354,6 +354,13 @@ extern "C" bf_status bf_forward_unfused(const bf_plan *plan, const float *in, fl
 
 namespace bf {
 bool bwd_supported(const bf_plan *p);
+bool bwd_large_supported(const bf_plan *p);
+size_t bwd_large_workspace(int H, int W, int count);
+cudaError_t launch_backward_large(const bf_plan *pl, const float *f, const float *o,
+                                  const float *q, const float *u, float *grad,
+                                  double *partials, int H, int W, int count, void *ws,
+                                  cudaStream_t s);
+cudaError_t launch_bwd_reduce(const double *partials, int n, double *out, cudaStream_t s);
 size_t bwd_blocks(int H, int W);
 cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, const float *q,
                             const float *u, float *grad, double *grad_sigma_r, double *partials,
@@ -362,6 +369,27 @@ cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, c
                             const float *u, float *grad, double *grad_sigma_r, double *partials,
                             int H, int W, cudaStream_t s, int count);
 }  // namespace bf
+
+// The adjoint of either path: the fused tile kernel, or for the box with
+// 8 < r <= 64 the per-term planes through the library scratch.
+static bf_status run_backward(const char *who, const bf_plan *plan, const float *f,
+                              const float *out, const float *q, const float *grad_out,
+                              float *grad_in, double *grad_sigma_r, double *partials, int H,
+                              int W, int count, cudaStream_t stream) {
+    if (bwd_supported(plan))
+        return cuda_check(launch_backward(plan, f, out, q, grad_out, grad_in, grad_sigma_r,
+                                          partials, H, W, stream, count),
+                          who);
+    void *ws = nullptr;
+    cudaError_t e = get_scratch(bwd_large_workspace(H, W, count), &ws);
+    if (e != cudaSuccess)
+        return fail(BF_ENOMEM, std::string(who) + ": cannot allocate the large-radius scratch");
+    e = launch_backward_large(plan, f, out, q, grad_out, grad_in,
+                              grad_sigma_r ? partials : nullptr, H, W, count, ws, stream);
+    if (e == cudaSuccess && grad_sigma_r)
+        e = launch_bwd_reduce(partials, (int)(bwd_blocks(H, W) * count), grad_sigma_r, stream);
+    return cuda_check(e, who);
+}
 
 extern "C" size_t bf_backward_workspace(const bf_plan *plan, int H, int W) {
     if (!plan || H < 1 || W < 1) return 0;
@@ -388,9 +416,9 @@ extern "C" bf_status bf_backward_stack(const bf_plan *plan, const float *f, cons
     if (H > BF_MAX_ROWS)
         return fail(BF_EUNSUPPORTED, "bf_backward_stack: image taller than " +
                                          std::to_string(BF_MAX_ROWS) + " rows");
-    if (!bwd_supported(plan))
+    if (!bwd_supported(plan) && !bwd_large_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward_stack: no kernel for this spatial support "
-                                     "(Gaussian R <= 24 or box r <= 8)");
+                                     "(Gaussian R <= 24 or box r <= 64)");
     if (grad_sigma_r && plan->cosine)
         return fail(BF_EINVAL, "bf_backward_stack: a cosine-polynomial plan has no sigma_r; "
                                "pass grad_sigma_r = NULL");
@@ -403,9 +431,9 @@ extern "C" bf_status bf_backward_stack(const bf_plan *plan, const float *f, cons
         if ((uintptr_t)workspace % 8 != 0)
             return fail(BF_EINVAL, "bf_backward_stack: workspace must be 8-byte aligned");
     }
-    return cuda_check(launch_backward(plan, f, out, q, grad_out, grad_in, grad_sigma_r,
-                                      reinterpret_cast<double *>(workspace), H, W, stream, count),
-                      "bf_backward_stack launch");
+    return run_backward("bf_backward_stack launch", plan, f, out, q, grad_out, grad_in,
+                        grad_sigma_r, reinterpret_cast<double *>(workspace), H, W, count,
+                        stream);
 }
 
 extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const float *out,
@@ -421,9 +449,9 @@ extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const floa
     if (H > BF_MAX_ROWS)
         return fail(BF_EUNSUPPORTED, "bf_backward: image taller than " +
                                          std::to_string(BF_MAX_ROWS) + " rows");
-    if (!bwd_supported(plan))
+    if (!bwd_supported(plan) && !bwd_large_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward: no kernel for this spatial support "
-                                     "(Gaussian R <= 24 or box r <= 8)");
+                                     "(Gaussian R <= 24 or box r <= 64)");
     if (grad_sigma_r && plan->cosine)
         return fail(BF_EINVAL, "bf_backward: a cosine-polynomial plan has no sigma_r; "
                                "pass grad_sigma_r = NULL");
@@ -436,9 +464,8 @@ extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const floa
         if ((uintptr_t)workspace % 8 != 0)
             return fail(BF_EINVAL, "bf_backward: workspace must be 8-byte aligned");
     }
-    return cuda_check(launch_backward(plan, f, out, q, grad_out, grad_in, grad_sigma_r,
-                                      reinterpret_cast<double *>(workspace), H, W, stream),
-                      "bf_backward launch");
+    return run_backward("bf_backward launch", plan, f, out, q, grad_out, grad_in,
+                        grad_sigma_r, reinterpret_cast<double *>(workspace), H, W, 1, stream);
 }
 
 // ---- tile-shape autotuner ----------------------------------------------------

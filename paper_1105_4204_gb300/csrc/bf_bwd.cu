@@ -112,6 +112,13 @@ cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, c
     return e;
 }
 
+// The fixed-order reduction of n partials into *out (used by the large-radius
+// adjoint too).
+cudaError_t launch_bwd_reduce(const double *partials, int n, double *out, cudaStream_t s) {
+    bwd_reduce<<<1, 256, 0, s>>>(partials, n, out);
+    return cudaGetLastError();
+}
+
 // Single-image form.
 cudaError_t launch_backward(const bf_plan *pl, const float *f, const float *o, const float *q,
                             const float *u, float *grad, double *grad_sigma_r, double *partials,

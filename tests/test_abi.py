@@ -284,6 +284,29 @@ def test_tall_images_are_refused_on_the_host(bf):
     assert str(65535 * 32).encode() in l.bf_last_error()
 
 
+def test_backward_supports_on_the_host(bf):
+    # the box with 8 < r <= 64 (the largest box a plan takes) has an adjoint
+    # through device scratch, which the no-alloc entry point refuses; the
+    # recursive Gaussian has none.  Refused before any pointer is read.
+    from paper_1105_4204_gb300 import _lib
+    l = _lib.lib()
+    l.bf_backward_noalloc.restype = ctypes.c_int
+    l.bf_backward_noalloc.argtypes = [ctypes.c_void_p] * 7 + [ctypes.c_int, ctypes.c_int,
+                                                              ctypes.c_void_p]
+    fake = ctypes.c_void_p(0x1000)
+    null = ctypes.c_void_p(0)
+    big = bf.Plan(12.0, 20.0, kind="box")
+    assert big.radius // 3 == 12
+    assert l.bf_backward_noalloc(big.handle, fake, fake, fake, fake, fake, null, 64, 64,
+                                 null) == 2
+    assert b"scratch" in l.bf_last_error()
+    with pytest.raises(Exception):  # no plan beyond the largest supported box
+        bf.Plan(65.0, 20.0, kind="box", radius=65)
+    rec = bf.Plan(10.0, 20.0, kind="recursive")
+    assert l.bf_backward(rec.handle, fake, fake, fake, fake, fake, null, 64, 64, null, 0,
+                         null) == 2
+
+
 def test_recursive_gaussian_plan(bf, oracle):
     # radius reports the extension P = ceil(6 sigma_s); achieved sigma is the cascade's
     # (closed form from the coefficients), equal to the oracle's measured impulse response
