@@ -134,6 +134,15 @@ def _load():
         lib.or_bf_brute_sv_at.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, _llp,
                                           ctypes.c_longlong, _dp]
+        lib.or_bf_brute_sv_shape.restype = None
+        lib.or_bf_brute_sv_shape.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_int, _dp, _dp]
+        lib.or_bf_brute_sv_shape_at.restype = None
+        lib.or_bf_brute_sv_shape_at.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _ip,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_int, _llp,
+                                                ctypes.c_longlong, _dp]
         lib.or_phi_table.restype = None
         lib.or_phi_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
                                      ctypes.c_longlong, _dp]
@@ -243,10 +252,12 @@ def bf_brute(f, sigma_s=3.0, sigma_r=30.0, T=255.0, kind="gauss", radius=0, pass
 
 
 def bf_brute_sv(f, radius, sigma_r=30.0, T=255.0, r_max=None, N=None,
-                range_mode="raised_cosine", return_q=False):
-    """Space-variant brute force (Section 4): at each pixel a box of half-width
-    radius[i, j] (clamped into [0, r_max]; r_max defaults to radius.max()),
-    eq. (BF) summed directly over it; single-channel H x W."""
+                range_mode="raised_cosine", return_q=False, spatial="box"):
+    """Space-variant brute force (Section 4): at each pixel a box (or, with
+    spatial="hat", the separable hat, weight (r + 1 - |a|)(r + 1 - |b|) at
+    offset (a, b)) of half-width radius[i, j] (clamped into [0, r_max]; r_max
+    defaults to radius.max()), eq. (BF) summed directly over it; single-channel
+    H x W."""
     lib = _load()
     if N is None:
         N = n_rule(sigma_r, T)
@@ -259,8 +270,15 @@ def bf_brute_sv(f, radius, sigma_r=30.0, T=255.0, r_max=None, N=None,
         r_max = int(rad.max()) if rad.size else 0
     o = np.empty((H, W), dtype=np.float64)
     q = np.empty((H, W), dtype=np.float64)
-    lib.or_bf_brute_sv(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max),
-                       _range_mode(range_mode), float(sigma_r), int(N), _ptr(o), _ptr(q))
+    if spatial == "box":
+        lib.or_bf_brute_sv(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max),
+                           _range_mode(range_mode), float(sigma_r), int(N), _ptr(o), _ptr(q))
+    elif spatial == "hat":
+        lib.or_bf_brute_sv_shape(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max), 1,
+                                 _range_mode(range_mode), float(sigma_r), int(N), _ptr(o),
+                                 _ptr(q))
+    else:
+        raise ValueError("spatial must be 'box' or 'hat'")
     return (o, q) if return_q else o
 
 
@@ -281,7 +299,7 @@ def bf_brute_sv_cos(f, radius, gamma, coefs, r_max=None):
 
 
 def bf_brute_sv_at(f, radius, idx, r_max, sigma_r=30.0, T=255.0, N=None,
-                   range_mode="raised_cosine"):
+                   range_mode="raised_cosine", spatial="box"):
     """bf_brute_sv at flat pixel indices ``idx`` only."""
     lib = _load()
     if N is None:
@@ -291,9 +309,16 @@ def bf_brute_sv_at(f, radius, idx, r_max, sigma_r=30.0, T=255.0, N=None,
     rad = np.ascontiguousarray(np.asarray(radius, dtype=np.int32))
     ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
     o = np.empty(len(ix), dtype=np.float64)
-    lib.or_bf_brute_sv_at(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max),
-                          _range_mode(range_mode), float(sigma_r), int(N),
-                          ix.ctypes.data_as(_llp), len(ix), _ptr(o))
+    if spatial == "box":
+        lib.or_bf_brute_sv_at(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max),
+                              _range_mode(range_mode), float(sigma_r), int(N),
+                              ix.ctypes.data_as(_llp), len(ix), _ptr(o))
+    elif spatial == "hat":
+        lib.or_bf_brute_sv_shape_at(_ptr(x), H, W, rad.ctypes.data_as(_ip), int(r_max), 1,
+                                    _range_mode(range_mode), float(sigma_r), int(N),
+                                    ix.ctypes.data_as(_llp), len(ix), _ptr(o))
+    else:
+        raise ValueError("spatial must be 'box' or 'hat'")
     return o
 
 

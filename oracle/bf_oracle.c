@@ -26,8 +26,8 @@
  *                        Section 3) and Algorithm 1 with it as the averaging
  *                        of step 4;
  *   - or_bf_brute_sv   : the space-variant extension (Section 4): at each
- *                        pixel its own box of half-width r(x), eq. (BF)
- *                        summed directly over it;
+ *                        pixel its own box (or, or_bf_brute_sv_shape, hat)
+ *                        of half-width r(x), eq. (BF) summed directly over it;
  *   - or_bf_*_cos      : the same filter, gradient and differences for a
  *                        general trigonometric range kernel of Section 2.2,
  *                        phi(s) = a_0 + a_1 cos(gamma s) + ... + a_N cos(N gamma s),
@@ -260,28 +260,33 @@ void or_bf_brute(const double *f, int H, int W, const double *w1, int R,
 }
 
 /* Space-variant extension (Section 4): the spatial kernel at pixel (i, j) is
- * the (2 r + 1) x (2 r + 1) box centred there, r = radius[i * W + j] clamped
- * into [0, r_max]; its constant weight cancels in the ratio, so eq. (BF) is
- * summed directly over the box of the clamp-extended image.  q_out (may be
- * NULL) receives the normaliser with unit-mass weights, Q / (2 r + 1)^2. */
-static void or_sv_at(const double *f, int H, int W, const int *radius, int r_max,
+ * centred there with half-width r = radius[i * W + j] clamped into
+ * [0, r_max]: the (2 r + 1) x (2 r + 1) box (hat = 0), or the separable hat
+ * (hat = 1), weight (r + 1 - |a|) (r + 1 - |b|) at offset (a, b).  The
+ * kernel's total weight cancels in the ratio, so eq. (BF) is summed directly
+ * with these weights over the clamp-extended image.  q_out (may be NULL)
+ * receives the normaliser with unit-mass weights. */
+static void or_sv_at(const double *f, int H, int W, const int *radius, int r_max, int hat,
                      const or_range *rg, int i, int j, double *out, double *q_out)
 {
     int r = or_clamp(radius[(size_t)i * W + j], 0, r_max);
     double fx = f[(size_t)i * W + j];
-    double p = 0.0, q = 0.0;
+    double p = 0.0, q = 0.0, mass = 0.0;
     for (int a = -r; a <= r; a++) {
         int zi = or_clamp(i + a, 0, H - 1);
+        double wa = hat ? (double)(r + 1 - abs(a)) : 1.0;
         for (int b = -r; b <= r; b++) {
             int zj = or_clamp(j + b, 0, W - 1);
+            double w = wa * (hat ? (double)(r + 1 - abs(b)) : 1.0);
             double v = f[(size_t)zi * W + zj];
-            double ph = or_phi(rg, v - fx);
+            double ph = w * or_phi(rg, v - fx);
             p += ph * v;
             q += ph;
+            mass += w;
         }
     }
     *out = p / q;
-    if (q_out) *q_out = q / ((2.0 * r + 1.0) * (2.0 * r + 1.0));
+    if (q_out) *q_out = q / mass;
 }
 
 void or_bf_brute_sv(const double *f, int H, int W, const int *radius, int r_max, int mode,
@@ -291,7 +296,19 @@ void or_bf_brute_sv(const double *f, int H, int W, const int *radius, int r_max,
 #pragma omp parallel for schedule(dynamic, 4)
     for (int i = 0; i < H; i++)
         for (int j = 0; j < W; j++)
-            or_sv_at(f, H, W, radius, r_max, &rg, i, j, out + (size_t)i * W + j,
+            or_sv_at(f, H, W, radius, r_max, 0, &rg, i, j, out + (size_t)i * W + j,
+                     q_out ? q_out + (size_t)i * W + j : NULL);
+}
+
+/* The space-variant filter with the hat (hat = 1) or the box (hat = 0). */
+void or_bf_brute_sv_shape(const double *f, int H, int W, const int *radius, int r_max, int hat,
+                          int mode, double sigma_r, int N, double *out, double *q_out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < H; i++)
+        for (int j = 0; j < W; j++)
+            or_sv_at(f, H, W, radius, r_max, hat, &rg, i, j, out + (size_t)i * W + j,
                      q_out ? q_out + (size_t)i * W + j : NULL);
 }
 
@@ -304,7 +321,7 @@ void or_bf_brute_sv_cos(const double *f, int H, int W, const int *radius, int r_
 #pragma omp parallel for schedule(dynamic, 4)
     for (int i = 0; i < H; i++)
         for (int j = 0; j < W; j++)
-            or_sv_at(f, H, W, radius, r_max, &rg, i, j, out + (size_t)i * W + j, NULL);
+            or_sv_at(f, H, W, radius, r_max, 0, &rg, i, j, out + (size_t)i * W + j, NULL);
 }
 
 /* The space-variant filter at a list of flat pixel indices only. */
@@ -315,8 +332,20 @@ void or_bf_brute_sv_at(const double *f, int H, int W, const int *radius, int r_m
     or_range rg = or_make_range(mode, sigma_r, N);
 #pragma omp parallel for schedule(dynamic, 16)
     for (long long t = 0; t < n_idx; t++)
-        or_sv_at(f, H, W, radius, r_max, &rg, (int)(idx[t] / W), (int)(idx[t] % W), out + t,
+        or_sv_at(f, H, W, radius, r_max, 0, &rg, (int)(idx[t] / W), (int)(idx[t] % W), out + t,
                  NULL);
+}
+
+/* The same at a list of flat pixel indices, box (hat = 0) or hat (hat = 1). */
+void or_bf_brute_sv_shape_at(const double *f, int H, int W, const int *radius, int r_max,
+                             int hat, int mode, double sigma_r, int N, const long long *idx,
+                             long long n_idx, double *out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long long t = 0; t < n_idx; t++)
+        or_sv_at(f, H, W, radius, r_max, hat, &rg, (int)(idx[t] / W), (int)(idx[t] % W),
+                 out + t, NULL);
 }
 
 /* Brute-force filter at a list of flat pixel indices only. */

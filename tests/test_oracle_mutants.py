@@ -1,7 +1,7 @@
 """The oracle's pins catch plausible mistakes.  Each case plants one mistake
 in a copy of the oracle's C source (a dropped range factor, a wrong clamp
-bound, a wrong frequency or sign, floor for ceil, an off-by-one box, a flipped
-gradient term, a wrong coefficient of the recursive filter), builds it with gcc on the CPU and checks that at least one of
+bound, a wrong frequency or sign, floor for ceil, an off-by-one box or hat, a
+flipped gradient term, a wrong coefficient of the recursive filter), builds it with gcc on the CPU and checks that at least one of
 the pin checks below fails on it -- while all of them pass on the oracle as
 committed."""
 import importlib.util
@@ -58,6 +58,8 @@ MUTANTS = {
                                            "double b1 = 2.44431 * q"),
     "recursive design digit of the small-sigma branch": (": 3.97156 - 4.14554 * sqrt",
                                                          ": 3.97156 - 4.14545 * sqrt"),
+    "space-variant hat weight off by one": ("double wa = hat ? (double)(r + 1 - abs(a)) : 1.0;",
+                                            "double wa = hat ? (double)(r + 2 - abs(a)) : 1.0;"),
 }
 
 
@@ -116,6 +118,14 @@ def _checks(o):
     sv = o.bf_brute_sv(np.array([[0.0, 100.0, 50.0]]), [[2, 1, 0]], sigma_r=200.0)
     if not np.allclose(sv[0], [gs["sv1d_0"], gs["sv1d_1"], gs["sv1d_2"]], atol=1e-7):
         failed.append("space-variant examples")
+    svh = o.bf_brute_sv(np.array([[0.0, 100.0, 50.0]]), [[2, 1, 0]], sigma_r=200.0,
+                        spatial="hat")
+    svh2 = o.bf_brute_sv(np.array([[0.0, 100.0], [100.0, 0.0]]), [[1, 0], [0, 1]],
+                         sigma_r=200.0, spatial="hat")
+    if not np.allclose(svh[0], [gs["svhat1d_0"], gs["svhat1d_1"], gs["svhat1d_2"]], atol=1e-7) \
+            or not np.allclose(svh2, [[gs["svhat2d_00"], gs["svhat2d_01"]],
+                                      [gs["svhat2d_10"], gs["svhat2d_11"]]], atol=1e-7):
+        failed.append("space-variant hat examples")
     gc = _golden("cosine_kernel_examples.txt")
     outc = o.bf_brute_cos(np.array([[0.0, 100.0], [100.0, 0.0]]), math.pi / 200, [0.5, 0.5],
                           w1=w1)

@@ -549,6 +549,63 @@ def test_space_variant_matches_a_python_loop(oracle):
                                   oracle.bf_brute_sv(f, np.full(f.shape, 3), sigma_r=sr))
 
 
+def test_space_variant_hat_hand_examples(oracle):
+    # Section 4's hat: closed forms worked by hand from eq. (BF) with the hat's
+    # weights (r + 1 - |a|)(r + 1 - |b|)
+    g = _golden_sv()
+    c, c2 = math.cos(0.5), math.cos(0.25)
+    assert g["svhat2d_00"] == pytest.approx(600 * c / (10 + 6 * c), abs=5e-8)
+    assert g["svhat1d_0"] == pytest.approx((1800 * c + 450 * c2) / (54 + 18 * c + 9 * c2),
+                                           abs=5e-8)
+    assert g["svhat1d_1"] == pytest.approx((800 + 200 * c2) / (4 * c + 8 + 4 * c2), abs=5e-8)
+    out = oracle.bf_brute_sv(np.array([[0.0, 100.0], [100.0, 0.0]]), [[1, 0], [0, 1]],
+                             sigma_r=200.0, spatial="hat")
+    np.testing.assert_allclose(out, [[g["svhat2d_00"], g["svhat2d_01"]],
+                                     [g["svhat2d_10"], g["svhat2d_11"]]], atol=1e-7)
+    out1 = oracle.bf_brute_sv(np.array([[0.0, 100.0, 50.0]]), [[2, 1, 0]], sigma_r=200.0,
+                              spatial="hat")
+    np.testing.assert_allclose(out1[0], [g["svhat1d_0"], g["svhat1d_1"], g["svhat1d_2"]],
+                               atol=1e-7)
+
+
+def test_space_variant_hat_constant_radius_is_the_triangle_filter(oracle):
+    # r(x) = r0 everywhere is the plain filter with separable triangle taps
+    # (r0 + 1 - |k|) / (r0 + 1)^2, the 1-D hat
+    f = _small_image(17, 23, seed=18)
+    for r0 in (1, 2, 5):
+        k = np.arange(-r0, r0 + 1)
+        w1 = (r0 + 1 - np.abs(k)) / float((r0 + 1) ** 2)
+        ref = oracle.bf_brute(f, sigma_r=25.0, w1=w1)
+        out = oracle.bf_brute_sv(f, np.full(f.shape, r0), sigma_r=25.0, spatial="hat")
+        np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-10)
+    # r = 0: a one-pixel hat returns the image
+    np.testing.assert_array_equal(
+        oracle.bf_brute_sv(f, np.zeros(f.shape, int), sigma_r=25.0, spatial="hat"), f)
+
+
+def test_space_variant_hat_wide_range_kernel_is_the_hat_mean(oracle):
+    # sigma_r -> infinity: out(x) is the hat-weighted mean of the clamp-extended
+    # image around x, here summed with numpy from the padded image
+    f = _small_image(15, 21, seed=19)
+    rad = np.random.default_rng(14).integers(0, 5, size=f.shape)
+    out = oracle.bf_brute_sv(f, rad, sigma_r=1e9, spatial="hat")
+    R = 4
+    fp = np.pad(f, R, mode="edge")
+    H, W = f.shape
+    ref = np.empty_like(f)
+    for i in range(H):
+        for j in range(W):
+            r = rad[i, j]
+            t = r + 1 - np.abs(np.arange(-r, r + 1))
+            w = np.outer(t, t).astype(np.float64)
+            win = fp[i + R - r:i + R + r + 1, j + R - r:j + R + r + 1]
+            ref[i, j] = (w * win).sum() / w.sum()
+    np.testing.assert_allclose(out, ref, rtol=1e-9)
+    idx = np.array([0, 7, 100, H * W - 1])
+    np.testing.assert_array_equal(
+        oracle.bf_brute_sv_at(f, rad, idx, 4, sigma_r=1e9, spatial="hat"), out.ravel()[idx])
+
+
 def test_space_variant_cosine_kernel_agrees_with_the_power_form(oracle):
     # the raised cosine written as its cosine polynomial gives the power-form
     # space-variant filter; a constant radius gives the one-box cosine filter
