@@ -641,7 +641,8 @@ def measure_configs(bf, torch, dev, stream, acc_jobs):
 
 def measure_space_variant(bf, torch, dev, stream, acc_jobs):
     """Space-variant extension (Section 4) on the 2048^2 workload image: smooth
-    seeded radius maps in [0, 8] and [0, 16] (one box half-width per pixel),
+    seeded radius maps in [0, 8] and [0, 16] (one box half-width per pixel;
+    the hat in [0, 8] too),
     sigma_r = 20 (N = 66); ms, Mpixel/s and the FP32 roofline fraction of the
     algorithmic operations (per pixel and term: phase, f cos, f sin; four
     summed-area tables of two running sums each and a three-operation box sum;
@@ -677,6 +678,27 @@ def measure_space_variant(bf, torch, dev, stream, acc_jobs):
                     "frac": ops / (ms * 1e-3) / peak,
                     "roofline": alu_roofline(ops, ms, _peak_ops(torch, dev),
                                              "29 per pixel and term + 4 per pixel")}
+    # the hat (r(x) in [0, 8]): per pixel and term 3 (phase, f cos, f sin),
+    # four tables of two running sums along each axis (16), four nine-entry
+    # second differences (8 additions and 2 scalings each, 40) and the combine (6)
+    rad = synth.radius_map(H, W, 8, seed=1)
+    rt = torch.from_numpy(rad).to(dev)
+    ms = _time(lambda: bf.forward_space_variant(plan, t, rt, r_max=8, out=o, spatial="hat"),
+               torch, stream, 5)
+    got_hat = o.cpu().numpy().ravel()[idx]
+    ops_hat = (65.0 * plan.n_terms + 4.0) * H * W
+
+    def _hat_acc(oracle):
+        ref = oracle.bf_brute_sv_at(img.astype(np.float64), rad, idx, 8, sigma_r=SIGMA_R,
+                                    T=T_RANGE, N=plan.N, spatial="hat")
+        return {"max_abs_err_vs_oracle": float(np.abs(got_hat - ref).max()),
+                "error_sample": "%d pixels (all borders + 1024 seeded)" % len(idx)}
+
+    acc_jobs.append(("space_variant_hat_2048_r0to8", _hat_acc))
+    res["space_variant_hat_2048_r0to8"] = {
+        "ms": ms, "mpx_s": H * W / (ms * 1e-3) / 1e6, "terms": plan.n_terms,
+        "roofline": alu_roofline(ops_hat, ms, _peak_ops(torch, dev),
+                                 "65 per pixel and term + 4 per pixel")}
     return res
 
 

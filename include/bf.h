@@ -235,6 +235,22 @@ bf_status bf_forward_space_variant(const bf_plan *plan, const void *in, bf_dtype
                                    long long row_stride_elems, cudaStream_t stream);
 
 /*
+ * The same with the hat of Section 4: pixel x weighs the clamp-extended image
+ * at offset (a, b) by (r(x) + 1 - |a|) (r(x) + 1 - |b|), |a|, |b| <= r(x)
+ * (the separable triangle of half-width r(x); its total weight cancels in the
+ * ratio).  O(1) per pixel and term: per axis the hat is the second
+ * difference, step r + 1, of a doubly integrated table, so each own pixel
+ * reads nine entries of each of the four tables.  The tables hold 32-bit
+ * fixed-point values whose every hat sum is exact.  r_max <= 8: with the hat's
+ * weight (r + 1)^4 the fixed-point step of a 32-bit table above that would
+ * let the rounding reach the 0.05 gray-level bar.  Arguments, layout and
+ * errors as bf_forward_space_variant.
+ */
+bf_status bf_forward_space_variant_hat(const bf_plan *plan, const void *in, bf_dtype dt,
+                                       const int *radius, int r_max, float *out, int H, int W,
+                                       long long row_stride_elems, cudaStream_t stream);
+
+/*
  * bf_forward for an image in HOST memory (not in the paper): in stream order,
  * copies host_in into the caller's device buffer dev_in, filters dev_in into
  * the caller's device buffer dev_out as bf_forward does, and copies dev_out

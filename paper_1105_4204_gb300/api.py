@@ -178,11 +178,15 @@ def set_shape(plan: Plan, img: torch.Tensor, shape: str, split: int = 1):
 
 
 def forward_space_variant(plan: Plan, img: torch.Tensor, radius: torch.Tensor, r_max: int = 16,
-                          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """Space-variant filter (Section 4): pixel x averages over its own box of
-    half-width radius[x] (int32 H x W on the device, clamped into [0, r_max]),
-    with the plan's range kernel.  Single channel; r_max <= 16 (smaller reads
-    less halo)."""
+                          out: torch.Tensor | None = None, stream=None,
+                          spatial: str = "box") -> torch.Tensor:
+    """Space-variant filter (Section 4): pixel x averages over its own box
+    (spatial="box", r_max <= 16) or separable hat (spatial="hat", r_max <= 8)
+    of half-width radius[x] (int32 H x W on the device, clamped into
+    [0, r_max]), with the plan's range kernel.  Single channel; a smaller
+    r_max reads less halo."""
+    if spatial not in ("box", "hat"):
+        raise ValueError("spatial must be 'box' or 'hat'")
     dt, H, W, C, rs = _image_args(img)
     if C != 1 or img.dim() != 2:
         raise ValueError("the space-variant filter takes a single-channel H x W image")
@@ -191,10 +195,9 @@ def forward_space_variant(plan: Plan, img: torch.Tensor, radius: torch.Tensor, r
         raise ValueError("radius must be a contiguous int32 H x W tensor on the image's device")
     if out is None:
         out = torch.empty((H, W), dtype=torch.float32, device=img.device)
-    check(lib().bf_forward_space_variant(plan.handle, ctypes.c_void_p(img.data_ptr()), dt,
-                                         ctypes.c_void_p(radius.data_ptr()), int(r_max),
-                                         ctypes.c_void_p(out.data_ptr()), H, W, rs,
-                                         _stream_ptr(stream)))
+    fn = lib().bf_forward_space_variant if spatial == "box" else lib().bf_forward_space_variant_hat
+    check(fn(plan.handle, ctypes.c_void_p(img.data_ptr()), dt, ctypes.c_void_p(radius.data_ptr()),
+             int(r_max), ctypes.c_void_p(out.data_ptr()), H, W, rs, _stream_ptr(stream)))
     return out
 
 

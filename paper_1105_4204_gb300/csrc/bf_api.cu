@@ -193,27 +193,42 @@ extern "C" bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt
     return forward_planes(plan, img, stream, "bf_forward");
 }
 
-extern "C" bf_status bf_forward_space_variant(const bf_plan *plan, const void *in, bf_dtype dt,
-                                              const int *radius, int r_max, float *out, int H,
-                                              int W, long long row_stride_elems,
-                                              cudaStream_t stream) {
-    const char *who = "bf_forward_space_variant";
+static bf_status space_variant(const char *who, const bf_plan *plan, const void *in,
+                               bf_dtype dt, const int *radius, int r_max, int hat, float *out,
+                               int H, int W, long long row_stride_elems, cudaStream_t stream) {
     if (!plan) return fail(BF_EINVAL, std::string(who) + ": plan is NULL");
     if (!in || !out || !radius) return fail(BF_EINVAL, std::string(who) + ": a pointer is NULL");
     if (H < 1 || W < 1) return fail(BF_EINVAL, std::string(who) + ": H and W must be >= 1");
     if (dt != BF_F32 && dt != BF_U8) return fail(BF_EINVAL, std::string(who) + ": unknown dtype");
     if (row_stride_elems < W) return fail(BF_EINVAL, std::string(who) + ": row_stride_elems < W");
-    if (r_max < 0 || r_max > sv_max_radius())
+    if (r_max < 0 || r_max > sv_max_radius(hat))
         return fail(BF_EINVAL, std::string(who) + ": r_max must be in [0, " +
-                                   std::to_string(sv_max_radius()) + "]");
+                                   std::to_string(sv_max_radius(hat)) + "]");
     if ((long long)H * W > (1LL << 31) / 4)
         return fail(BF_EUNSUPPORTED, std::string(who) + ": image too large");
     if (H > BF_MAX_ROWS)
         return fail(BF_EUNSUPPORTED, std::string(who) + ": image taller than " +
                                          std::to_string(BF_MAX_ROWS) + " rows");
     return cuda_check(launch_space_variant(plan, in, (int)dt, row_stride_elems, radius, r_max,
-                                           out, H, W, stream),
+                                           hat, out, H, W, stream),
                       who);
+}
+
+extern "C" bf_status bf_forward_space_variant(const bf_plan *plan, const void *in, bf_dtype dt,
+                                              const int *radius, int r_max, float *out, int H,
+                                              int W, long long row_stride_elems,
+                                              cudaStream_t stream) {
+    return space_variant("bf_forward_space_variant", plan, in, dt, radius, r_max, 0, out, H, W,
+                         row_stride_elems, stream);
+}
+
+extern "C" bf_status bf_forward_space_variant_hat(const bf_plan *plan, const void *in,
+                                                  bf_dtype dt, const int *radius, int r_max,
+                                                  float *out, int H, int W,
+                                                  long long row_stride_elems,
+                                                  cudaStream_t stream) {
+    return space_variant("bf_forward_space_variant_hat", plan, in, dt, radius, r_max, 1, out, H,
+                         W, row_stride_elems, stream);
 }
 
 extern "C" bf_status bf_forward_host(const bf_plan *plan, const void *host_in, bf_dtype dt,

@@ -79,10 +79,15 @@ constexpr int sv_table_stride(int n, int rem) {
     return n;
 }
 
-template <int RM, int T, int NTHR>
+template <int RM, int T, int NTHR, bool HAT>
 struct SvGeom {
     static constexpr int E = T + 2 * RM;  // extended tile edge
-    static constexpr int ES = E + 1;      // table edge (a zero row and column first)
+    // Table entries per axis: the box's summed-area table has a zero row and
+    // column first (E + 1); the hat's doubly integrated table two, and one
+    // entry past the tile (E + 2).
+    static constexpr int DT = E + (HAT ? 2 : 1);
+    static constexpr int Z = HAT ? 2 : 1;  // leading zero rows and columns
+    static constexpr int ES = DT | 1;      // table row stride: odd
     static constexpr int FS = E + 1;      // f~ tile row stride: odd, so that a thread
                                           // per row reads without bank conflicts
     // Table lines (a row in step 1, a column in step 2) go to threads in
@@ -91,8 +96,11 @@ struct SvGeom {
     // broadcast read of f~) and tables RMD banks apart.
     static constexpr int F = E / 32 * 32;  // lines per plane in whole warps
     static constexpr int RMD = E - F;      // remaining lines per plane
-    static constexpr int TS = sv_table_stride(ES * ES, RMD);  // entries per table
-    static constexpr int NBOX = (2 * RM + 1) * (2 * RM + 1);  // largest box
+    static constexpr int TS = sv_table_stride(DT * ES, RMD);  // entries per table
+    // the largest total weight of a pixel's kernel: (2 RM + 1)^2 boxes, or
+    // (RM + 1)^4 for the hat of half-width RM
+    static constexpr int NBOX = HAT ? (RM + 1) * (RM + 1) * (RM + 1) * (RM + 1)
+                                    : (2 * RM + 1) * (2 * RM + 1);
     static constexpr int KQ = sv_plain_exponent(NBOX);
     static constexpr int OWN = T * T / NTHR;  // own pixels per thread
     static constexpr size_t SMEM = sizeof(unsigned) * 4 * TS + sizeof(float) * E * FS;
@@ -104,10 +112,10 @@ struct SvGeom {
 // 2^k for -126 <= k <= 127, exactly.
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 
-template <int RM, int T, int NTHR>
+template <int RM, int T, int NTHR, bool HAT>
 __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvParams p) {
-    using G = SvGeom<RM, T, NTHR>;
-    constexpr int E = G::E, ES = G::ES, FS = G::FS, TS = G::TS, OWN = G::OWN;
+    using G = SvGeom<RM, T, NTHR, HAT>;
+    constexpr int E = G::E, ES = G::ES, FS = G::FS, TS = G::TS, OWN = G::OWN, Z = G::Z;
     constexpr int NW = NTHR / 32;
     extern __shared__ unsigned sv_smem[];
     // tables 0 cos, 1 sin, 2 f~ cos, 3 f~ sin, then the E x E f~ tile
@@ -132,12 +140,14 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
         mn = fminf(mn, v);
         mx = fmaxf(mx, v);
     }
-    for (int k = tid; k < ES; k += NTHR) {  // the zero row and column of every table
+    for (int k = tid; k < G::DT; k += NTHR) {  // the leading zero rows and columns
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            Tb[t * TS + k] = 0u;
-            Tb[t * TS + k * ES] = 0u;
-        }
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int z = 0; z < Z; ++z) {
+                Tb[t * TS + z * ES + k] = 0u;
+                Tb[t * TS + k * ES + z] = 0u;
+            }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -211,28 +221,61 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
         // 1. one plane row: fixed point, running sum along the row
         if (line) {
             const float *frow = Fs + l * FS;
-            unsigned *row = Tb + q * TS + (l + 1) * ES + 1;
-            unsigned run = 0u;
-#pragma unroll 8
-            for (int j = 0; j < E; ++j) {
+            auto value = [&](int j) {  // entry j of the row, biased fixed point
                 const float fv = frow[j];
                 float rr = __fmaf_rn(tm, fv, -quarter);
                 rr = rr - rintf(rr);
                 const float v = __cosf(kTwoPi * rr);
                 const float s = weighted ? fv * sP : sQ;
-                run += __float_as_uint(__fmaf_rn(v, s, kSvMagic));
-                row[j] = run;
+                return __float_as_uint(__fmaf_rn(v, s, kSvMagic));
+            };
+            if constexpr (!HAT) {
+                unsigned *row = Tb + q * TS + (l + 1) * ES + 1;
+                unsigned run = 0u;
+#pragma unroll 8
+                for (int j = 0; j < E; ++j) {
+                    run += value(j);
+                    row[j] = run;
+                }
+            } else {
+                // P2[t] = sum_{s < t} P1[s], P1[s] = sum_{j < s} v[j], t = 0 .. E + 1
+                unsigned *row = Tb + q * TS + (l + 2) * ES;
+                unsigned p1 = 0u, p2 = 0u;
+#pragma unroll 8
+                for (int j = 0; j < E; ++j) {
+                    row[j] = p2;
+                    p2 += p1;
+                    p1 += value(j);
+                }
+                row[E] = p2;
+                row[E + 1] = p2 + p1;
             }
         }
         __syncthreads();
         // 2. the columns: summed-area tables
         if (line) {
-            unsigned *col = Tb + q * TS + ES + l + 1;
-            unsigned run = 0u;
+            if constexpr (!HAT) {
+                unsigned *col = Tb + q * TS + ES + l + 1;
+                unsigned run = 0u;
 #pragma unroll 8
-            for (int i = 0; i < E; ++i) {
-                run += col[i * ES];
-                col[i * ES] = run;
+                for (int i = 0; i < E; ++i) {
+                    run += col[i * ES];
+                    col[i * ES] = run;
+                }
+            } else {
+                // the same double integration down column l + 2, in place:
+                // input row i sits at table row i + 2, output row t goes to row t
+                unsigned *col = Tb + q * TS + l + 2;
+                unsigned p1 = 0u, p2 = 0u;
+#pragma unroll 8
+                for (int i = 0; i < E; ++i) {
+                    const unsigned in = col[(i + 2) * ES];
+                    col[i * ES] = p2;
+                    p2 += p1;
+                    p1 += in;
+                }
+                col[E * ES] = p2;
+                col[(E + 1) * ES] = p2 + p1;
             }
         }
         __syncthreads();
@@ -247,15 +290,34 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
             rs = rs - rintf(rs);
             const float cx = __cosf(kTwoPi * rc), sx = __cosf(kTwoPi * rs);
             const int r = rad[k];
-            const int a0 = (RM + pi - r) * ES, a1 = (RM + pi + r + 1) * ES;
-            const int b0 = RM + pj - r, b1 = RM + pj + r + 1;
-            const unsigned bias = (unsigned)((2 * r + 1) * (2 * r + 1)) * kSvMagicBits;
             float S[4];
+            if constexpr (!HAT) {
+                const int a0 = (RM + pi - r) * ES, a1 = (RM + pi + r + 1) * ES;
+                const int b0 = RM + pj - r, b1 = RM + pj + r + 1;
+                const unsigned bias = (unsigned)((2 * r + 1) * (2 * r + 1)) * kSvMagicBits;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const unsigned *Tt = Tb + t * TS;
-                const unsigned s = Tt[a1 + b1] - Tt[a0 + b1] - Tt[a1 + b0] + Tt[a0 + b0] - bias;
-                S[t] = __int2float_rn((int)s);
+                for (int t = 0; t < 4; ++t) {
+                    const unsigned *Tt = Tb + t * TS;
+                    const unsigned s =
+                        Tt[a1 + b1] - Tt[a0 + b1] - Tt[a1 + b0] + Tt[a0 + b0] - bias;
+                    S[t] = __int2float_rn((int)s);
+                }
+            } else {
+                // per axis, the hat of half-width r centred at c is the second
+                // difference, step r + 1, of the doubly integrated table at c + 1
+                const int ym = (RM + pi - r) * ES, yc = (RM + pi + 1) * ES;
+                const int yp = (RM + pi + r + 2) * ES;
+                const int xm = RM + pj - r, xc = RM + pj + 1, xp = RM + pj + r + 2;
+                const unsigned m2 = (unsigned)((r + 1) * (r + 1));
+                const unsigned bias = m2 * m2 * kSvMagicBits;  // the weights' sum, (r + 1)^4
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const unsigned *Tt = Tb + t * TS;
+                    const unsigned corners = Tt[ym + xm] + Tt[ym + xp] + Tt[yp + xm] + Tt[yp + xp];
+                    const unsigned edges = Tt[ym + xc] + Tt[yc + xm] + Tt[yc + xp] + Tt[yp + xc];
+                    const unsigned s = corners - 2u * edges + 4u * Tt[yc + xc] - bias;
+                    S[t] = __int2float_rn((int)s);
+                }
             }
             Q[k] = __fmaf_rn(am, __fmaf_rn(cx, S[0], sx * S[1]), Q[k]);
             P[k] = __fmaf_rn(am, __fmaf_rn(cx, S[2], sx * S[3]), P[k]);
@@ -272,31 +334,31 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
     }
 }
 
-template <int RM, int T, int NTHR>
+template <int RM, int T, int NTHR, bool HAT>
 cudaError_t launch_sv(const SvParams &prm, cudaStream_t s) {
-    using G = SvGeom<RM, T, NTHR>;
+    using G = SvGeom<RM, T, NTHR, HAT>;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(bf_sv_fwd<RM, T, NTHR>,
+        e = cudaFuncSetAttribute(bf_sv_fwd<RM, T, NTHR, HAT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     dim3 grid((prm.W + T - 1) / T, (prm.H + T - 1) / T);
-    bf_sv_fwd<RM, T, NTHR><<<grid, NTHR, G::SMEM, s>>>(prm);
+    bf_sv_fwd<RM, T, NTHR, HAT><<<grid, NTHR, G::SMEM, s>>>(prm);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int sv_max_radius() { return 16; }
+int sv_max_radius(int hat) { return hat ? 8 : 16; }
 
 cudaError_t launch_space_variant(const bf_plan *pl, const void *in, int dtype,
-                                 long long row_stride, const int *radius, int r_max, float *out,
-                                 int H, int W, cudaStream_t s) {
+                                 long long row_stride, const int *radius, int r_max, int hat,
+                                 float *out, int H, int W, cudaStream_t s) {
     SvParams prm;
     prm.in = in;
     prm.in_stride = row_stride;
@@ -307,9 +369,14 @@ cudaError_t launch_space_variant(const bf_plan *pl, const void *in, int dtype,
     prm.H = H;
     prm.W = W;
     fill_terms(pl, &prm.terms);
-    if (r_max <= 4) return launch_sv<4, 32, 256>(prm, s);
-    if (r_max <= 8) return launch_sv<8, 32, 256>(prm, s);
-    return launch_sv<16, 64, 512>(prm, s);
+    if (hat) {
+        if (r_max <= 4) return launch_sv<4, 32, 256, true>(prm, s);
+        if (r_max <= 8) return launch_sv<8, 32, 256, true>(prm, s);
+        return cudaErrorInvalidValue;
+    }
+    if (r_max <= 4) return launch_sv<4, 32, 256, false>(prm, s);
+    if (r_max <= 8) return launch_sv<8, 32, 256, false>(prm, s);
+    return launch_sv<16, 64, 512, false>(prm, s);
 }
 
 }  // namespace bf

@@ -1,8 +1,8 @@
 """GPU parity of the space-variant extension (Section 4: each pixel averages
-over its own box) against the FP64 oracle, element by element, within 0.05
-gray levels; ragged sizes, every table size (r_max up to 4, 8, 16), the
-degenerate radius 0, clamped radii, u8 input, and a full-size image on
-sampled pixels."""
+over its own box or hat) against the FP64 oracle, element by element, within
+0.05 gray levels; ragged sizes, every table size (r_max up to 4, 8, 16 for the
+box, 4 and 8 for the hat), the degenerate radius 0, clamped radii, u8 input,
+and a full-size image on sampled pixels."""
 import numpy as np
 import pytest
 
@@ -24,11 +24,11 @@ def bf():
     return pkg
 
 
-def _sv(bf, img, rad, plan, r_max):
+def _sv(bf, img, rad, plan, r_max, spatial="box"):
     import torch
     t = torch.from_numpy(np.ascontiguousarray(img)).cuda()
     rt = torch.from_numpy(np.ascontiguousarray(rad, dtype=np.int32)).cuda()
-    out = bf.forward_space_variant(plan, t, rt, r_max=r_max)
+    out = bf.forward_space_variant(plan, t, rt, r_max=r_max, spatial=spatial)
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
@@ -119,3 +119,67 @@ def test_general_cosine_kernel(bf, oracle, coefs):
     out = _sv(bf, img, rad, plan, 12)
     ref = oracle.bf_brute_sv_cos(img, rad, gamma, coefs, r_max=12)
     assert np.abs(out - ref).max() <= TOL
+
+
+# ------------------------------------------------------------------ the hat
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 17), (5, 3), (37, 53), (70, 131), (97, 64)])
+@pytest.mark.parametrize("r_max", [0, 3, 6, 8])
+def test_hat_random_radius_maps(bf, oracle, H, W, r_max):
+    img = synth.rectangles(H, W, n_rect=5, noise=10.0, seed=H * 100 + W + 1)
+    rad = synth.radius_map(H, W, r_max, seed=r_max + 20, smooth=False)
+    plan = bf.Plan(3.0, 25.0, kind="box")
+    out = _sv(bf, img, rad, plan, r_max, spatial="hat")
+    ref = oracle.bf_brute_sv(img, rad, sigma_r=25.0, r_max=r_max, N=plan.N, spatial="hat")
+    err = np.abs(out - ref).max()
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("sigma_r,N", [(10.0, 264), (60.0, 8)])
+def test_hat_degrees_and_constant_radius(bf, oracle, sigma_r, N):
+    img = synth.smooth_field(75, 88, noise=5.0, seed=int(sigma_r) + 3)
+    plan = bf.Plan(2.0, sigma_r, kind="gauss")
+    assert plan.N == N
+    rad = synth.radius_map(75, 88, 8, seed=5)
+    out = _sv(bf, img, rad, plan, 8, spatial="hat")
+    ref = oracle.bf_brute_sv(img, rad, sigma_r=sigma_r, r_max=8, N=N, spatial="hat")
+    assert np.abs(out - ref).max() <= TOL
+    # a constant half-width is the plain filter with separable triangle taps
+    for r0 in (1, 8):
+        k = np.arange(-r0, r0 + 1)
+        w1 = (r0 + 1 - np.abs(k)) / float((r0 + 1) ** 2)
+        out = _sv(bf, img, np.full(img.shape, r0, np.int32), plan, 8, spatial="hat")
+        ref = oracle.bf_brute(img, sigma_r=sigma_r, w1=w1, N=N)
+        assert np.abs(out - ref).max() <= TOL
+
+
+def test_hat_radius_zero_u8_and_clamping(bf):
+    img = synth.rectangles(40, 70, noise=10.0, seed=3)
+    plan = bf.Plan(3.0, 30.0)
+    out = _sv(bf, img, np.zeros(img.shape, np.int32), plan, 0, spatial="hat")
+    np.testing.assert_allclose(out, img, rtol=0, atol=1e-4)
+    rng = np.random.default_rng(9)
+    u8 = rng.integers(0, 256, size=(61, 77)).astype(np.uint8)
+    rad = synth.radius_map(61, 77, 6, seed=10, smooth=False)
+    a = _sv(bf, u8, rad, plan, 6, spatial="hat")
+    np.testing.assert_array_equal(a, _sv(bf, u8.astype(np.float32), rad, plan, 6, spatial="hat"))
+    wild = rad.copy()
+    wild[::2] += 30
+    np.testing.assert_array_equal(_sv(bf, u8, wild, plan, 6, spatial="hat"),
+                                  _sv(bf, u8, np.clip(wild, 0, 6), plan, 6, spatial="hat"))
+    with pytest.raises(Exception):
+        _sv(bf, u8, rad, plan, 9, spatial="hat")  # the hat takes r_max <= 8
+
+
+def test_hat_full_size_sampled(bf, oracle):
+    H = W = 2048
+    img = synth.smooth_field(H, W, noise=5.0, seed=0)
+    rad = synth.radius_map(H, W, 8, seed=1)
+    plan = bf.Plan(2.0, 20.0, kind="box")
+    out = _sv(bf, img, rad, plan, 8, spatial="hat")
+    np.testing.assert_array_equal(out, _sv(bf, img, rad, plan, 8, spatial="hat"))
+    idx = synth.sample_indices(H, W, 2048, seed=6)
+    ref = oracle.bf_brute_sv_at(img, rad, idx, 8, sigma_r=20.0, N=plan.N, spatial="hat")
+    err = np.abs(out.ravel()[idx] - ref).max()
+    print("space-variant hat 2048^2 max abs err %.3e over %d px" % (err, len(idx)))
+    assert err <= TOL
