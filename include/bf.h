@@ -251,6 +251,23 @@ bf_status bf_forward_space_variant_hat(const bf_plan *plan, const void *in, bf_d
                                        long long row_stride_elems, cudaStream_t stream);
 
 /*
+ * Both of the above for C interleaved channels (H x W x C, as bf_forward),
+ * each filtered with the same radius map:
+ *   spatial          : 0 the box (r_max <= 16), 1 the hat (r_max <= 8)
+ *   in               : device image, type dt, rows row_stride_elems (>= W C)
+ *                      elements apart, channel c of pixel (y, x) at
+ *                      y row_stride_elems + x C + c
+ *   out              : device float H x W x C, interleaved
+ *   C                : 1 .. 4
+ * bf_forward_space_variant(_hat) is this with C = 1.  Errors as
+ * bf_forward_space_variant, plus BF_EINVAL for C or spatial out of range.
+ */
+bf_status bf_forward_space_variant_ex(const bf_plan *plan, const void *in, bf_dtype dt,
+                                      const int *radius, int r_max, int spatial, float *out,
+                                      int H, int W, int C, long long row_stride_elems,
+                                      cudaStream_t stream);
+
+/*
  * bf_forward for an image in HOST memory (not in the paper): in stream order,
  * copies host_in into the caller's device buffer dev_in, filters dev_in into
  * the caller's device buffer dev_out as bf_forward does, and copies dev_out

@@ -84,6 +84,9 @@ def _declare(lib):
         "bf_forward_space_variant_hat": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int,
                                                  c_void_p, c_int, c_int, ctypes.c_longlong,
                                                  c_void_p]),
+        "bf_forward_space_variant_ex": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
+                                                c_void_p, c_int, c_int, c_int, ctypes.c_longlong,
+                                                c_void_p]),
         "bf_forward_host": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int,
                                     c_int, c_int, ctypes.c_longlong, c_void_p]),
         "bf_fp32_pipe_rate": (c_int, [c_int, ctypes.POINTER(ctypes.c_double), c_void_p]),

@@ -183,21 +183,22 @@ def forward_space_variant(plan: Plan, img: torch.Tensor, radius: torch.Tensor, r
     """Space-variant filter (Section 4): pixel x averages over its own box
     (spatial="box", r_max <= 16) or separable hat (spatial="hat", r_max <= 8)
     of half-width radius[x] (int32 H x W on the device, clamped into
-    [0, r_max]), with the plan's range kernel.  Single channel; a smaller
-    r_max reads less halo."""
+    [0, r_max]), with the plan's range kernel.  H x W, or H x W x C with
+    interleaved channels (C <= 4, each filtered with the same radius map); a
+    smaller r_max reads less halo."""
     if spatial not in ("box", "hat"):
         raise ValueError("spatial must be 'box' or 'hat'")
     dt, H, W, C, rs = _image_args(img)
-    if C != 1 or img.dim() != 2:
-        raise ValueError("the space-variant filter takes a single-channel H x W image")
     if radius.dtype != torch.int32 or tuple(radius.shape) != (H, W) or not radius.is_contiguous() \
             or radius.device != img.device:
         raise ValueError("radius must be a contiguous int32 H x W tensor on the image's device")
     if out is None:
-        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
-    fn = lib().bf_forward_space_variant if spatial == "box" else lib().bf_forward_space_variant_hat
-    check(fn(plan.handle, ctypes.c_void_p(img.data_ptr()), dt, ctypes.c_void_p(radius.data_ptr()),
-             int(r_max), ctypes.c_void_p(out.data_ptr()), H, W, rs, _stream_ptr(stream)))
+        out = torch.empty(tuple(img.shape), dtype=torch.float32, device=img.device)
+    check(lib().bf_forward_space_variant_ex(plan.handle, ctypes.c_void_p(img.data_ptr()), dt,
+                                            ctypes.c_void_p(radius.data_ptr()), int(r_max),
+                                            0 if spatial == "box" else 1,
+                                            ctypes.c_void_p(out.data_ptr()), H, W, C, rs,
+                                            _stream_ptr(stream)))
     return out
 
 

@@ -195,22 +195,26 @@ extern "C" bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt
 
 static bf_status space_variant(const char *who, const bf_plan *plan, const void *in,
                                bf_dtype dt, const int *radius, int r_max, int hat, float *out,
-                               int H, int W, long long row_stride_elems, cudaStream_t stream) {
+                               int H, int W, int C, long long row_stride_elems,
+                               cudaStream_t stream) {
     if (!plan) return fail(BF_EINVAL, std::string(who) + ": plan is NULL");
     if (!in || !out || !radius) return fail(BF_EINVAL, std::string(who) + ": a pointer is NULL");
     if (H < 1 || W < 1) return fail(BF_EINVAL, std::string(who) + ": H and W must be >= 1");
+    if (C < 1 || C > 4) return fail(BF_EINVAL, std::string(who) + ": C must be 1 .. 4");
+    if (hat != 0 && hat != 1) return fail(BF_EINVAL, std::string(who) + ": spatial must be 0 or 1");
     if (dt != BF_F32 && dt != BF_U8) return fail(BF_EINVAL, std::string(who) + ": unknown dtype");
-    if (row_stride_elems < W) return fail(BF_EINVAL, std::string(who) + ": row_stride_elems < W");
+    if (row_stride_elems < (long long)W * C)
+        return fail(BF_EINVAL, std::string(who) + ": row_stride_elems < W * C");
     if (r_max < 0 || r_max > sv_max_radius(hat))
         return fail(BF_EINVAL, std::string(who) + ": r_max must be in [0, " +
                                    std::to_string(sv_max_radius(hat)) + "]");
-    if ((long long)H * W > (1LL << 31) / 4)
+    if ((long long)H * W * C > (1LL << 31) / 4)
         return fail(BF_EUNSUPPORTED, std::string(who) + ": image too large");
     if (H > BF_MAX_ROWS)
         return fail(BF_EUNSUPPORTED, std::string(who) + ": image taller than " +
                                          std::to_string(BF_MAX_ROWS) + " rows");
     return cuda_check(launch_space_variant(plan, in, (int)dt, row_stride_elems, radius, r_max,
-                                           hat, out, H, W, stream),
+                                           hat, out, H, W, C, stream),
                       who);
 }
 
@@ -219,7 +223,7 @@ extern "C" bf_status bf_forward_space_variant(const bf_plan *plan, const void *i
                                               int W, long long row_stride_elems,
                                               cudaStream_t stream) {
     return space_variant("bf_forward_space_variant", plan, in, dt, radius, r_max, 0, out, H, W,
-                         row_stride_elems, stream);
+                         1, row_stride_elems, stream);
 }
 
 extern "C" bf_status bf_forward_space_variant_hat(const bf_plan *plan, const void *in,
@@ -228,7 +232,16 @@ extern "C" bf_status bf_forward_space_variant_hat(const bf_plan *plan, const voi
                                                   long long row_stride_elems,
                                                   cudaStream_t stream) {
     return space_variant("bf_forward_space_variant_hat", plan, in, dt, radius, r_max, 1, out, H,
-                         W, row_stride_elems, stream);
+                         W, 1, row_stride_elems, stream);
+}
+
+extern "C" bf_status bf_forward_space_variant_ex(const bf_plan *plan, const void *in,
+                                                 bf_dtype dt, const int *radius, int r_max,
+                                                 int spatial, float *out, int H, int W, int C,
+                                                 long long row_stride_elems,
+                                                 cudaStream_t stream) {
+    return space_variant("bf_forward_space_variant_ex", plan, in, dt, radius, r_max, spatial, out,
+                         H, W, C, row_stride_elems, stream);
 }
 
 extern "C" bf_status bf_forward_host(const bf_plan *plan, const void *host_in, bf_dtype dt,

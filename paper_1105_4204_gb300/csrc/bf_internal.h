@@ -96,11 +96,11 @@ size_t recursive_workspace(const bf_plan *p, int H, int W);
 cudaError_t launch_recursive(const bf_plan *p, const BfImage &img, void *ws, cudaStream_t s);
 
 // Space-variant extension (one half-width per pixel, 0 <= r <= r_max <=
-// sv_max_radius(hat)), single channel; the box (hat = 0) or the separable
-// hat (hat = 1).
+// sv_max_radius(hat)), C interleaved channels; the box (hat = 0) or the
+// separable hat (hat = 1).
 int sv_max_radius(int hat);
 cudaError_t launch_space_variant(const bf_plan *pl, const void *in, int dtype,
                                  long long row_stride, const int *radius, int r_max, int hat,
-                                 float *out, int H, int W, cudaStream_t s);
+                                 float *out, int H, int W, int C, cudaStream_t s);
 
 }  // namespace bf

@@ -38,6 +38,8 @@
 // mantissa bits.  The tables keep those bit patterns as they are; their
 // constant part, 1.5 * 2^23's bit pattern per entry, is taken out of each box
 // sum as (box area) x that pattern.
+// Interleaved channels (H x W x C) are filtered independently with the same
+// radius map, one grid z-slice per channel.
 // HBM sees f and the radius map read once and out written once.
 #include <cstdint>
 
@@ -55,6 +57,7 @@ constexpr int kSvMaxQ = 21;                 // |round(v 2^k)| <= 2^21 < 2^22
 struct SvParams {
     const void *in;
     long long in_stride;  // elements between rows
+    int C;                // interleaved channels (blockIdx.z), in and out
     int dtype;            // 0 f32, 1 u8
     const int *radius;    // H x W, row-major
     int r_max;
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
         const int i = idx / E, j = idx - (idx / E) * E;
         const int gy = min(max(y0 - RM + i, 0), H - 1);
         const int gx = min(max(x0 - RM + j, 0), W - 1);
-        const long long off = (long long)gy * p.in_stride + gx;
+        const long long off = (long long)gy * p.in_stride + (long long)gx * p.C + blockIdx.z;
         const float v = p.dtype == 0 ? __ldg(reinterpret_cast<const float *>(p.in) + off)
                                      : (float)__ldg(reinterpret_cast<const uint8_t *>(p.in) + off);
         Fs[i * FS + j] = v;
@@ -330,7 +333,8 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
     for (int k = 0; k < OWN; ++k) {
         const int pi = tid / T + k * (NTHR / T), pj = tid % T;
         const int gy = y0 + pi, gx = x0 + pj;
-        if (gy < H && gx < W) p.out[(long long)gy * W + gx] = c + P[k] / Q[k] * back;
+        if (gy < H && gx < W)
+            p.out[((long long)gy * W + gx) * p.C + blockIdx.z] = c + P[k] / Q[k] * back;
     }
 }
 
@@ -347,7 +351,7 @@ cudaError_t launch_sv(const SvParams &prm, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    dim3 grid((prm.W + T - 1) / T, (prm.H + T - 1) / T);
+    dim3 grid((prm.W + T - 1) / T, (prm.H + T - 1) / T, prm.C);
     bf_sv_fwd<RM, T, NTHR, HAT><<<grid, NTHR, G::SMEM, s>>>(prm);
     return cudaGetLastError();
 }
@@ -358,10 +362,11 @@ int sv_max_radius(int hat) { return hat ? 8 : 16; }
 
 cudaError_t launch_space_variant(const bf_plan *pl, const void *in, int dtype,
                                  long long row_stride, const int *radius, int r_max, int hat,
-                                 float *out, int H, int W, cudaStream_t s) {
+                                 float *out, int H, int W, int C, cudaStream_t s) {
     SvParams prm;
     prm.in = in;
     prm.in_stride = row_stride;
+    prm.C = C;
     prm.dtype = dtype;
     prm.radius = radius;
     prm.r_max = r_max;

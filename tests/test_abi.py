@@ -360,6 +360,15 @@ def test_space_variant_rejects_bad_arguments_without_touching_a_gpu(bf):
     assert l.bf_forward_space_variant(p.handle, fake, 0, fake, 4, fake, 16, 16, 8, null) == 1
     assert l.bf_forward_space_variant(p.handle, fake, 0, fake, 4, fake, 16384, 32769, 32769,
                                       null) == 2
+    # channels 1 .. 4 with rows of at least W C elements; spatial 0 or 1
+    l.bf_forward_space_variant_ex.restype = ctypes.c_int
+    assert l.bf_forward_space_variant_ex(p.handle, fake, 0, fake, 4, 0, fake, 16, 16, 5, 80,
+                                         null) == 1
+    assert l.bf_forward_space_variant_ex(p.handle, fake, 0, fake, 4, 0, fake, 16, 16, 3, 47,
+                                         null) == 1
+    assert b"W * C" in l.bf_last_error()
+    assert l.bf_forward_space_variant_ex(p.handle, fake, 0, fake, 4, 2, fake, 16, 16, 1, 16,
+                                         null) == 1
     # the hat takes half-widths up to 8
     assert l.bf_forward_space_variant_hat(p.handle, fake, 0, fake, 9, fake, 16, 16, 16, null) == 1
     assert b"[0, 8]" in l.bf_last_error()

@@ -183,3 +183,23 @@ def test_hat_full_size_sampled(bf, oracle):
     err = np.abs(out.ravel()[idx] - ref).max()
     print("space-variant hat 2048^2 max abs err %.3e over %d px" % (err, len(idx)))
     assert err <= TOL
+
+
+@pytest.mark.parametrize("spatial,r_max", [("box", 8), ("box", 16), ("hat", 8)])
+def test_interleaved_channels(bf, oracle, spatial, r_max):
+    # H x W x 3 u8, every channel with the same radius map: each channel as
+    # the single-channel call (bit for bit) and as the oracle
+    import torch
+    img = synth.rect_disk_u8(45, 70, C=3, n_shapes=8, seed=4)
+    rad = synth.radius_map(45, 70, r_max, seed=7, smooth=False)
+    plan = bf.Plan(2.0, 30.0, kind="box")
+    t = torch.from_numpy(img).cuda()
+    rt = torch.from_numpy(rad).cuda()
+    out = bf.forward_space_variant(plan, t, rt, r_max=r_max, spatial=spatial).cpu().numpy()
+    assert out.shape == img.shape
+    for c in range(3):
+        single = _sv(bf, np.ascontiguousarray(img[..., c]), rad, plan, r_max, spatial=spatial)
+        np.testing.assert_array_equal(out[..., c], single)
+        ref = oracle.bf_brute_sv(img[..., c].astype(np.float64), rad, sigma_r=30.0, r_max=r_max,
+                                 N=plan.N, spatial=spatial)
+        assert np.abs(out[..., c] - ref).max() <= TOL
