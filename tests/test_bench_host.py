@@ -40,6 +40,9 @@ def test_reference_arm_line():
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    # ms_per_step is the timed step's own (sampled) time; the full step's is extrapolated
+    assert 0 < line["px_per_step"] < 3 * 2048 * 2048
+    assert 0 < line["ms_per_step"] <= line["ms_per_full_step_extrapolated"]
 
 
 def test_traffic_is_tied_to_the_kernel_sources(monkeypatch):
