@@ -124,6 +124,8 @@ __global__ void __launch_bounds__(kLbCols) lb_vpass(const __grid_constant__ LbPa
     const int xc = min(x, W - 1);
     const int n_in = kLbRowsV + 2 * halo;
     float *a = lb_sm + threadIdx.x;
+    // unrolled so that eight independent loads are in flight before their stores
+#pragma unroll 8
     for (int i = 0; i < n_in; ++i) {
         const int gy = y0 - halo + i;
         float v;
@@ -181,19 +183,22 @@ __global__ void __launch_bounds__(kLbRowsH) lb_hpass(const __grid_constant__ LbP
     float *d_out = dst + (img * kLbPlanes + q) * n;
     const int n_in = kLbColsH + 2 * halo;
     const int stride = n_in | 1;  // odd: a thread per row hits distinct banks
-    for (int rr = 0; rr < kLbRowsH; ++rr) {
+    // the staged rows x columns as asynchronous 4-byte copies (the warp does
+    // not wait for each load): round A from the clamped column, round B with
+    // a zero fill outside the image
+    for (int idx = threadIdx.x; idx < kLbRowsH * n_in; idx += kLbRowsH) {
+        const int rr = idx / n_in, j = idx - (idx / n_in) * n_in;
         const int gy = min(y0 + rr, H - 1);
-        for (int j = threadIdx.x; j < n_in; j += blockDim.x) {
-            const int gx = x0 - halo + j;
-            float v;
-            if constexpr (ROUND == 0) {
-                v = s[(long long)gy * W + min(max(gx, 0), W - 1)];
-            } else {
-                v = (gx >= 0 && gx < W) ? s[(long long)gy * W + gx] : 0.f;
-            }
-            lb_sm[rr * stride + j] = v;
-        }
+        const int gx = x0 - halo + j;
+        const bool in = gx >= 0 && gx < W;
+        const float *src_el = s + (long long)gy * W + min(max(gx, 0), W - 1);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(lb_sm + rr * stride + j);
+        const int bytes = (ROUND == 0 || in) ? 4 : 0;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src_el),
+                     "r"(bytes)
+                     : "memory");
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     float *a = lb_sm + threadIdx.x * stride;
     float fold_l = 0.f, fold_r = 0.f;
@@ -213,11 +218,11 @@ __global__ void __launch_bounds__(kLbRowsH) lb_hpass(const __grid_constant__ LbP
     if (has_l) a[0] = fold_l;
     if (has_r) a[bj] = fold_r;
     __syncthreads();
-    for (int rr = 0; rr < kLbRowsH; ++rr) {
+#pragma unroll 8
+    for (int idx = threadIdx.x; idx < kLbRowsH * kLbColsH; idx += kLbRowsH) {
+        const int rr = idx / kLbColsH, j = idx - (idx / kLbColsH) * kLbColsH;
         const int gy = y0 + rr;
-        if (gy >= H) break;
-        for (int j = threadIdx.x; j < kLbColsH; j += blockDim.x)
-            if (x0 + j < W) d_out[(long long)gy * W + x0 + j] = lb_sm[rr * stride + j];
+        if (gy < H && x0 + j < W) d_out[(long long)gy * W + x0 + j] = lb_sm[rr * stride + j];
     }
 }
 
