@@ -294,6 +294,21 @@ bf_status bf_forward_host(const bf_plan *plan, const void *host_in, bf_dtype dt,
                           long long row_stride_elems, cudaStream_t stream);
 
 /*
+ * bf_forward_host with the copy back on a second stream (not in the paper):
+ * the copy in (when host_in is not NULL) and the filter run on `stream` as in
+ * bf_forward_host; the copy of dev_out into host_out waits for this call's
+ * filter on `copy_stream` only, so that `stream` goes on with the next
+ * filter while the result travels.  host_out is complete once copy_stream
+ * reaches the copy.  Later work must not write dev_out before the copy is
+ * done: use another dev_out, or make `stream` wait for copy_stream.
+ * copy_stream must differ from stream.  Errors as bf_forward_host.
+ */
+bf_status bf_forward_host_overlap(const bf_plan *plan, const void *host_in, bf_dtype dt,
+                                  void *dev_in, float *dev_out, float *host_out, int H, int W,
+                                  int C, long long row_stride_elems, cudaStream_t stream,
+                                  cudaStream_t copy_stream);
+
+/*
  * bf_forward over a stack of `count` single-channel images of one size, laid
  * out contiguously (image k at in + k*H*W elements, out + k*H*W floats),
  * all filtered with the same plan in one launch (channels are independent,

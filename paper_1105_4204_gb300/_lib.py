@@ -89,6 +89,9 @@ def _declare(lib):
                                                 c_void_p]),
         "bf_forward_host": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_int,
                                     c_int, c_int, ctypes.c_longlong, c_void_p]),
+        "bf_forward_host_overlap": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p,
+                                            c_void_p, c_int, c_int, c_int, ctypes.c_longlong,
+                                            c_void_p, c_void_p]),
         "bf_fp32_pipe_rate": (c_int, [c_int, ctypes.POINTER(ctypes.c_double), c_void_p]),
     }
     for name, (res, args) in sig.items():

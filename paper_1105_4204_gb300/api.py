@@ -213,13 +213,16 @@ def fp32_pipe_rate(paired: bool = False, stream=None) -> float:
 
 def forward_host(plan: Plan, img_host: torch.Tensor | None, out_host: torch.Tensor | None = None,
                  stream=None, dev_in: torch.Tensor | None = None,
-                 dev_out: torch.Tensor | None = None) -> torch.Tensor | None:
+                 dev_out: torch.Tensor | None = None, copy_stream=None) -> torch.Tensor | None:
     """End-to-end call for a host image (``bf_forward_host``): copies img_host
     (pinned for asynchrony) into ``dev_in``, filters it into ``dev_out`` and
     copies the result into ``out_host`` (a new pinned tensor when None), in
     order on the stream.  ``img_host=None`` filters what ``dev_in`` already
     holds (no copy in); the device buffers are allocated when not given.
-    Returns out_host; it is complete once the stream reaches the call's end."""
+    With ``copy_stream`` (``bf_forward_host_overlap``) the copy back runs on
+    that stream after this call's filter, so that ``stream`` can go on.
+    Returns out_host; it is complete once the stream that copies it reaches
+    the call's end."""
     src = img_host if img_host is not None else dev_in
     if src is None:
         raise ValueError("forward_host needs img_host or a filled dev_in")
@@ -237,10 +240,13 @@ def forward_host(plan: Plan, img_host: torch.Tensor | None, out_host: torch.Tens
         raise ValueError("dev_in must have img_host's dtype and strides")
     if not out_host.is_contiguous() or not dev_out.is_contiguous():
         raise ValueError("out_host and dev_out must be contiguous")
-    check(lib().bf_forward_host(
-        plan.handle, ctypes.c_void_p(img_host.data_ptr() if img_host is not None else 0), dt,
-        ctypes.c_void_p(dev_in.data_ptr()), ctypes.c_void_p(dev_out.data_ptr()),
-        ctypes.c_void_p(out_host.data_ptr()), H, W, C, rs, _stream_ptr(stream)))
+    args = (plan.handle, ctypes.c_void_p(img_host.data_ptr() if img_host is not None else 0), dt,
+            ctypes.c_void_p(dev_in.data_ptr()), ctypes.c_void_p(dev_out.data_ptr()),
+            ctypes.c_void_p(out_host.data_ptr()), H, W, C, rs, _stream_ptr(stream))
+    if copy_stream is None:
+        check(lib().bf_forward_host(*args))
+    else:
+        check(lib().bf_forward_host_overlap(*args, _stream_ptr(copy_stream)))
     return out_host
 
 

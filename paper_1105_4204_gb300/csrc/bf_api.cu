@@ -274,6 +274,29 @@ extern "C" bf_status bf_forward_host(const bf_plan *plan, const void *host_in, b
     return BF_OK;
 }
 
+extern "C" bf_status bf_forward_host_overlap(const bf_plan *plan, const void *host_in,
+                                             bf_dtype dt, void *dev_in, float *dev_out,
+                                             float *host_out, int H, int W, int C,
+                                             long long row_stride_elems, cudaStream_t stream,
+                                             cudaStream_t copy_stream) {
+    if (host_out && stream == copy_stream)
+        return fail(BF_EINVAL, "bf_forward_host_overlap: copy_stream must differ from stream");
+    const bf_status st = bf_forward_host(plan, host_in, dt, dev_in, dev_out, nullptr, H, W, C,
+                                         row_stride_elems, stream);
+    if (st != BF_OK || !host_out) return st;
+    // the copy back waits for this call's filter only, on the copy stream
+    cudaEvent_t done;
+    cudaError_t e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_check(e, "bf_forward_host_overlap: event");
+    e = cudaEventRecord(done, stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(copy_stream, done, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, dev_out, (size_t)H * W * C * sizeof(float),
+                            cudaMemcpyDeviceToHost, copy_stream);
+    cudaEventDestroy(done);  // released once the recorded work completes
+    return cuda_check(e, "bf_forward_host_overlap: device -> host copy");
+}
+
 // Runs one BfImage description (interleaved channels or a stack).
 static bf_status forward_planes(const bf_plan *plan, const BfImage &img, cudaStream_t stream,
                                 const char *who) {

@@ -345,6 +345,11 @@ def test_forward_host_rejects_bad_arguments_without_touching_a_gpu(bf):
     assert b"dev_in" in l.bf_last_error()
     assert l.bf_forward_host(p.handle, fake, 0, fake, fake, fake, 16, 16, 1, 8, null) == 1
     assert l.bf_forward_host(p.handle, fake, 0, fake, fake, fake, 16, 16, 5, 80, null) == 2
+    # the overlapping form needs a copy stream other than the filter's
+    l.bf_forward_host_overlap.restype = ctypes.c_int
+    assert l.bf_forward_host_overlap(p.handle, fake, 0, fake, fake, fake, 16, 16, 1, 16, null,
+                                     null) == 1
+    assert b"copy_stream" in l.bf_last_error()
 
 
 def test_space_variant_rejects_bad_arguments_without_touching_a_gpu(bf):

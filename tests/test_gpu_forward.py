@@ -242,6 +242,28 @@ def test_forward_host_matches_the_device_call(bf, oracle):
                                   .cpu().numpy())
 
 
+def test_forward_host_overlap_matches_the_device_call(bf):
+    # the copy back on a second stream: every result equals bf_forward's, with
+    # three calls in flight whose copies overlap the next call's filter
+    import torch
+    img = synth.smooth_field(300, 410, noise=5.0, seed=8)
+    host = torch.from_numpy(img).pin_memory()
+    plans = [bf.Plan(s, 20.0, kind="box") for s in (2.0, 8.0, 12.0)]
+    d_in = torch.empty_like(host, device="cuda")
+    d_out = [torch.empty(img.shape, dtype=torch.float32, device="cuda") for _ in plans]
+    outs = [torch.empty(img.shape, dtype=torch.float32).pin_memory() for _ in plans]
+    main, copy = torch.cuda.current_stream(), torch.cuda.Stream()
+    for rep in range(2):
+        for i, p in enumerate(plans):
+            bf.forward_host(p, host if i == 0 else None, out_host=outs[i], stream=main,
+                            dev_in=d_in, dev_out=d_out[i], copy_stream=copy)
+        main.wait_stream(copy)
+    torch.cuda.synchronize()
+    for p, o in zip(plans, outs):
+        np.testing.assert_array_equal(o.numpy(), bf.forward(p, torch.from_numpy(img).cuda())
+                                      .cpu().numpy())
+
+
 def test_row_stride_and_channels_f32(bf, oracle):
     import torch
     base = synth.rect_disk_u8(33, 40, C=2, n_shapes=6, seed=9).astype(np.float32)
