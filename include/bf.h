@@ -213,19 +213,22 @@ bf_status bf_forward(const bf_plan *plan, const void *in, bf_dtype dt, float *ou
  *              / sum_{|y|_inf <= r(x)} phi(f(x-y) - f(x)).
  * Computed through eq. (final-form) with per-term summed-area tables of the
  * four auxiliary images of the tile, O(1) per pixel and term whatever r(x).
- * The tables hold 32-bit fixed-point values whose step is set by r_max and,
- * for the f-weighted planes, by the value range of the tile, so that every
- * box sum comes out exact for the fixed-point planes; the step's rounding
- * error is of the order of the FP32 sine's.  Results therefore depend, to
- * rounding, on r_max (and on the tile each pixel falls in), not only on r(x).
+ * Each tile of the output builds its tables over a halo of the largest r(x)
+ * among its own pixels.  The tables hold 32-bit fixed-point values whose step
+ * is set by that largest box and, for the f-weighted planes, by the value
+ * range of the extended tile, so that every box sum comes out exact for the
+ * fixed-point planes; the step's rounding error is of the order of the FP32
+ * sine's.  Results therefore depend, to rounding, on the tile each pixel falls
+ * in (its largest radius and its values), not only on r(x).
  * The plan's own spatial kernel is not used; its range kernel (raised cosine
  * or cosine polynomial) is.  Input values must be finite.
  *   in               : device image, H x W, single channel, type dt, rows
  *                      row_stride_elems (>= W) elements apart
  *   radius           : device int32 H x W, row-major (row stride W): the
  *                      half-widths r(x); values are clamped into [0, r_max]
- *   r_max            : 0 <= r_max <= 16, the largest half-width used (it sets
- *                      the halo each tile reads; smaller is faster)
+ *   r_max            : 0 <= r_max <= 16, a bound on the half-widths (it
+ *                      selects the kernel's largest halo and shared-memory
+ *                      footprint; smaller is faster)
  *   out              : device float H x W, row stride W
  * Asynchronous on `stream`.  Errors: BF_EINVAL (NULL pointers, sizes,
  * r_max), BF_EUNSUPPORTED (image too large), BF_ECUDA (launch failure).
