@@ -121,6 +121,8 @@ struct SvGeom {
         return (q & 1 ? O1 : 0) + (q >> 1) * DT;
     }
     static_assert(4 * E <= NTHR, "a thread per table row and per table column");
+    // the box's carry lines (step 1 to step 2): entries per plane, 16 (mod 32)
+    static constexpr int CY = sv_table_stride(E, 16);
     static_assert(NTHR % T == 0 && NTHR % 32 == 0 && T % 32 == 0, "own-pixel layout");
 };
 
@@ -138,6 +140,10 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
     float *Fs = reinterpret_cast<float *>(Tb + DT * ES);
     __shared__ float red[2][NW];
     __shared__ int redr[NW];
+    // the box's first half-row totals per plane and row (plane q at
+    // q CY), then a line of zeros
+    constexpr int CY = G::CY;
+    __shared__ unsigned Cy[HAT ? 1 : 5 * CY + 8];
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int x0 = blockIdx.x * T, y0 = blockIdx.y * T;
@@ -162,6 +168,8 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
 #pragma unroll
     for (int w = 1; w < NW; ++w) R = max(R, redr[w]);
     const int E = T + 2 * R;  // this tile's extended edge (<= G::E)
+    if constexpr (!HAT)
+        for (int k = tid; k < CY; k += NTHR) Cy[4 * CY + 8 + k] = 0u;
     for (int k = tid; k < G::DT; k += NTHR) {  // the leading zero rows and columns
 #pragma unroll
         for (int t = 0; t < 4; ++t)
@@ -251,12 +259,21 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
         line = RMD > 0 && v < PW && q < 4;
     }
     // step 1 takes a thread per (row l1, pair p1): the pair's plain plane p1
-    // (cos or sin) and weighted plane p1 + 2 share one f~ read and one sine;
-    // rows in blocks of 32 of one pair, the remaining rows of both pairs in
-    // one warp when RMD <= 16, else a warp per pair
+    // (cos or sin) and weighted plane p1 + 2 share one f~ read and one sine.
+    // The box splits each row into two halves, (pair, half) k = 2 half + p1
+    // taking the place of q above (the halves' offsets differ by a multiple
+    // of 32 only when SL does; the layout argument holds per half); the hat
+    // keeps whole rows: rows in blocks of 32 of one pair, the remaining rows
+    // of both pairs in one warp when RMD <= 16, else a warp per pair.
+    const int SL = (E + 1) / 2;  // the box's first half-row: columns [0, SL)
     bool line1;
-    int p1, l1;
-    if (tid < 2 * F) {
+    int p1, l1, half = 0;
+    if constexpr (!HAT) {
+        line1 = line;
+        p1 = q & 1;
+        half = q >> 1;
+        l1 = l;
+    } else if (tid < 2 * F) {
         line1 = true;
         p1 = tid / F;
         l1 = tid - p1 * F;
@@ -289,16 +306,23 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
                 w = __float_as_uint(__fmaf_rn(v, fv * sP, kSvMagic));
             };
             if constexpr (!HAT) {
+                // running sums over this half of the row; the first half's
+                // totals become the second half's carry, added in step 2
+                const int j0 = half * SL, j1 = half ? E : SL;
                 unsigned *row = Tb + G::off(p1) + (l1 + 1) * ES + 1;
                 unsigned ru = 0u, rw = 0u;
 #pragma unroll 8
-                for (int j = 0; j < E; ++j) {
+                for (int j = j0; j < j1; ++j) {
                     unsigned u, w;
                     value(j, u, w);
                     ru += u;
                     rw += w;
                     row[j] = ru;
                     row[j + DT] = rw;
+                }
+                if (!half) {
+                    Cy[p1 * CY + l1] = ru;
+                    Cy[(p1 + 2) * CY + l1] = rw;
                 }
             } else {
                 // P2[t] = sum_{s < t} P1[s], P1[s] = sum_{j < s} v[j], t = 0 .. E + 1
@@ -325,11 +349,15 @@ __global__ void __launch_bounds__(NTHR) bf_sv_fwd(const __grid_constant__ SvPara
         // 2. the columns: summed-area tables
         if (line) {
             if constexpr (!HAT) {
+                // the second half's columns add the first half's row totals;
+                // the first half's read a zero line (kept 8 banks from the
+                // carries, so a warp spanning both halves reads without conflict)
                 unsigned *col = Tb + G::off(q) + ES + l + 1;
+                const unsigned *cy = Cy + (l < SL ? 4 * CY + 8 : q * CY);
                 unsigned run = 0u;
 #pragma unroll 8
                 for (int i = 0; i < E; ++i) {
-                    run += col[i * ES];
+                    run += col[i * ES] + cy[i];
                     col[i * ES] = run;
                 }
             } else {
