@@ -473,6 +473,9 @@ __global__ void lr_final(const float *__restrict__ Acc, int n_slots, float *__re
         if (x < W && y < H) {
             const size_t o = blocked_at(W, x, y);
             float q = Acc[o], pp = Acc[plane + o];
+            // unrolled so that the slots' loads are in flight together (the
+            // sums still run in slot order)
+#pragma unroll 8
             for (int s = 1; s < n_slots; ++s) {
                 q += Acc[2 * s * plane + o];
                 pp += Acc[(2 * s + 1) * plane + o];

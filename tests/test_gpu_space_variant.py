@@ -203,3 +203,38 @@ def test_interleaved_channels(bf, oracle, spatial, r_max):
         ref = oracle.bf_brute_sv(img[..., c].astype(np.float64), rad, sigma_r=30.0, r_max=r_max,
                                  N=plan.N, spatial=spatial)
         assert np.abs(out[..., c] - ref).max() <= TOL
+
+
+def _per_tile_radii(H, W, T, r_max, seed):
+    """A radius map whose output tiles (T x T, as the kernel cuts them) each
+    have their own largest radius R in [0, r_max]: random radii up to R inside
+    the tile, R itself at one corner or edge pixel, so that neighbouring
+    tiles build tables of different halos next to each other."""
+    rng = np.random.default_rng(seed)
+    rad = np.zeros((H, W), np.int32)
+    for y0 in range(0, H, T):
+        for x0 in range(0, W, T):
+            h, w = min(T, H - y0), min(T, W - x0)
+            R = int(rng.integers(0, r_max + 1))
+            blk = rng.integers(0, R + 1, size=(h, w)).astype(np.int32) if R else np.zeros((h, w), np.int32)
+            if rng.random() < 0.5:
+                blk[:] = np.minimum(blk, max(R - 1, 0))  # R only at the chosen pixel
+            yy, xx = [(0, 0), (0, w - 1), (h - 1, 0), (h - 1, w - 1), (h // 2, 0)][int(rng.integers(0, 5))]
+            blk[yy, xx] = R
+            rad[y0:y0 + h, x0:x0 + w] = blk
+    return rad
+
+
+@pytest.mark.parametrize("spatial,r_max,T", [("box", 4, 32), ("box", 8, 32), ("box", 16, 64),
+                                             ("hat", 4, 32), ("hat", 8, 32)])
+def test_tiles_with_their_own_halos(bf, oracle, spatial, r_max, T):
+    # each tile's tables span a halo of its own largest radius: tiles of
+    # radius 0 next to tiles of r_max, the largest radius on a tile's corner
+    H, W = 2 * T + 23, 3 * T + 9
+    img = synth.rectangles(H, W, n_rect=8, noise=10.0, seed=T + r_max)
+    rad = _per_tile_radii(H, W, T, r_max, seed=r_max + (7 if spatial == "hat" else 0))
+    plan = bf.Plan(3.0, 20.0, kind="box")
+    out = _sv(bf, img, rad, plan, r_max, spatial=spatial)
+    ref = oracle.bf_brute_sv(img, rad, sigma_r=20.0, r_max=r_max, N=plan.N, spatial=spatial)
+    err = np.abs(out - ref).max()
+    assert err <= TOL, err
