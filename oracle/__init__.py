@@ -121,6 +121,14 @@ def _load():
         lib.or_rg_coefs.argtypes = [ctypes.c_double, _dp]
         lib.or_rg_filter.restype = None
         lib.or_rg_filter.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]
+        lib.or_rg_matrix.restype = None
+        lib.or_rg_matrix.argtypes = [ctypes.c_int, ctypes.c_double, _dp]
+        lib.or_bf_brute_mat.restype = None
+        lib.or_bf_brute_mat.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_int, _dp]
+        lib.or_bf_grad_mat.restype = None
+        lib.or_bf_grad_mat.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
         lib.or_bf_trig_rg.restype = ctypes.c_double
         lib.or_bf_trig_rg.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
@@ -528,6 +536,54 @@ def rg_filter(img, sigma: float) -> np.ndarray:
     y = np.empty_like(x)
     _load().or_rg_filter(_ptr(x), H, W, float(sigma), _ptr(y))
     return y
+
+
+def rg_matrix(n: int, sigma: float) -> np.ndarray:
+    """The recursive Gaussian of one line of n samples as an n x n matrix
+    (row a: the weights of the inputs in output a)."""
+    M = np.empty((n, n), dtype=np.float64)
+    _load().or_rg_matrix(int(n), float(sigma), _ptr(M))
+    return M
+
+
+def bf_brute_mat(f, Mv, Mh, sigma_r=30.0, T=255.0, N=None, range_mode="raised_cosine"):
+    """eq. (BF) with explicit per-axis weight matrices: pixel (zi, zj) weighs
+    Mv[i, zi] Mh[j, zj] in the output at (i, j)."""
+    if N is None:
+        N = n_rule(sigma_r, T)
+    x = _f64(f)
+    H, W = x.shape
+    Mv, Mh = _f64(Mv), _f64(Mh)
+    assert Mv.shape == (H, H) and Mh.shape == (W, W)
+    out = np.empty((H, W), dtype=np.float64)
+    _load().or_bf_brute_mat(_ptr(x), H, W, _ptr(Mv), _ptr(Mh), _range_mode(range_mode),
+                            float(sigma_r), int(N), _ptr(out))
+    return out
+
+
+def bf_grad_mat(f, u, Mv, Mh, sigma_r=25.0, T=255.0, N=None, range_mode="raised_cosine"):
+    """Exact FP64 gradient of sum(u * out) w.r.t. f and sigma_r (N fixed) for
+    the filter of bf_brute_mat."""
+    if N is None:
+        N = n_rule(sigma_r, T)
+    x, uu = _f64(f), _f64(u)
+    H, W = x.shape
+    Mv, Mh = _f64(Mv), _f64(Mh)
+    assert Mv.shape == (H, H) and Mh.shape == (W, W)
+    g = np.empty((H, W), dtype=np.float64)
+    gs = ctypes.c_double(0.0)
+    _load().or_bf_grad_mat(_ptr(x), _ptr(uu), H, W, _ptr(Mv), _ptr(Mh), _range_mode(range_mode),
+                           float(sigma_r), int(N), _ptr(g), ctypes.byref(gs))
+    return g, float(gs.value)
+
+
+def bf_grad_rg(f, u, sigma_s=4.0, sigma_r=25.0, T=255.0, N=None):
+    """Exact FP64 gradient of sum(u * out) for the recursive Gaussian spatial
+    filter (Section 3): bf_grad_mat with the line filter's matrices."""
+    x = _f64(f)
+    H, W = x.shape
+    return bf_grad_mat(x, u, rg_matrix(H, sigma_s), rg_matrix(W, sigma_s), sigma_r=sigma_r,
+                       T=T, N=N)
 
 
 def bf_trig_rg(f, sigma_s=10.0, sigma_r=30.0, T=255.0, N=None, return_q=False):

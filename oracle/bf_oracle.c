@@ -24,7 +24,10 @@
  *   - or_rg_* / or_bf_trig_rg : the recursive O(1) Gaussian of Young and van
  *                        Vliet (the spatial filter of the paper's experiments,
  *                        Section 3) and Algorithm 1 with it as the averaging
- *                        of step 4;
+ *                        of step 4; or_rg_matrix, the same line filter as a
+ *                        matrix, and or_bf_brute_mat / or_bf_grad_mat, the
+ *                        filter and its exact gradient with explicit per-axis
+ *                        weight matrices;
  *   - or_bf_brute_sv   : the space-variant extension (Section 4): at each
  *                        pixel its own box (or, or_bf_brute_sv_shape, hat)
  *                        of half-width r(x), eq. (BF) summed directly over it;
@@ -695,6 +698,123 @@ void or_rg_filter(const double *x, int H, int W, double sigma, double *y)
     or_rg_filter_c(a, H, W, sigma, t, b);
     for (size_t p = 0; p < n; p++) y[p] = creal(b[p]);
     free(a); free(t); free(b);
+}
+
+/* The recursive Gaussian of one line of n samples as an n x n matrix:
+ * M[a n + b] is the weight of input b in output a (column b is the line's
+ * response to the unit vector e_b, both recursions and their starts and the
+ * extension past the end included).  The filter is linear, so these weights
+ * are the whole filter. */
+void or_rg_matrix(int n, double sigma, double *M)
+{
+    double c[4];
+    int P = or_rg_coefs(sigma, c);
+    double complex *e = (double complex *)malloc(sizeof(double complex) * (size_t)n);
+    double complex *w = (double complex *)malloc(sizeof(double complex) * (size_t)(n + P));
+    double complex *y = (double complex *)malloc(sizeof(double complex) * (size_t)n);
+    for (int b = 0; b < n; b++) {
+        for (int k = 0; k < n; k++) e[k] = k == b ? 1.0 : 0.0;
+        or_rg_line(e, 1, n, c, P, w, y);
+        for (int a = 0; a < n; a++) M[(size_t)a * n + b] = creal(y[a]);
+    }
+    free(e); free(w); free(y);
+}
+
+/* P and Q of eq. (BF) at pixel (i, j) with explicit per-axis weights: pixel
+ * (zi, zj) weighs Mv[i][zi] Mh[j][zj] (any separable linear spatial filter,
+ * its border handling folded into the matrices). */
+static void or_pq_mat(const double *f, int H, int W, const double *Mv, const double *Mh,
+                      const or_range *rg, int i, int j, double *P, double *Q)
+{
+    double fx = f[(size_t)i * W + j], num = 0.0, den = 0.0;
+    for (int zi = 0; zi < H; zi++) {
+        double wv = Mv[(size_t)i * H + zi];
+        if (wv == 0.0) continue;
+        for (int zj = 0; zj < W; zj++) {
+            double weight = wv * Mh[(size_t)j * W + zj];
+            double val = f[(size_t)zi * W + zj];
+            double k = or_phi(rg, val - fx);
+            num += weight * k * val;
+            den += weight * k;
+        }
+    }
+    *P = num;
+    *Q = den;
+}
+
+/* eq. (BF) summed over every pixel with the weights of or_pq_mat. */
+void or_bf_brute_mat(const double *f, int H, int W, const double *Mv, const double *Mh,
+                     int mode, double sigma_r, int N, double *out)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < H; i++)
+        for (int j = 0; j < W; j++) {
+            double P, Q;
+            or_pq_mat(f, H, W, Mv, Mh, &rg, i, j, &P, &Q);
+            out[(size_t)i * W + j] = P / Q;
+        }
+}
+
+/* Exact gradient of L = sum_x u(x) out(x) with respect to every pixel of f
+ * and to sigma_r (N held fixed) with the weights of or_pq_mat: the chain rule
+ * of or_grad_rg, each pixel z of the image contributing with its weight in
+ * the output at x (through its value and the argument f(z) - f(x)) and x
+ * through the argument. */
+void or_bf_grad_mat(const double *f, const double *u, int H, int W, const double *Mv,
+                    const double *Mh, int mode, double sigma_r, int N, double *grad_f,
+                    double *grad_sigma_r)
+{
+    or_range rg = or_make_range(mode, sigma_r, N);
+    size_t n = (size_t)H * W;
+    int nt = or_num_threads();
+    double *buf = (double *)calloc(n * (size_t)nt, sizeof(double));
+    double *gs = (double *)calloc((size_t)nt, sizeof(double));
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *g = buf + n * (size_t)tid;
+        double gsl = 0.0;
+#pragma omp for schedule(dynamic, 4)
+        for (int i = 0; i < H; i++) {
+            for (int j = 0; j < W; j++) {
+                double P, Q;
+                or_pq_mat(f, H, W, Mv, Mh, &rg, i, j, &P, &Q);
+                double o = P / Q;
+                double alpha = u[(size_t)i * W + j] / Q;
+                double fx = f[(size_t)i * W + j];
+                const size_t px = (size_t)i * W + j;
+                for (int zi = 0; zi < H; zi++) {
+                    double wv = Mv[(size_t)i * H + zi];
+                    if (wv == 0.0) continue;
+                    for (int zj = 0; zj < W; zj++) {
+                        const size_t pz = (size_t)zi * W + zj;
+                        double aw = alpha * wv * Mh[j * (size_t)W + zj];
+                        double dv = f[pz] - o;
+                        double arg = f[pz] - fx;
+                        double dk = or_dphi(&rg, arg);
+                        g[pz] += aw * (or_phi(&rg, arg) + dk * dv);
+                        g[px] -= aw * dk * dv;
+                        if (grad_sigma_r) gsl += aw * or_dphi_dsigma(&rg, arg) * dv;
+                    }
+                }
+            }
+        }
+        gs[tid] = gsl;
+    }
+    for (size_t p = 0; p < n; p++) {
+        double s = 0.0;
+        for (int t = 0; t < nt; t++) s += buf[n * (size_t)t + p];
+        grad_f[p] = s;
+    }
+    double s = 0.0;
+    for (int t = 0; t < nt; t++) s += gs[t];
+    if (grad_sigma_r) *grad_sigma_r = s;
+    free(buf);
+    free(gs);
 }
 
 /* Algorithm 1, steps 1-5, in the paper's complex notation (as or_bf_trig),

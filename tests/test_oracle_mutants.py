@@ -60,6 +60,9 @@ MUTANTS = {
                                                          ": 3.97156 - 4.14545 * sqrt"),
     "space-variant hat weight off by one": ("double wa = hat ? (double)(r + 1 - abs(a)) : 1.0;",
                                             "double wa = hat ? (double)(r + 2 - abs(a)) : 1.0;"),
+    "matrix weights transposed": ("double weight = wv * Mh[(size_t)j * W + zj];",
+                                  "double weight = wv * Mh[(size_t)zj * W + j];"),
+    "matrix-form gradient term flipped": ("g[px] -= aw * dk * dv;", "g[px] += aw * dk * dv;"),
 }
 
 
@@ -149,6 +152,29 @@ def _checks(o):
         if not np.allclose(c, [B, b1 / b0, b2 / b0, b3 / b0], rtol=1e-9, atol=1e-15):
             failed.append("recursive Gaussian published design")
             break
+    # the filter and gradient with explicit per-axis weight matrices: the
+    # clamp-extended Gaussian's matrices give the tap-based results, and the
+    # recursive filter's give Algorithm 1 with the recursion
+    def clamp_matrix(nn, taps):
+        R = (len(taps) - 1) // 2
+        M = np.zeros((nn, nn))
+        for a in range(nn):
+            for d in range(-R, R + 1):
+                M[a, min(max(a - d, 0), nn - 1)] += taps[d + R]
+        return M
+    fm = f[:9, :10]
+    um = u[:9, :10]
+    Mv, Mh = clamp_matrix(9, wg), clamp_matrix(10, wg)
+    g_taps, s_taps = o.bf_grad(fm, um, sigma_s=1.5, sigma_r=30.0)
+    g_mat, s_mat = o.bf_grad_mat(fm, um, Mv, Mh, sigma_r=30.0)
+    if not np.allclose(g_mat, g_taps, rtol=0, atol=1e-10) or abs(s_mat - s_taps) > 1e-9 \
+            or not np.allclose(o.bf_brute_mat(fm, Mv, Mh, sigma_r=30.0),
+                               o.bf_brute(fm, sigma_r=30.0, w1=wg), rtol=0, atol=1e-9):
+        failed.append("matrix form = taps")
+    Rv, Rh = o.rg_matrix(9, 3.0), o.rg_matrix(10, 3.0)
+    if not np.allclose(o.bf_brute_mat(fm, Rv, Rh, sigma_r=30.0),
+                       o.bf_trig_rg(fm, sigma_s=3.0, sigma_r=30.0), rtol=0, atol=1e-8):
+        failed.append("matrix form = Algorithm 1 with the recursive filter")
     return failed
 
 

@@ -464,6 +464,42 @@ def test_algorithm1_with_the_recursive_filter(oracle):
     np.testing.assert_allclose(out.ravel()[idx], ref, atol=1e-6)
 
 
+def test_recursive_filter_matrix_is_the_line_filter(oracle):
+    # rg_matrix's columns are the line's unit responses: applying the matrix is the
+    # filter (a 1-row image filters its row alone), rows sum to 1 (unit DC gain),
+    # and the interior rows are shifts of one impulse response
+    W, sigma = 37, 2.5
+    M = oracle.rg_matrix(W, sigma)
+    x = np.random.default_rng(3).uniform(0, 255, W)
+    np.testing.assert_allclose(M @ x, oracle.rg_filter(x[None, :], sigma)[0], atol=1e-10)
+    np.testing.assert_allclose(M.sum(axis=1), 1.0, atol=1e-12)
+    np.testing.assert_allclose(M[18, 18 - 5:18 + 6], M[19, 19 - 5:19 + 6], atol=1e-6)
+    assert oracle.rg_matrix(1, sigma)[0, 0] == pytest.approx(1.0, abs=1e-14)
+
+
+@pytest.mark.parametrize("sigma_s", [0.8, 3.0, 7.0])
+def test_recursive_filter_gradient_matches_finite_differences(oracle, sigma_s):
+    # the exact gradient with the recursive filter (its matrices in the chain rule)
+    # against central differences of Algorithm 1 with the recursion, at corner,
+    # edge and interior pixels, and for sigma_r with N held fixed
+    f = synth.rectangles(13, 17, n_rect=4, noise=8.0, seed=5).astype(np.float64)
+    u = np.random.default_rng(6).standard_normal(f.shape)
+    N = oracle.n_rule(25.0)
+    g, gs = oracle.bf_grad_rg(f, u, sigma_s=sigma_s, sigma_r=25.0, N=N)
+    h = 1e-4
+
+    def L(ff, sr=25.0):
+        return float((u * oracle.bf_trig_rg(ff, sigma_s=sigma_s, sigma_r=sr, N=N)).sum())
+    for (i, j) in [(0, 0), (0, 16), (12, 0), (12, 16), (6, 8), (3, 0), (0, 9)]:
+        fp, fm = f.copy(), f.copy()
+        fp[i, j] += h
+        fm[i, j] -= h
+        fd = (L(fp) - L(fm)) / (2 * h)
+        assert g[i, j] == pytest.approx(fd, rel=2e-5, abs=2e-6)
+    fd_s = (L(f, 25.0 + h) - L(f, 25.0 - h)) / (2 * h)
+    assert gs == pytest.approx(fd_s, rel=1e-6, abs=1e-7)
+
+
 # ------------------------------------------------------ space-variant (Section 4)
 
 def _golden_sv():
