@@ -405,7 +405,11 @@ bf_status bf_forward_unfused(const bf_plan *plan, const float *in, float *out, i
  * large-radius path uses, shared with it, allocated on first need and kept
  * until bf_release_scratch(); the first such call on a device must not
  * happen during stream capture).  That path is bandwidth-bound, not fused.
- * The recursive Gaussian has no adjoint (BF_EUNSUPPORTED).
+ * The recursive Gaussian (Section 3) takes the same path with its own line
+ * filter and that filter's transpose (the recursions run in the same
+ * directions from zero starts, the adjoints of the steady-state starts added
+ * at the line's ends and the extension folded onto its last pixel), about
+ * 48 * H * W + 24 * P * (H + W) bytes of that scratch, P = ceil(6 sigma_s).
  * Accuracy: dL/df within 1e-3 of the exact gradient (relative to its largest
  * element).  dL/dsigma_r carries the FP32 expansion's error in the kernel's
  * sigma_r-derivative weighted by grad_out / Q.  It stays within 1e-3 where Q

@@ -102,7 +102,8 @@ static int default_split(const bf_plan *p, const BfImage &img, int shape) {
 }
 
 
-// Library-owned scratch for the large-radius box path, one buffer per device,
+// Library-owned scratch for the streaming paths (the large-radius box and the
+// recursive Gaussian, forward and adjoint), one buffer per device,
 // grown on demand and reused until bf_release_scratch().
 static std::mutex g_scratch_mu;
 static void *g_scratch[64];
@@ -406,7 +407,7 @@ extern "C" bf_status bf_forward_unfused(const bf_plan *plan, const float *in, fl
 namespace bf {
 bool bwd_supported(const bf_plan *p);
 bool bwd_large_supported(const bf_plan *p);
-size_t bwd_large_workspace(int H, int W, int count);
+size_t bwd_large_workspace(const bf_plan *pl, int H, int W, int count);
 cudaError_t launch_backward_large(const bf_plan *pl, const float *f, const float *o,
                                   const float *q, const float *u, float *grad,
                                   double *partials, int H, int W, int count, void *ws,
@@ -432,9 +433,9 @@ static bf_status run_backward(const char *who, const bf_plan *plan, const float 
                                           partials, H, W, stream, count),
                           who);
     void *ws = nullptr;
-    cudaError_t e = get_scratch(bwd_large_workspace(H, W, count), &ws);
+    cudaError_t e = get_scratch(bwd_large_workspace(plan, H, W, count), &ws);
     if (e != cudaSuccess)
-        return fail(BF_ENOMEM, std::string(who) + ": cannot allocate the large-radius scratch");
+        return fail(BF_ENOMEM, std::string(who) + ": cannot allocate the adjoint's scratch");
     e = launch_backward_large(plan, f, out, q, grad_out, grad_in,
                               grad_sigma_r ? partials : nullptr, H, W, count, ws, stream);
     if (e == cudaSuccess && grad_sigma_r)
@@ -469,7 +470,8 @@ extern "C" bf_status bf_backward_stack(const bf_plan *plan, const float *f, cons
                                          std::to_string(BF_MAX_ROWS) + " rows");
     if (!bwd_supported(plan) && !bwd_large_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward_stack: no kernel for this spatial support "
-                                     "(Gaussian R <= 24 or box r <= 64)");
+                                     "(Gaussian R <= 24, box r <= 64 or the recursive "
+                                     "Gaussian)");
     if (grad_sigma_r && plan->cosine)
         return fail(BF_EINVAL, "bf_backward_stack: a cosine-polynomial plan has no sigma_r; "
                                "pass grad_sigma_r = NULL");
@@ -502,7 +504,8 @@ extern "C" bf_status bf_backward(const bf_plan *plan, const float *f, const floa
                                          std::to_string(BF_MAX_ROWS) + " rows");
     if (!bwd_supported(plan) && !bwd_large_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward: no kernel for this spatial support "
-                                     "(Gaussian R <= 24 or box r <= 64)");
+                                     "(Gaussian R <= 24, box r <= 64 or the recursive "
+                                     "Gaussian)");
     if (grad_sigma_r && plan->cosine)
         return fail(BF_EINVAL, "bf_backward: a cosine-polynomial plan has no sigma_r; "
                                "pass grad_sigma_r = NULL");

@@ -25,6 +25,19 @@
 // 32 x 64 block, summed over the terms in order and reduced afterwards as the
 // fused adjoint's partials are.  Every kernel reads and writes device memory:
 // this path trades bandwidth for a support of any size.
+//
+// The recursive Gaussian (Section 3) runs the same rounds with its own line
+// filter per axis in place of the boxes (rb_vpass, rb_hpass): W is the
+// forward line, the causal recursion from the steady state of the first
+// sample over the line and P samples of its last one, then the anticausal
+// recursion from the steady state of the causal pass's last output.  W^T
+// reverses those steps: the zero-extended line through the causal recursion
+// from zero, the anticausal recursion from zero with the adjoint of the
+// anticausal start added at the last sample, then the adjoint of the causal
+// start added at the first pixel and the extension's samples folded onto the
+// last pixel.  Both recursions run in the difference form of the forward
+// filter (unit DC gain whatever the rounding of B); the extension's samples
+// go to buffers of their own.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -300,24 +313,181 @@ __global__ void __launch_bounds__(256) lb_combine(const __grid_constant__ LbPara
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// ---- recursive Gaussian -------------------------------------------------------
+
+constexpr int kRbThreads = 64;  // lines per block (a thread each)
+
+struct RbCoef {
+    float B;          // the recursions' input weight
+    float D1, D2;     // a2 + a3 and a3 of the difference form
+    float oneMinusB;  // a1 + a2 + a3, the weight of a steady start's three samples
+    float invB;
+    int P;            // extension past the last sample
+};
+
+// One step of the difference form: w(e) = w(e-1) + [B (x - w(e-1)) - (D1 d1 + D2 d2)],
+// d1, d2 the last two increments (the recursion B x + a1 w(e-1) + a2 w(e-2) + a3 w(e-3)).
+__device__ __forceinline__ float rb_step(const RbCoef &c, float x, float &w, float &d1,
+                                         float &d2) {
+    const float dw = __fsub_rn(__fmul_rn(c.B, __fsub_rn(x, w)),
+                               __fmaf_rn(c.D2, d2, __fmul_rn(c.D1, d1)));
+    w = __fadd_rn(w, dw);
+    d2 = d1;
+    d1 = dw;
+    return w;
+}
+
+// The line filter (ROUND 0: W; 1: W^T) of one line of n samples, stride st
+// apart in `line` (samples 0 .. n-1, filtered in place) and `ext` (the P
+// extension samples, stride st), whose input sample k < n comes from in(k).
+template <int ROUND, class In>
+__device__ __forceinline__ void rb_line(const RbCoef &c, In &&in, int n, float *line,
+                                        float *ext, long long st) {
+    const int E = n + c.P;
+    float w, d1 = 0.f, d2 = 0.f;
+    float z1 = 0.f, z2 = 0.f, z3 = 0.f;  // the causal pass's last three outputs
+    float last = 0.f;                    // ROUND 0: sample n - 1, the extension's value
+    if constexpr (ROUND == 0) {
+        w = in(0);  // steady state of the first sample
+    } else {
+        w = 0.f;
+    }
+    for (int k = 0; k < E; ++k) {
+        float x;
+        if (k < n) {
+            x = in(k);
+            last = x;
+        } else {
+            x = ROUND == 0 ? last : 0.f;
+        }
+        rb_step(c, x, w, d1, d2);
+        if (k < n) line[k * st] = w;
+        else ext[(k - n) * st] = w;
+        z3 = z2;
+        z2 = z1;
+        z1 = w;
+    }
+    // anticausal: ROUND 0 from the steady state of the causal pass's last
+    // output; ROUND 1 from zero, the adjoint of that start entering at E - 1
+    if constexpr (ROUND == 0) {
+        w = z1;
+    } else {
+        w = 0.f;
+    }
+    d1 = d2 = 0.f;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, fold = 0.f;
+    for (int k = E - 1; k >= 0; --k) {
+        float x = k < n ? line[k * st] : ext[(k - n) * st];
+        if (ROUND == 1 && k == E - 1)
+            x = __fadd_rn(x, __fmul_rn(__fmaf_rn(c.oneMinusB, z1, __fmaf_rn(c.D1, z2,
+                                                                            __fmul_rn(c.D2, z3))),
+                                       c.invB));
+        rb_step(c, x, w, d1, d2);
+        if (k < n) line[k * st] = w;
+        else if (ROUND == 1) fold = __fadd_rn(fold, w);
+        v2 = v1;
+        v1 = v0;
+        v0 = w;
+    }
+    if constexpr (ROUND == 1) {
+        // the causal start's adjoint on the first pixel, the extension folded
+        // onto the last
+        float first = __fadd_rn(v0, __fmul_rn(__fmaf_rn(c.oneMinusB, v0,
+                                                        __fmaf_rn(c.D1, v1, __fmul_rn(c.D2, v2))),
+                                              c.invB));
+        if (n == 1) {
+            first = __fadd_rn(first, fold);
+        } else {
+            line[(n - 1) * st] = __fadd_rn(line[(n - 1) * st], fold);
+        }
+        line[0] = first;
+    }
+}
+
+// Vertical pass of plane q of image img (blockIdx.z = img * planes + q): the
+// plane generated down each column (round A: every row of the image, round
+// B: alpha-weighted) and filtered in place in dst; the extension rows in X
+// (P rows per plane).
+// grid: (ceil(W / kRbThreads), 1, images x planes); block: kRbThreads
+template <int ROUND>
+__global__ void __launch_bounds__(kRbThreads) rb_vpass(const __grid_constant__ LbParams p,
+                                                      const RbCoef c, float *__restrict__ dst,
+                                                      float *__restrict__ X, float tm,
+                                                      int planes) {
+    const int H = p.H, W = p.W;
+    const long long n = (long long)H * W;
+    const int x = blockIdx.x * kRbThreads + threadIdx.x;
+    const int img = blockIdx.z / planes, q = blockIdx.z - img * planes;
+    if (x >= W) return;
+    const long long ioff = img * n + x;
+    const long long pl = (long long)img * kLbPlanes + q;
+    auto in = [&](int k) { return lb_plane<ROUND>(p, ioff + (long long)k * W, q, tm); };
+    rb_line<ROUND>(c, in, H, dst + pl * n + x, X + pl * c.P * W + x, W);
+}
+
+// Horizontal pass of plane q of image img: src's rows filtered into dst; the
+// extension columns in X (P per row).
+// grid: (ceil(H / kRbThreads), 1, images x planes); block: kRbThreads
+template <int ROUND>
+__global__ void __launch_bounds__(kRbThreads) rb_hpass(const __grid_constant__ LbParams p,
+                                                      const RbCoef c,
+                                                      const float *__restrict__ src,
+                                                      float *__restrict__ dst,
+                                                      float *__restrict__ X, int planes) {
+    const int H = p.H, W = p.W;
+    const long long n = (long long)H * W;
+    const int y = blockIdx.x * kRbThreads + threadIdx.x;
+    const int img = blockIdx.z / planes, q = blockIdx.z - img * planes;
+    if (y >= H) return;
+    const long long pl = (long long)img * kLbPlanes + q;
+    const float *row = src + pl * n + (long long)y * W;
+    auto in = [&](int k) { return row[k]; };
+    rb_line<ROUND>(c, in, W, dst + pl * n + (long long)y * W,
+                   X + (pl * H + y) * (long long)c.P, 1);
+}
+
 }  // namespace
 
 bool bwd_large_supported(const bf_plan *p) {
+    if (p->kind == BF_SPATIAL_GAUSS_RECURSIVE) return p->rg_P >= 1;
     return p->kind == BF_SPATIAL_BOX_ITER && p->passes == 3 && p->r_box > 8 &&
            3 * p->r_box <= kLbMaxHalo;
 }
 
+// Extension samples per image of the recursive Gaussian's passes (P rows of
+// W and H rows of P per plane); none for the box.
+static size_t lb_ext(const bf_plan *pl, int H, int W) {
+    if (pl->kind != BF_SPATIAL_GAUSS_RECURSIVE) return 0;
+    return (size_t)kLbPlanes * (size_t)pl->rg_P * ((size_t)W + (size_t)H);
+}
+
 // Images of a stack per chunk: as many as kLbChunkBytes of scratch hold (at
 // least one), and at most 65535 / kLbPlanes (the grid's z dimension).
-static int lb_chunk(int H, int W, int count) {
-    const size_t per = 2 * (size_t)kLbPlanes * (size_t)H * (size_t)W * sizeof(float);
+static int lb_chunk(const bf_plan *pl, int H, int W, int count) {
+    const size_t per =
+        (2 * (size_t)kLbPlanes * (size_t)H * (size_t)W + lb_ext(pl, H, W)) * sizeof(float);
     const size_t fit = std::max<size_t>(1, kLbChunkBytes / per);
     return (int)std::min<size_t>(std::min<size_t>(fit, (size_t)count), 65535 / kLbPlanes);
 }
 
-size_t bwd_large_workspace(int H, int W, int count) {
-    const size_t n = (size_t)H * (size_t)W * (size_t)lb_chunk(H, W, count);
-    return 2 * align256((size_t)kLbPlanes * n * sizeof(float)) + 256;
+// The recursive Gaussian's extension buffers for a chunk of k images: the
+// vertical pass's P rows of W and the horizontal pass's H rows of P per plane.
+static size_t lb_ext_v(const bf_plan *pl, int W, size_t k) {
+    return pl->kind == BF_SPATIAL_GAUSS_RECURSIVE
+               ? align256((size_t)kLbPlanes * pl->rg_P * (size_t)W * k * sizeof(float))
+               : 0;
+}
+static size_t lb_ext_h(const bf_plan *pl, int H, size_t k) {
+    return pl->kind == BF_SPATIAL_GAUSS_RECURSIVE
+               ? align256((size_t)kLbPlanes * pl->rg_P * (size_t)H * k * sizeof(float))
+               : 0;
+}
+
+size_t bwd_large_workspace(const bf_plan *pl, int H, int W, int count) {
+    const size_t k = (size_t)lb_chunk(pl, H, W, count);
+    const size_t n = (size_t)H * (size_t)W * k;
+    return 2 * align256((size_t)kLbPlanes * n * sizeof(float)) + lb_ext_v(pl, W, k) +
+           lb_ext_h(pl, H, k) + 256;
 }
 
 // count images n = H W apart; partials: count x ceil(W/64) x ceil(H/32)
@@ -327,7 +497,7 @@ cudaError_t launch_backward_large(const bf_plan *pl, const float *f, const float
                                   double *partials, int H, int W, int count, void *ws,
                                   cudaStream_t s) {
     const long long n = (long long)H * W;
-    const int chunk = lb_chunk(H, W, count);
+    const int chunk = lb_chunk(pl, H, W, count);
     char *base = reinterpret_cast<char *>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     const size_t buf = align256((size_t)kLbPlanes * n * chunk * sizeof(float));
     float *B = reinterpret_cast<float *>(base);  // vertical-pass planes
@@ -335,6 +505,59 @@ cudaError_t launch_backward_large(const bf_plan *pl, const float *f, const float
     LbParams p;
     p.H = H;
     p.W = W;
+    p.inv_sigma_r = pl->sigma_r > 0 ? (float)(1.0 / pl->sigma_r) : 0.f;
+    p.c0 = (float)(0.5 * pl->T);
+    if (pl->kind == BF_SPATIAL_GAUSS_RECURSIVE) {
+        // the recursive Gaussian: extension buffers after the two plane buffers
+        float *XV = reinterpret_cast<float *>(base + 2 * buf);
+        float *XH = reinterpret_cast<float *>(base + 2 * buf + lb_ext_v(pl, W, chunk));
+        RbCoef c;
+        c.B = (float)pl->rg[0];
+        c.D1 = (float)(pl->rg[2] + pl->rg[3]);
+        c.D2 = (float)pl->rg[3];
+        c.oneMinusB = (float)(pl->rg[1] + pl->rg[2] + pl->rg[3]);
+        c.invB = (float)(1.0 / pl->rg[0]);
+        c.P = pl->rg_P;
+        p.r = 0;
+        p.halo = 0;
+        p.total = 1.f;
+        p.scale = 1.f;  // the recursive filter has unit gain
+        for (int d = 0; d <= kLbMaxHalo; ++d) p.tail[d] = 0.f;
+        const bool sig = partials != nullptr;
+        const int planes_a = sig ? 6 : 4;
+        const int gvx = (W + kRbThreads - 1) / kRbThreads, ghx = (H + kRbThreads - 1) / kRbThreads;
+        const dim3 gc((W + kCombTW - 1) / kCombTW, (H + kCombTH - 1) / kCombTH);
+        const size_t nblk = (size_t)gc.x * gc.y;
+        const int nt = (int)pl->a32.size();
+        for (int img0 = 0; img0 < count; img0 += chunk) {
+            const int nimg = std::min(chunk, count - img0);
+            p.f = f + img0 * n;
+            p.o = o + img0 * n;
+            p.q = q + img0 * n;
+            p.u = u + img0 * n;
+            float *g = grad + img0 * n;
+            double *part = sig ? partials + img0 * nblk : nullptr;
+            const dim3 gcz(gc.x, gc.y, nimg);
+            for (int m = 0; m < nt; ++m) {
+                const float am = pl->a32[m], tm = pl->turns32[m], wm = (float)pl->omega[m];
+                rb_vpass<0><<<dim3(gvx, 1, nimg * planes_a), kRbThreads, 0, s>>>(p, c, B, XV, tm,
+                                                                                  planes_a);
+                rb_hpass<0><<<dim3(ghx, 1, nimg * planes_a), kRbThreads, 0, s>>>(p, c, B, A, XH,
+                                                                                  planes_a);
+                if (sig)
+                    lb_combine<0, true><<<gcz, 256, 0, s>>>(p, A, g, part, am, tm, wm, m == 0);
+                else
+                    lb_combine<0, false><<<gcz, 256, 0, s>>>(p, A, g, nullptr, am, tm, wm,
+                                                             m == 0);
+                rb_vpass<1><<<dim3(gvx, 1, nimg * 4), kRbThreads, 0, s>>>(p, c, B, XV, tm, 4);
+                rb_hpass<1><<<dim3(ghx, 1, nimg * 4), kRbThreads, 0, s>>>(p, c, B, A, XH, 4);
+                lb_combine<1, false><<<gcz, 256, 0, s>>>(p, A, g, nullptr, am, tm, wm, 0);
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
+    }
     p.r = pl->r_box;
     p.halo = 3 * pl->r_box;
     const double L = 2.0 * pl->r_box + 1.0;

@@ -57,8 +57,8 @@ extern "C" bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, co
     if (!bwd_supported(plan))
         return fail(BF_EUNSUPPORTED, "bf_backward_noalloc: no kernel for this spatial support "
                                      "without device scratch (Gaussian R <= 24 or box r <= 8; "
-                                     "the box with r > 8 runs through scratch that "
-                                     "bf_backward allocates)");
+                                     "the box with r > 8 and the recursive Gaussian run "
+                                     "through scratch that bf_backward allocates)");
     if (grad_sigma_r && plan->cosine)
         return fail(BF_EINVAL, "bf_backward_noalloc: a cosine-polynomial plan has no sigma_r; "
                                "pass grad_sigma_r = NULL");

@@ -285,9 +285,9 @@ def test_tall_images_are_refused_on_the_host(bf):
 
 
 def test_backward_supports_on_the_host(bf):
-    # the box with 8 < r <= 64 (the largest box a plan takes) has an adjoint
-    # through device scratch, which the no-alloc entry point refuses; the
-    # recursive Gaussian has none.  Refused before any pointer is read.
+    # the box with 8 < r <= 64 (the largest box a plan takes) and the
+    # recursive Gaussian have adjoints through device scratch, which the
+    # no-alloc entry point refuses before any pointer is read
     from paper_1105_4204_gb300 import _lib
     l = _lib.lib()
     l.bf_backward_noalloc.restype = ctypes.c_int
@@ -303,8 +303,9 @@ def test_backward_supports_on_the_host(bf):
     with pytest.raises(Exception):  # no plan beyond the largest supported box
         bf.Plan(65.0, 20.0, kind="box", radius=65)
     rec = bf.Plan(10.0, 20.0, kind="recursive")
-    assert l.bf_backward(rec.handle, fake, fake, fake, fake, fake, null, 64, 64, null, 0,
-                         null) == 2
+    assert l.bf_backward_noalloc(rec.handle, fake, fake, fake, fake, fake, null, 64, 64,
+                                 null) == 2
+    assert b"recursive" in l.bf_last_error()
 
 
 def test_recursive_gaussian_plan(bf, oracle):

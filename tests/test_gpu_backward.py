@@ -1,7 +1,8 @@
 """GPU parity of the adjoint (dL/df and dL/dsigma_r) against the FP64 oracle:
 its exact gradient of eq. (BF), and central finite differences of its brute
 force.  The fused adjoint kernel serves the Gaussian and the box with r <= 8;
-the box with 8 < r <= 64 runs through per-term planes in device scratch.
+the box with 8 < r <= 64 and the recursive Gaussian (Section 3) run through
+per-term planes in device scratch.
 Bar: relative error <= 1e-3 (norm-wise, and per element against the largest
 element), as the differentiable workload specifies."""
 import numpy as np
@@ -252,6 +253,67 @@ def test_autograd_with_a_large_box(bf, oracle):
     for b in range(2):
         gref, gsref = oracle.bf_grad(imgs[b].astype(np.float64), u[b].astype(np.float64),
                                      sigma_r=30.0, w1=_w1(oracle, plan), N=plan.N)
+        assert np.abs(f.grad[b].cpu().numpy() - gref).max() <= REL * np.abs(gref).max()
+        gs_tot += gsref
+    assert abs(float(sr.grad) - gs_tot) <= REL * abs(gs_tot)
+
+
+@pytest.mark.parametrize("ss", [0.8, 3.0, 7.0])
+@pytest.mark.parametrize("H,W", [(13, 17), (37, 45), (64, 31)])
+def test_recursive_gaussian_gradient(bf, oracle, ss, H, W):
+    # the recursive filter's adjoint (its line filter's transpose) against the
+    # exact FP64 gradient with the filter's weight matrices
+    img = synth.rectangles(H, W, n_rect=4, noise=10.0, seed=H + int(10 * ss))
+    u = synth.upstream(img.shape, seed=W + int(10 * ss))
+    plan = bf.Plan(ss, 25.0, kind="recursive")
+    g, gs = _gpu_grad(bf, img, u, plan)
+    gref, gsref = oracle.bf_grad_rg(img.astype(np.float64), u.astype(np.float64), sigma_s=ss,
+                                    sigma_r=25.0, N=plan.N)
+    print("recursive sigma_s=%g %dx%d: max rel %.3e, sigma_r %.6g vs %.6g" % (
+        ss, H, W, np.abs(g - gref).max() / np.abs(gref).max(), gs, gsref))
+    _check(g, gref, gs, gsref)
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 17), (17, 1), (5, 3), (2, 2)])
+def test_recursive_gaussian_degenerate_images(bf, oracle, H, W):
+    # lines shorter than the recursions' reach: the starts' adjoints and the
+    # extension's fold carry most of each line (dL/dsigma_r with the 1e-2 bar
+    # of the other degenerate cases)
+    img = synth.rectangles(H, W, n_rect=3, noise=10.0, seed=H * 7 + W)
+    u = synth.upstream(img.shape, seed=H + 3 * W)
+    plan = bf.Plan(4.0, 20.0, kind="recursive")
+    g, gs = _gpu_grad(bf, img, u, plan)
+    gref, gsref = oracle.bf_grad_rg(img.astype(np.float64), u.astype(np.float64), sigma_s=4.0,
+                                    sigma_r=20.0, N=plan.N)
+    scale = max(np.abs(gref).max(), 1e-12)
+    assert np.abs(g - gref).max() <= REL * scale, np.abs(g - gref).max() / scale
+    assert abs(gs - gsref) <= 10 * REL * abs(gsref) + 1e-5
+
+
+def test_recursive_gaussian_stack_and_autograd(bf, oracle):
+    # a stack's images as single calls (bit for bit), and the autograd function
+    import torch
+    imgs = np.stack([synth.smooth_field(30, 41, noise=6.0, seed=s) for s in range(3)])
+    u = synth.upstream(imgs.shape, seed=41)
+    plan = bf.Plan(5.0, 30.0, kind="recursive")
+    ft = torch.from_numpy(imgs).cuda()
+    ut = torch.from_numpy(u).cuda()
+    out, q = bf.forward_stack(plan, ft, return_q=True)
+    g, gs = bf.backward_stack(plan, ft, out, q, ut)
+    total = 0.0
+    for b in range(3):
+        gb, gsb = bf.backward(plan, ft[b].contiguous(), out[b].contiguous(),
+                              q[b].contiguous(), ut[b].contiguous())
+        assert torch.equal(g[b], gb)
+        total += float(gsb)
+    assert float(gs) == pytest.approx(total, rel=1e-9, abs=1e-12)
+    f = ft.clone().requires_grad_(True)
+    sr = torch.tensor(30.0, device="cuda", requires_grad=True)
+    (bf.bilateral(f, 5.0, sr, kind="recursive") * ut).sum().backward()
+    gs_tot = 0.0
+    for b in range(3):
+        gref, gsref = oracle.bf_grad_rg(imgs[b].astype(np.float64), u[b].astype(np.float64),
+                                        sigma_s=5.0, sigma_r=30.0, N=plan.N)
         assert np.abs(f.grad[b].cpu().numpy() - gref).max() <= REL * np.abs(gref).max()
         gs_tot += gsref
     assert abs(float(sr.grad) - gs_tot) <= REL * abs(gs_tot)

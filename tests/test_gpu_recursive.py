@@ -86,14 +86,9 @@ def test_paper_timing_image_size(bf, oracle, ss):
     assert err <= TOL
 
 
-def test_backward_and_batch_refuse_the_recursive_filter(bf):
-    import torch
+def test_batch_refuses_the_recursive_filter(bf):
+    # (its adjoint is tested with the others in test_gpu_backward.py)
     from paper_1105_4204_gb300._lib import BfError
     plan = bf.Plan(3.0, 30.0, kind="recursive")
-    f = torch.rand(16, 16, device="cuda") * 255
-    out, q = bf.forward(plan, f, return_q=True)
-    with pytest.raises(BfError) as e:
-        bf.backward(plan, f, out, q, torch.ones_like(f))
-    assert e.value.status == 2
     with pytest.raises(BfError):
         bf.Batch([plan], [(16, 16)])
