@@ -465,7 +465,8 @@ bf_status bf_backward_stack(const bf_plan *plan, const float *f, const float *ou
  *   whose work overlaps on the GPU (other streams, other host threads) race
  *   on the array: serialise them.
  *   Supports: the fused adjoint's (Gaussian R <= 24, box r <= 8); the box
- *   with r > 8 needs device scratch and returns BF_EUNSUPPORTED here.
+ *   with r > 8 and the recursive Gaussian need device scratch and return
+ *   BF_EUNSUPPORTED here.
  *   Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  */
 bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, const float *out,
@@ -480,8 +481,9 @@ bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, const float *
  * terms) from a device work queue, largest cost first; each radius bucket
  * r = 1 .. 8 has its own configuration (tile shape and term split, see
  * bf_batch_set_config), and the term groups of split images are summed in
- * group order by one more kernel.  Images with 8 < r <= 64 run the streaming
- * sweeps of bf_forward in the same graph, in up to four concurrent chains
+ * group order by one more kernel.  Images with 8 < r <= 64, and images whose
+ * plan is the recursive Gaussian, run the streaming sweeps of bf_forward in
+ * the same graph, in up to four concurrent chains
  * (images spread over the chains largest cost first), concurrently with the
  * persistent launch.  Each image's result is bit-identical to bf_forward's
  * in the same configuration (bf_forward_set_shape with the bucket's shape
@@ -490,8 +492,9 @@ bf_status bf_backward_noalloc(const bf_plan *plan, const float *f, const float *
  * bf_batch_create  : plans[count], H[count], W[count] are host arrays; the
  *                    batch copies what it needs (the plans may be destroyed
  *                    afterwards).  Every plan must be the 3-pass box with
- *                    1 <= r <= 64 (BF_EUNSUPPORTED otherwise).  Allocates the
- *                    batch's device tables, queue and, if some r > 8, one
+ *                    1 <= r <= 64 or the recursive Gaussian
+ *                    (BF_EUNSUPPORTED otherwise).  Allocates the batch's
+ *                    device tables, queue and, if some image streams, one
  *                    scratch per chain of streaming images (the largest
  *                    bf_forward scratch among the chain's images); all freed
  *                    by bf_batch_destroy.

@@ -11,7 +11,8 @@
 // idle SMs per image.  The claim loop is bounded by the number of tiles; a
 // block that would exceed it sets the device error flag instead.
 //
-// Images with 8 < r <= 64: the streaming sweeps of the single-image path,
+// Images with 8 < r <= 64, and the recursive Gaussian's: the streaming sweeps
+// of the single-image path,
 // spread over kBatchLanes chains (largest cost first onto the least loaded);
 // the images of a chain run one after the other through that chain's
 // scratch, the chains and the persistent launch run concurrently.
@@ -455,8 +456,10 @@ static cudaError_t batch_build_graph(bf_batch *b) {
             img.in_z = 1;
             img.out_z = 1;
             const int lane = b->stream_lane[k];
-            le = launch_large_box(&b->stream_plans[k], img, b->d_scratch[lane],
-                                  b->lane_stream[lane]);
+            const bf_plan *sp = &b->stream_plans[k];
+            le = sp->kind == BF_SPATIAL_GAUSS_RECURSIVE
+                     ? launch_recursive(sp, img, b->d_scratch[lane], b->lane_stream[lane])
+                     : launch_large_box(sp, img, b->d_scratch[lane], b->lane_stream[lane]);
         }
         // join every lane back
         for (int k = 0; k < b->n_lanes && le == cudaSuccess; ++k) {
@@ -481,10 +484,12 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
         if (H[i] < 1 || W[i] < 1) return fail(BF_EINVAL, "bf_batch_create: a size is < 1");
         if ((long long)H[i] * W[i] > (1LL << 31) / 4)
             return fail(BF_EUNSUPPORTED, "bf_batch_create: an image is too large");
-        if (plans[i]->kind != BF_SPATIAL_BOX_ITER || plans[i]->r_box < 1 ||
-            plans[i]->r_box > kBatchMaxR)
+        const bool box_ok = plans[i]->kind == BF_SPATIAL_BOX_ITER && plans[i]->r_box >= 1 &&
+                            plans[i]->r_box <= kBatchMaxR;
+        if (!box_ok && plans[i]->kind != BF_SPATIAL_GAUSS_RECURSIVE)
             return fail(BF_EUNSUPPORTED,
-                        "bf_batch_create: the batch serves the 3-pass box with 1 <= r <= 64");
+                        "bf_batch_create: the batch serves the 3-pass box with 1 <= r <= 64 "
+                        "and the recursive Gaussian");
     }
     bf_batch *b = new (std::nothrow) bf_batch();
     if (!b) return fail(BF_ENOMEM, "bf_batch_create: out of host memory");
@@ -505,7 +510,10 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
         ImgDesc d{};
         d.H = H[i];
         d.W = W[i];
-        d.r = pl->r_box;
+        // the streaming images (box r > 8, and the recursive Gaussian, which
+        // carries r = kBatchTileMaxR + 1) run on the lanes, not in the tile queue
+        const bool rec = pl->kind == BF_SPATIAL_GAUSS_RECURSIVE;
+        d.r = rec ? kBatchTileMaxR + 1 : pl->r_box;
         d.n_terms = (int)pl->a32.size();
         d.term_off = (int)ta.size();
         d.q_scale = pl->q_scale;
@@ -514,7 +522,8 @@ extern "C" bf_status bf_batch_create(bf_batch **out, const bf_plan *const *plans
             b->h_imgs.push_back(d);
             b->stream_ids.push_back(i);
             b->stream_plans.push_back(*pl);
-            stream_ws.push_back(large_workspace(pl, H[i], W[i]));
+            stream_ws.push_back(rec ? recursive_workspace(pl, H[i], W[i])
+                                    : large_workspace(pl, H[i], W[i]));
             continue;
         }
         for (int k = 0; k < d.n_terms; ++k) {

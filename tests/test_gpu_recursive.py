@@ -86,9 +86,28 @@ def test_paper_timing_image_size(bf, oracle, ss):
     assert err <= TOL
 
 
-def test_batch_refuses_the_recursive_filter(bf):
-    # (its adjoint is tested with the others in test_gpu_backward.py)
-    from paper_1105_4204_gb300._lib import BfError
-    plan = bf.Plan(3.0, 30.0, kind="recursive")
-    with pytest.raises(BfError):
-        bf.Batch([plan], [(16, 16)])
+def test_batch_with_recursive_and_box_images(bf):
+    # recursive-Gaussian images run on the batch's streaming chains beside box
+    # images on tiles and on chains: each streaming image equals its
+    # single-image call bit for bit (the tile image up to the summation order
+    # of the single call's own configuration); the adjoint is tested with the
+    # others in test_gpu_backward.py
+    import torch
+    specs = [("recursive", 3.0, 30.0, 70, 90), ("box", 2.0, 25.0, 64, 80),
+             ("recursive", 10.0, 20.0, 130, 50), ("box", 12.0, 20.0, 40, 100),
+             ("recursive", 0.8, 40.0, 1, 33)]
+    plans = [bf.Plan(ss, sr, kind=k) for k, ss, sr, _, _ in specs]
+    imgs = [torch.from_numpy(synth.rectangles(h, w, seed=i)).cuda()
+            for i, (_, _, _, h, w) in enumerate(specs)]
+    outs = [torch.empty_like(t) for t in imgs]
+    batch = bf.Batch(plans, [tuple(t.shape) for t in imgs])
+    batch.bind(imgs, outs)
+    batch.forward()
+    torch.cuda.synchronize()
+    assert batch.check() == 0
+    for (k, ss, _, _, _), p, t, o in zip(specs, plans, imgs, outs):
+        ref = bf.forward(p, t)
+        if k == "recursive" or p.radius // 3 > 8:
+            assert torch.equal(o, ref)
+        else:
+            torch.testing.assert_close(o, ref, rtol=0, atol=1e-3)
