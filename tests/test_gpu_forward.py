@@ -367,6 +367,24 @@ def test_config2_full_size_sampled(bf, oracle, sigma_s):
     assert err <= TOL
 
 
+@pytest.mark.parametrize("r,H,W", [(32, 520, 333), (24, 530, 261)])
+def test_box_large_radius_prefetching_sweep(bf, oracle, r, H, W):
+    # images tall enough that the horizontal sweep takes its prefetching
+    # variant (one block per SM, the next chunk's loads issued ahead): an odd
+    # number of 16-row blocks and a width that ends inside a chunk; sampled
+    # pixels against the oracle
+    img = synth.smooth_field(H, W, noise=5.0, seed=r + W)
+    plan = bf.Plan(float(r), 20.0, kind="box", radius=r)
+    out = _run(bf, img, plan)
+    idx = synth.sample_indices(H, W, 256, seed=r)[::3]
+    ref = oracle.bf_brute_at(img.astype(np.float64), idx, sigma_r=20.0,
+                             w1=plan_w1(oracle, plan), N=plan.N)
+    err = np.abs(out.ravel()[idx] - ref).max()
+    print("box r=%d %dx%d (prefetching sweep) max abs err %.3e on %d px" % (
+        r, H, W, err, len(idx)))
+    assert err <= TOL
+
+
 def test_box_large_radius_error_does_not_grow_along_the_sweep(bf, oracle):
     # The vertical sweep runs one band over all 2048 rows here.  Its running
     # sums stay accurate only if a regenerated plane value equals the one
