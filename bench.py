@@ -520,6 +520,7 @@ def run_ours(args):
 
     if rank == 0 and not args.no_extras:
         extras.update(measure_fwd_bwd(bf, torch, dev, stream))
+        extras.update(measure_rg_bwd(bf, torch, dev, stream))
         extras.update(measure_batch(bf, torch, dev, stream))
         extras.update(measure_configs(bf, torch, dev, stream, acc_jobs))
         extras.update(measure_space_variant(bf, torch, dev, stream, acc_jobs))
@@ -605,6 +606,28 @@ def measure_fwd_bwd(bf, torch, dev, stream):
             "roofline_bwd": alu_roofline(b_ops, t_fb - t_f, peak,
                                          "gauss_bwd_instr_per_px x pixels; backward time = "
                                          "fwd+bwd minus fwd")}
+
+
+def measure_rg_bwd(bf, torch, dev, stream):
+    """The recursive Gaussian's adjoint (Section 3's spatial filter) on the
+    differentiable workload's stack: 16 x 512 x 512, sigma_s = 4, sigma_r = 25
+    (N = 43), with and without dL/dsigma_r (forward outside the timing)."""
+    import synth
+    B, HH, WW = 16, 512, 512
+    imgs = torch.from_numpy(np.stack([synth.rectangles(HH, WW, seed=s) for s in range(B)])).to(dev)
+    u = torch.from_numpy(synth.upstream((B, HH, WW), seed=1)).to(dev)
+    plan = bf.Plan(4.0, 25.0, 255.0, kind="recursive")
+    outs = torch.empty_like(imgs)
+    qs = torch.empty_like(imgs)
+    grads = torch.empty_like(imgs)
+    ws = torch.empty(64 * 1024, dtype=torch.float64, device=dev)
+    bf.forward_stack(plan, imgs, return_q=True, out=outs, q=qs)
+    t_b = _time(lambda: bf.backward_stack(plan, imgs, outs, qs, u, grad_in=grads, workspace=ws),
+                torch, stream, 3)
+    t_bd = _time(lambda: bf.backward_stack(plan, imgs, outs, qs, u, need_sigma=False,
+                                           grad_in=grads), torch, stream, 3)
+    return {"recursive_bwd_config": "16 x 512^2, recursive gauss sigma_s=4, sigma_r=25 (N=43)",
+            "recursive_bwd_ms": t_b, "recursive_bwd_image_gradient_only_ms": t_bd}
 
 
 def measure_configs(bf, torch, dev, stream, acc_jobs):
@@ -805,7 +828,7 @@ def run_extras_only(which):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     jobs = []  # accuracy checks need the oracle: not run on this profiling path
-    fn = {"fwd_bwd": measure_fwd_bwd, "batch": measure_batch,
+    fn = {"fwd_bwd": measure_fwd_bwd, "rg_bwd": measure_rg_bwd, "batch": measure_batch,
           "configs": lambda *a: measure_configs(*a, jobs),
           "space_variant": lambda *a: measure_space_variant(*a, jobs),
           "table2": measure_table2}[which]
@@ -825,7 +848,7 @@ def main():
     ap.add_argument("--sigma-s", default=None,
                     help="comma-separated subset of the workload's sigma_s values (profiling runs)")
     ap.add_argument("--extras-only",
-                    choices=["fwd_bwd", "batch", "configs", "space_variant", "table2"],
+                    choices=["fwd_bwd", "rg_bwd", "batch", "configs", "space_variant", "table2"],
                     default=None,
                     help="time only that extra workload and print its figures (profiling runs; "
                          "not the benchmark line)")

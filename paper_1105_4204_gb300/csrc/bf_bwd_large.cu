@@ -343,29 +343,33 @@ __device__ __forceinline__ float rb_step(const RbCoef &c, float x, float &w, flo
 template <int ROUND, class In>
 __device__ __forceinline__ void rb_line(const RbCoef &c, In &&in, int n, float *line,
                                         float *ext, long long st) {
+    constexpr int CH = 8;  // samples whose loads are issued together
     const int E = n + c.P;
     float w, d1 = 0.f, d2 = 0.f;
     float z1 = 0.f, z2 = 0.f, z3 = 0.f;  // the causal pass's last three outputs
-    float last = 0.f;                    // ROUND 0: sample n - 1, the extension's value
-    if constexpr (ROUND == 0) {
-        w = in(0);  // steady state of the first sample
-    } else {
-        w = 0.f;
-    }
-    for (int k = 0; k < E; ++k) {
-        float x;
-        if (k < n) {
-            x = in(k);
-            last = x;
-        } else {
-            x = ROUND == 0 ? last : 0.f;
+    // ROUND 0: the steady state of the first sample, and the extension's value
+    const float first_in = ROUND == 0 ? in(0) : 0.f;
+    const float last_in = ROUND == 0 ? in(n - 1) : 0.f;
+    w = first_in;
+    for (int k0 = 0; k0 < E; k0 += CH) {
+        float xs[CH];
+#pragma unroll
+        for (int d = 0; d < CH; ++d) {
+            const int k = k0 + d;
+            xs[d] = k < n ? in(k) : last_in;  // ROUND 1: last_in is 0 (zero extension)
         }
-        rb_step(c, x, w, d1, d2);
-        if (k < n) line[k * st] = w;
-        else ext[(k - n) * st] = w;
-        z3 = z2;
-        z2 = z1;
-        z1 = w;
+#pragma unroll
+        for (int d = 0; d < CH; ++d) {
+            const int k = k0 + d;
+            if (k < E) {
+                rb_step(c, xs[d], w, d1, d2);
+                if (k < n) line[k * st] = w;
+                else ext[(k - n) * st] = w;
+                z3 = z2;
+                z2 = z1;
+                z1 = w;
+            }
+        }
     }
     // anticausal: ROUND 0 from the steady state of the causal pass's last
     // output; ROUND 1 from zero, the adjoint of that start entering at E - 1
@@ -376,18 +380,30 @@ __device__ __forceinline__ void rb_line(const RbCoef &c, In &&in, int n, float *
     }
     d1 = d2 = 0.f;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, fold = 0.f;
-    for (int k = E - 1; k >= 0; --k) {
-        float x = k < n ? line[k * st] : ext[(k - n) * st];
-        if (ROUND == 1 && k == E - 1)
-            x = __fadd_rn(x, __fmul_rn(__fmaf_rn(c.oneMinusB, z1, __fmaf_rn(c.D1, z2,
-                                                                            __fmul_rn(c.D2, z3))),
-                                       c.invB));
-        rb_step(c, x, w, d1, d2);
-        if (k < n) line[k * st] = w;
-        else if (ROUND == 1) fold = __fadd_rn(fold, w);
-        v2 = v1;
-        v1 = v0;
-        v0 = w;
+    for (int k1 = E - 1; k1 >= 0; k1 -= CH) {
+        float xs[CH];
+#pragma unroll
+        for (int d = 0; d < CH; ++d) {
+            const int k = k1 - d;
+            xs[d] = k >= 0 ? (k < n ? line[k * st] : ext[(k - n) * st]) : 0.f;
+        }
+#pragma unroll
+        for (int d = 0; d < CH; ++d) {
+            const int k = k1 - d;
+            if (k >= 0) {
+                float x = xs[d];
+                if (ROUND == 1 && k == E - 1)
+                    x = __fadd_rn(x, __fmul_rn(__fmaf_rn(c.oneMinusB, z1,
+                                                         __fmaf_rn(c.D1, z2, __fmul_rn(c.D2, z3))),
+                                               c.invB));
+                rb_step(c, x, w, d1, d2);
+                if (k < n) line[k * st] = w;
+                else if (ROUND == 1) fold = __fadd_rn(fold, w);
+                v2 = v1;
+                v1 = v0;
+                v0 = w;
+            }
+        }
     }
     if constexpr (ROUND == 1) {
         // the causal start's adjoint on the first pixel, the extension folded
